@@ -1,0 +1,129 @@
+"""Diagonal-Jacobian (Jacobi) amplitude iteration with DIIS (test infrastructure).
+
+The paper drives ASCC with the diagonal approximate Jacobian update plus DIIS
+used by ground-state CCSD codes (Sec. III.B) and stops when the largest
+residual and the energy change fall below thresholds (Sec. III.A).  The
+paper does not spell out the DIIS details; the rules below are the ones this
+project fixes, and the CUDA solver follows the same rules:
+
+* denominators from the bare orbital energies:
+    D1[i,a] = e_i - e_a,  D2[i,j,a,b] = e_i + e_j - e_a - e_b,
+    D3[i,j,k,a,b,c] = e_i + e_j + e_k - e_a - e_b - e_c;
+* Jacobi step t' = t + R / D;
+* DIIS over the vector (t1, t2, t3'): the error is e = t' - t, the history
+  keeps the last `diis_dim` pairs (t', e); once it holds `diis_start` pairs
+  the new amplitudes are sum_k c_k t'_k with c solving the bordered system
+  [[G, 1], [1, 0]] [c; l] = [0; 1], G_kl = e_k . e_l scaled by 1/max diag G
+  plus a 1e-12 ridge, solved by Gaussian elimination with partial pivoting;
+  a non-finite or degenerate solve empties the history but the newest pair;
+* converged when max|R| <= r_tol and |E - E_previous| <= e_tol, checked on
+  the residual of the current amplitudes before any update.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class SolveResult:
+    energy: float
+    iterations: int
+    max_resid: float
+    converged: bool
+    t1: np.ndarray
+    t2: np.ndarray
+    t3: np.ndarray
+    history: list = field(default_factory=list)
+
+
+def bordered_solve(G: np.ndarray):
+    """DIIS coefficients from the Gram matrix G (see module docstring)."""
+    m = G.shape[0]
+    scale = np.max(np.abs(np.diag(G)))
+    if not np.isfinite(scale) or scale <= 0.0:
+        return None
+    A = np.zeros((m + 1, m + 1))
+    A[:m, :m] = G / scale + 1e-12 * np.eye(m)
+    A[:m, m] = 1.0
+    A[m, :m] = 1.0
+    b = np.zeros(m + 1); b[m] = 1.0
+    # Gaussian elimination with partial pivoting
+    n = m + 1
+    for c in range(n):
+        piv = c + int(np.argmax(np.abs(A[c:, c])))
+        if abs(A[piv, c]) < 1e-300:
+            return None
+        if piv != c:
+            A[[c, piv]] = A[[piv, c]]; b[[c, piv]] = b[[piv, c]]
+        for r in range(c + 1, n):
+            f = A[r, c] / A[c, c]
+            A[r, c:] -= f * A[c, c:]
+            b[r] -= f * b[c]
+    x = np.zeros(n)
+    for r in range(n - 1, -1, -1):
+        x[r] = (b[r] - A[r, r + 1:] @ x[r + 1:]) / A[r, r]
+    if not np.all(np.isfinite(x)):
+        return None
+    return x[:m]
+
+
+def denominators(eps, o, t3_idx=None):
+    eo, ev = eps[:o], eps[o:]
+    D1 = eo[:, None] - ev[None, :]
+    D2 = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+    if t3_idx is None or len(t3_idx) == 0:
+        D3 = np.zeros(0)
+    else:
+        i, j, k, a, b, c = t3_idx.T
+        D3 = eo[i] + eo[j] + eo[k] - ev[a] - ev[b] - ev[c]
+    return D1, D2, D3
+
+
+def solve(resid_fn, eps, o, t1, t2, t3, t3_idx=None, r_tol=1e-8, e_tol=1e-10,
+          max_iter=200, diis_dim=8, diis_start=3, verbose=False):
+    """Iterate resid_fn(t1, t2, t3) -> (E, R1, R2, R3) to convergence."""
+    D1, D2, D3 = denominators(eps, o, t3_idx)
+    shapes = [t1.shape, t2.shape, t3.shape]
+    sizes = [t1.size, t2.size, t3.size]
+
+    def pack(a, b, c):
+        return np.concatenate([a.ravel(), b.ravel(), c.ravel()])
+
+    def unpack(x):
+        p = np.cumsum([0] + sizes)
+        return [x[p[k]:p[k + 1]].reshape(shapes[k]) for k in range(3)]
+
+    hist_t, hist_e = [], []
+    e_prev = None
+    log = []
+    for it in range(max_iter + 1):
+        En, R1, R2, R3 = resid_fn(t1, t2, t3)
+        rmax = max(np.max(np.abs(R1)) if R1.size else 0.0, np.max(np.abs(R2)),
+                   np.max(np.abs(R3)) if R3 is not None and R3.size else 0.0)
+        log.append((it, En, rmax))
+        if verbose:
+            print(f"it {it:3d}  E {En:.12f}  max|R| {rmax:.3e}")
+        if not np.isfinite(En) or not np.isfinite(rmax):
+            return SolveResult(En, it, rmax, False, t1, t2, t3, log)
+        if e_prev is not None and rmax <= r_tol and abs(En - e_prev) <= e_tol:
+            return SolveResult(En, it, rmax, True, t1, t2, t3, log)
+        if it == max_iter:
+            break
+        e_prev = En
+        R3v = R3 if R3 is not None else np.zeros(0)
+        tn = pack(t1 + R1 / D1, t2 + R2 / D2, t3 + (R3v / D3 if R3v.size else 0.0))
+        err = tn - pack(t1, t2, t3)
+        hist_t.append(tn); hist_e.append(err)
+        if len(hist_t) > diis_dim:
+            hist_t.pop(0); hist_e.pop(0)
+        if len(hist_t) >= diis_start:
+            Emat = np.array(hist_e)
+            c = bordered_solve(Emat @ Emat.T)
+            if c is None:
+                hist_t = hist_t[-1:]; hist_e = hist_e[-1:]
+            else:
+                tn = c @ np.array(hist_t)
+        t1, t2, t3 = unpack(tn)
+    return SolveResult(En, max_iter, rmax, False, t1, t2, t3, log)
