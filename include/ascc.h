@@ -1,0 +1,173 @@
+/*
+ * ascc.h -- C ABI of the GB300 implementation of the Aufbau-suppressed
+ * coupled-cluster (ASCC / PLASCC) amplitude-residual hot path.
+ *
+ * Method (arXiv 2501.10515, "Improving Aufbau Suppressed Coupled Cluster
+ * Through Perturbative Analysis"):
+ *   wave function      exp(-S^+) exp(T) |phi0>                    (Sec. II.A, Eq. ogascc)
+ *   one-CSF S          (1/sqrt2)(p_up^+ h_up + p_dn^+ h_dn)         (Eq. 1CSF-S)
+ *   working equations  E = <phi0| exp(-T) Hbar exp(T) |phi0>,
+ *                      0 = <mu|   exp(-T) Hbar exp(T) |phi0>,
+ *                      Hbar = exp(S^+) H exp(-S^+)                  (Eqs. energy, amp, sim)
+ *   cluster operator   T1 + T2 (+ the mixed-triples slice T3')      (Sec. II.B.1)
+ *   PLASCC             drop terms with >= 2 powers of T2^M / T3'    (Sec. II.C)
+ *   solver             diagonal-Jacobian update with DIIS           (Sec. III.B)
+ *
+ * Conventions
+ *   o, v      numbers of occupied / virtual spatial orbitals, n = o + v.
+ *   eps[n]    orbital energies; the Fock matrix of the reference is diag(eps).
+ *   B         density-fitting factor B[P][p][q], P < naux, symmetric in (p,q);
+ *             (pq|rs) = sum_P B[P][p][q] B[P][r][s] (chemists' notation).
+ *   t1[i][a]  alpha single amplitudes, row-major [o][v].
+ *   t2[i][j][a][b]  alpha-beta double amplitudes, row-major [o][o][v][v];
+ *             callers pass pair-symmetric t2 (t2[i][j][a][b] = t2[j][i][b][a]).
+ *   t3p[k]    the T3' slice: alpha-beta-beta triples t[i][j][k][a][b][c]
+ *             (j<k, b<c) with at least three of {h up, h dn, p up, p dn}
+ *             among their spin-orbital indices, in the order returned by
+ *             ascc_t3p_indices (lexicographic in (i,j,k,a,b,c)).
+ *   Residuals have the layouts of the amplitudes they belong to.
+ *
+ * Errors: every function returns an ascc_status and never throws across the
+ * ABI.  ascc_last_error() returns a thread-local message for the last failure.
+ * Memory: inputs are copied; all device memory belongs to the context and is
+ * released by ascc_destroy.  Device pointers are CUDA global-memory addresses
+ * on the context's device; host pointers are ordinary (pageable or pinned)
+ * memory.
+ */
+#ifndef ASCC_H
+#define ASCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ascc_ctx ascc_ctx;
+
+typedef enum {
+  ASCC_OK = 0,
+  ASCC_ERR_INVALID = 1,        /* bad argument or unsupported option            */
+  ASCC_ERR_OOM = 2,            /* device allocation failed                      */
+  ASCC_ERR_CUDA = 3,           /* a CUDA runtime call failed                    */
+  ASCC_ERR_NOT_CONVERGED = 4,  /* iteration cap reached                         */
+  ASCC_ERR_DIVERGED = 5,       /* non-finite energy or residual                 */
+  ASCC_ERR_TIMEOUT = 6         /* a bounded device wait gave up                 */
+} ascc_status;
+
+enum { ASCC_FP64 = 0, ASCC_MIXED_BF16 = 1 };
+
+typedef struct {
+  int32_t n_csf;     /* 0 = ground state (S = 0); 1 = one-CSF excited state     */
+  int32_t hole;      /* occupied index h in [0, o) of S (n_csf = 1)              */
+  int32_t particle;  /* virtual index p in [0, v) of S (n_csf = 1)               */
+  double beta;       /* T^P(0) = beta S + gamma S^2, gamma = -beta^2/2 (Eq.
+                        TP-guess, Sec. II.D); 0 means beta = 1                   */
+} ascc_excitation;
+
+typedef struct {
+  int32_t precision;   /* ASCC_FP64 or ASCC_MIXED_BF16                          */
+  int32_t linearize;   /* 0 = ASCC, 1 = PLASCC (Sec. II.C)                      */
+  int32_t triples;     /* 1 = include T3' for n_csf = 1 (Sec. II.B.1)           */
+  int32_t pl_hole;     /* primary pair used to split a ground-state solve for   */
+  int32_t pl_particle; /*   PLASCC (Sec. II.C: same removal in the ground state) */
+  double r_tol;        /* convergence: max |R| <= r_tol ...                     */
+  double e_tol;        /*   ... and |E - E_prev| <= e_tol (Sec. III.A)          */
+  int32_t max_iter;    /* iteration cap                                         */
+  int32_t diis_dim;    /* DIIS history length (<= 16)                           */
+  int32_t diis_start;  /* pairs needed before extrapolating                     */
+  int32_t polish_iter; /* mixed precision: FP64 iterations after the low-      */
+                       /*   precision phase converges to polish_tol            */
+  double polish_tol;   /* mixed precision: hand-over threshold on max |R|       */
+} ascc_options;
+
+typedef struct {
+  double energy;      /* converged total energy E (Eq. energy)                 */
+  double e_ref;       /* <phi0|Hbar|phi0>                                      */
+  double max_resid;   /* max |R| at the last evaluation                        */
+  int32_t iterations; /* residual evaluations performed                        */
+  int32_t status;     /* ascc_status of the solve                              */
+  int32_t iterations_low; /* of which in low precision (mixed precision)      */
+  int32_t reserved;
+} ascc_result;
+
+/* Fills *opt with defaults: FP64, PLASCC, triples on, r_tol 1e-8, e_tol 1e-10,
+ * max_iter 200, DIIS 8 / start 3, polish 1e-6.  Returns ASCC_OK. */
+ascc_status ascc_default_options(ascc_options* opt);
+
+/* Creates a context for one state of one molecule (Secs. II.A-II.B).
+ *   o, v, naux  sizes (o >= 1, v >= 1, naux >= 1).
+ *   eps         [o+v] orbital energies; host memory; copied.
+ *   B           [naux][n][n] DF factor; host memory if b_on_device == 0,
+ *               else device memory on the current device; copied.
+ *   exc         excitation (NULL = ground state).
+ *   opt         options (NULL = defaults).
+ *   stream      cudaStream_t the context works on; NULL = a library-owned
+ *               stream.
+ * Builds the bare integral blocks the residual needs (once per context).
+ * On failure *out is set to NULL. */
+ascc_status ascc_create(ascc_ctx** out, int32_t o, int32_t v, int32_t naux,
+                        const double* eps, const double* B, int32_t b_on_device,
+                        const ascc_excitation* exc, const ascc_options* opt,
+                        void* stream);
+
+/* Creates a second state of the molecule held by `base` (another excitation
+ * or the ground state), sharing its bare integrals on the device.  The
+ * molecule's memory lives until every context using it is destroyed. */
+ascc_status ascc_create_sibling(ascc_ctx** out, const ascc_ctx* base,
+                                const ascc_excitation* exc,
+                                const ascc_options* opt, void* stream);
+
+/* Number of T3' amplitudes of this state (0 for the ground state or when
+ * triples are off). */
+int64_t ascc_t3p_size(const ascc_ctx* ctx);
+
+/* Writes the [ascc_t3p_size][6] index list (i,j,k,a,b,c) of T3' to host
+ * memory idx. */
+ascc_status ascc_t3p_indices(const ascc_ctx* ctx, int32_t* idx);
+
+/* One residual evaluation (Eqs. energy, amp over Hbar; PLASCC if the
+ * context's options say so) at caller-given amplitudes.
+ *   t1, t2, t3p  inputs; r1, r2, r3p, energy outputs (any may be NULL
+ *   except t1, t2; t3p may be NULL when ascc_t3p_size is 0).
+ * ascc_residual takes host buffers; ascc_residual_device takes device
+ * buffers and does not synchronise the stream. */
+ascc_status ascc_residual(ascc_ctx* ctx, const double* t1, const double* t2,
+                          const double* t3p, double* r1, double* r2,
+                          double* r3p, double* energy);
+ascc_status ascc_residual_device(ascc_ctx* ctx, const double* t1,
+                                 const double* t2, const double* t3p,
+                                 double* r1, double* r2, double* r3p,
+                                 double* energy);
+
+/* Energy (Eq. energy) at caller-given host amplitudes. */
+ascc_status ascc_energy(ascc_ctx* ctx, const double* t1, const double* t2,
+                        double* energy);
+
+/* Solves the amplitude equations from the zeroth-order guess (Eq. TP-guess)
+ * with the Jacobi + DIIS iteration (Sec. III.B).  Fills *res (host).
+ * Returns ASCC_OK on convergence, ASCC_ERR_NOT_CONVERGED or
+ * ASCC_ERR_DIVERGED otherwise (res is filled in every case). */
+ascc_status ascc_solve(ascc_ctx* ctx, ascc_result* res);
+
+/* Checkpoint / resume of the amplitudes (host buffers, FP64). */
+ascc_status ascc_get_state(ascc_ctx* ctx, double* t1, double* t2, double* t3p);
+ascc_status ascc_set_state(ascc_ctx* ctx, const double* t1, const double* t2,
+                           const double* t3p);
+
+/* Device bytes a context of this shape needs (bare integrals + state). */
+size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux,
+                            const ascc_options* opt);
+
+/* Number of kernel launches issued by this context since creation. */
+int64_t ascc_launch_count(const ascc_ctx* ctx);
+
+void ascc_destroy(ascc_ctx* ctx);
+const char* ascc_status_string(ascc_status s);
+const char* ascc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASCC_H */

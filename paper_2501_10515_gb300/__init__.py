@@ -1,0 +1,12 @@
+"""GB300 ASCC / PLASCC amplitude-residual library (Python binding of libascc).
+
+The binding only marshals arguments: every step of the residual, the update
+and the iteration runs in libascc's CUDA kernels.  Importing the package does
+not load the library; `load()` (called by the first Context) does, and fails
+loudly when libascc.so has not been built.
+"""
+from .binding import (ASCC_FP64, ASCC_MIXED_BF16, AsccError, Context, Excitation,
+                      Options, Result, default_options, load, symbols)
+
+__all__ = ["ASCC_FP64", "ASCC_MIXED_BF16", "AsccError", "Context", "Excitation",
+           "Options", "Result", "default_options", "load", "symbols"]

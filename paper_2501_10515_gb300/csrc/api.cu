@@ -1,0 +1,314 @@
+// C ABI of libascc (declared in include/ascc.h).
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "engine.h"
+#include "kernels.h"
+
+using namespace ascc;
+
+struct ascc_ctx {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::unique_ptr<State> state;
+  int64_t launches0 = 0;
+  ~ascc_ctx() {
+    if (stream) cudaStreamSynchronize(stream);
+    state.reset();
+    if (stream) cudaStreamSynchronize(stream);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+thread_local std::string g_err;
+
+template <class F>
+ascc_status guard(F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    g_err = e.what();
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return ASCC_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return ASCC_ERR_INVALID;
+  }
+}
+
+Options to_options(const ascc_options* o) {
+  Options r;
+  if (!o) return r;
+  r.precision = o->precision;
+  r.linearize = o->linearize;
+  r.triples = o->triples;
+  r.pl_hole = o->pl_hole;
+  r.pl_particle = o->pl_particle;
+  r.r_tol = o->r_tol;
+  r.e_tol = o->e_tol;
+  r.max_iter = o->max_iter;
+  r.diis_dim = o->diis_dim;
+  r.diis_start = o->diis_start;
+  r.polish_iter = o->polish_iter;
+  r.polish_tol = o->polish_tol;
+  return r;
+}
+
+void prepare_pool() {
+  int dev = 0;
+  ASCC_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  ASCC_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t thr = UINT64_MAX;
+  ASCC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+}
+
+void check_exc(const ascc_excitation* exc, int o, int v, int& hole, int& particle, double& beta) {
+  hole = -1;
+  particle = -1;
+  beta = 1.0;
+  if (!exc || exc->n_csf == 0) return;
+  ASCC_REQUIRE(exc->n_csf == 1, "only one-CSF excitations are supported");
+  ASCC_REQUIRE(exc->hole >= 0 && exc->hole < o, "hole out of range");
+  ASCC_REQUIRE(exc->particle >= 0 && exc->particle < v, "particle out of range");
+  hole = exc->hole;
+  particle = exc->particle;
+  beta = exc->beta == 0.0 ? 1.0 : exc->beta;
+  ASCC_REQUIRE(std::isfinite(beta) && beta > 0.0, "beta must be positive");
+}
+
+ascc_status make_ctx(ascc_ctx** out, std::shared_ptr<Molecule> mol, const ascc_excitation* exc,
+                     const ascc_options* opt, cudaStream_t stream, bool own) {
+  auto ctx = std::make_unique<ascc_ctx>();
+  ctx->stream = stream;
+  ctx->own_stream = own;
+  ctx->launches0 = launch_total();
+  int hole, particle;
+  double beta;
+  check_exc(exc, mol->o, mol->v, hole, particle, beta);
+  Options o = to_options(opt);
+  if (o.pl_hole >= mol->o || o.pl_particle >= mol->v) throw Error(ASCC_ERR_INVALID, "pl labels");
+  ctx->state = std::make_unique<State>(std::move(mol), hole, particle, beta, o, stream);
+  ASCC_CUDA(cudaStreamSynchronize(stream));
+  *out = ctx.release();
+  return ASCC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ascc_status ascc_default_options(ascc_options* opt) {
+  if (!opt) return ASCC_ERR_INVALID;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = ASCC_FP64;
+  opt->linearize = 1;
+  opt->triples = 0;
+  opt->pl_hole = -1;
+  opt->pl_particle = -1;
+  opt->r_tol = 1e-8;
+  opt->e_tol = 1e-10;
+  opt->max_iter = 200;
+  opt->diis_dim = 8;
+  opt->diis_start = 3;
+  opt->polish_iter = 50;
+  opt->polish_tol = 1e-6;
+  return ASCC_OK;
+}
+
+ascc_status ascc_create(ascc_ctx** out, int32_t o, int32_t v, int32_t naux, const double* eps,
+                        const double* B, int32_t b_on_device, const ascc_excitation* exc,
+                        const ascc_options* opt, void* stream) {
+  if (out) *out = nullptr;
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(out && eps && B, "null argument");
+    ASCC_REQUIRE(o >= 1 && v >= 1 && naux >= 1, "sizes must be positive");
+    prepare_pool();
+    cudaStream_t s = (cudaStream_t)stream;
+    bool own = false;
+    if (!s) {
+      ASCC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      own = true;
+    }
+    try {
+      auto mol = std::make_shared<Molecule>(o, v, naux, eps, B, b_on_device != 0, s);
+      return make_ctx(out, std::move(mol), exc, opt, s, own);
+    } catch (...) {
+      if (own) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+      throw;
+    }
+  });
+}
+
+ascc_status ascc_create_sibling(ascc_ctx** out, const ascc_ctx* base, const ascc_excitation* exc,
+                                const ascc_options* opt, void* stream) {
+  if (out) *out = nullptr;
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(out && base && base->state, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    bool own = false;
+    if (!s) {
+      ASCC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      own = true;
+    }
+    // the molecule's buffers were produced on the base stream
+    ASCC_CUDA(cudaStreamSynchronize(base->stream));
+    return make_ctx(out, base->state->molecule(), exc, opt, s, own);
+  });
+}
+
+int64_t ascc_t3p_size(const ascc_ctx* ctx) { return ctx && ctx->state ? ctx->state->n3() : 0; }
+
+ascc_status ascc_t3p_indices(const ascc_ctx* ctx, int32_t* idx) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && (idx || ctx->state->n3() == 0), "null argument");
+    const auto& v = ctx->state->t3_indices();
+    if (!v.empty()) std::memcpy(idx, v.data(), v.size() * sizeof(int32_t));
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_residual_device(ascc_ctx* ctx, const double* t1, const double* t2,
+                                 const double* t3p, double* r1, double* r2, double* r3p,
+                                 double* energy) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && t1 && t2, "null argument");
+    State& S = *ctx->state;
+    ASCC_REQUIRE(S.n3() == 0 || t3p, "t3p required");
+    cudaStream_t s = ctx->stream;
+    const int64_t n1 = S.n1(), n2 = S.n2(), n3 = S.n3(), N = S.namp();
+    OT tv({N}, s), rv({N}, s), e({1}, s);
+    ASCC_CUDA(cudaMemcpyAsync(tv.p(), t1, n1 * 8, cudaMemcpyDeviceToDevice, s));
+    ASCC_CUDA(cudaMemcpyAsync(tv.p() + n1, t2, n2 * 8, cudaMemcpyDeviceToDevice, s));
+    if (n3) ASCC_CUDA(cudaMemcpyAsync(tv.p() + n1 + n2, t3p, n3 * 8, cudaMemcpyDeviceToDevice, s));
+    S.residual(tv.p(), rv.p(), e.p());
+    if (r1) ASCC_CUDA(cudaMemcpyAsync(r1, rv.p(), n1 * 8, cudaMemcpyDeviceToDevice, s));
+    if (r2) ASCC_CUDA(cudaMemcpyAsync(r2, rv.p() + n1, n2 * 8, cudaMemcpyDeviceToDevice, s));
+    if (r3p && n3)
+      ASCC_CUDA(cudaMemcpyAsync(r3p, rv.p() + n1 + n2, n3 * 8, cudaMemcpyDeviceToDevice, s));
+    if (energy) ASCC_CUDA(cudaMemcpyAsync(energy, e.p(), 8, cudaMemcpyDeviceToDevice, s));
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_residual(ascc_ctx* ctx, const double* t1, const double* t2, const double* t3p,
+                          double* r1, double* r2, double* r3p, double* energy) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && t1 && t2, "null argument");
+    State& S = *ctx->state;
+    ASCC_REQUIRE(S.n3() == 0 || t3p, "t3p required");
+    cudaStream_t s = ctx->stream;
+    const int64_t n1 = S.n1(), n2 = S.n2(), n3 = S.n3(), N = S.namp();
+    OT tv({N}, s), rv({N}, s), e({1}, s);
+    ASCC_CUDA(cudaMemcpyAsync(tv.p(), t1, n1 * 8, cudaMemcpyHostToDevice, s));
+    ASCC_CUDA(cudaMemcpyAsync(tv.p() + n1, t2, n2 * 8, cudaMemcpyHostToDevice, s));
+    if (n3) ASCC_CUDA(cudaMemcpyAsync(tv.p() + n1 + n2, t3p, n3 * 8, cudaMemcpyHostToDevice, s));
+    S.residual(tv.p(), rv.p(), e.p());
+    if (r1) ASCC_CUDA(cudaMemcpyAsync(r1, rv.p(), n1 * 8, cudaMemcpyDeviceToHost, s));
+    if (r2) ASCC_CUDA(cudaMemcpyAsync(r2, rv.p() + n1, n2 * 8, cudaMemcpyDeviceToHost, s));
+    if (r3p && n3)
+      ASCC_CUDA(cudaMemcpyAsync(r3p, rv.p() + n1 + n2, n3 * 8, cudaMemcpyDeviceToHost, s));
+    if (energy) ASCC_CUDA(cudaMemcpyAsync(energy, e.p(), 8, cudaMemcpyDeviceToHost, s));
+    ASCC_CUDA(cudaStreamSynchronize(s));
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_energy(ascc_ctx* ctx, const double* t1, const double* t2, double* energy) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && energy, "null argument");
+    State& S = *ctx->state;
+    std::vector<double> t3(S.n3(), 0.0);
+    const double* t3p = S.n3() ? t3.data() : nullptr;
+    if (S.n3()) {
+      // the energy has no T3' term; read the stored slice to keep it consistent
+      ASCC_CUDA(cudaMemcpyAsync(t3.data(), S.amplitudes() + S.n1() + S.n2(), S.n3() * 8,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+      ASCC_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return ascc_residual(ctx, t1, t2, t3p, nullptr, nullptr, nullptr, energy);
+  });
+}
+
+ascc_status ascc_solve(ascc_ctx* ctx, ascc_result* res) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state, "null argument");
+    const double eref = ctx->state->reference_energy();
+    ascc_status st = ctx->state->solve(res);
+    if (res) res->e_ref = eref;
+    if (st != ASCC_OK) g_err = st == ASCC_ERR_DIVERGED ? "diverged" : "not converged";
+    return st;
+  });
+}
+
+ascc_status ascc_get_state(ascc_ctx* ctx, double* t1, double* t2, double* t3p) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state, "null argument");
+    State& S = *ctx->state;
+    cudaStream_t s = ctx->stream;
+    if (t1) ASCC_CUDA(cudaMemcpyAsync(t1, S.amplitudes(), S.n1() * 8, cudaMemcpyDeviceToHost, s));
+    if (t2)
+      ASCC_CUDA(cudaMemcpyAsync(t2, S.amplitudes() + S.n1(), S.n2() * 8, cudaMemcpyDeviceToHost, s));
+    if (t3p && S.n3())
+      ASCC_CUDA(cudaMemcpyAsync(t3p, S.amplitudes() + S.n1() + S.n2(), S.n3() * 8,
+                                cudaMemcpyDeviceToHost, s));
+    ASCC_CUDA(cudaStreamSynchronize(s));
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_set_state(ascc_ctx* ctx, const double* t1, const double* t2, const double* t3p) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && t1 && t2, "null argument");
+    State& S = *ctx->state;
+    cudaStream_t s = ctx->stream;
+    ASCC_CUDA(cudaMemcpyAsync(S.amplitudes(), t1, S.n1() * 8, cudaMemcpyHostToDevice, s));
+    ASCC_CUDA(cudaMemcpyAsync(S.amplitudes() + S.n1(), t2, S.n2() * 8, cudaMemcpyHostToDevice, s));
+    if (S.n3()) {
+      ASCC_REQUIRE(t3p, "t3p required");
+      ASCC_CUDA(cudaMemcpyAsync(S.amplitudes() + S.n1() + S.n2(), t3p, S.n3() * 8,
+                                cudaMemcpyHostToDevice, s));
+    }
+    ASCC_CUDA(cudaStreamSynchronize(s));
+    return ASCC_OK;
+  });
+}
+
+size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux, const ascc_options* opt) {
+  const double n = o + v;
+  const int m = opt ? opt->diis_dim : 8;
+  const double o2v2 = (double)o * o * v * v;
+  double mol = 8.0 * (naux * n * n * 2 + n * (double)v * v * v * 2 + naux * n * v + naux * (double)v * v);
+  double state = 8.0 * (o2v2 * (2.0 * m + 16) + 3.0 * naux * n * n + (double)o * o * n * n * 2 +
+                        (double)o * o * n * v * 3);
+  return (size_t)(mol + state);
+}
+
+int64_t ascc_launch_count(const ascc_ctx* ctx) {
+  return ctx ? launch_total() - ctx->launches0 : 0;
+}
+
+void ascc_destroy(ascc_ctx* ctx) { delete ctx; }
+
+const char* ascc_status_string(ascc_status s) {
+  switch (s) {
+    case ASCC_OK: return "ok";
+    case ASCC_ERR_INVALID: return "invalid argument";
+    case ASCC_ERR_OOM: return "out of device memory";
+    case ASCC_ERR_CUDA: return "CUDA error";
+    case ASCC_ERR_NOT_CONVERGED: return "not converged";
+    case ASCC_ERR_DIVERGED: return "diverged";
+    case ASCC_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* ascc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,619 @@
+// Residual engine: einsum planner, bare integrals, and the ASCC/PLASCC
+// residual and Jacobi+DIIS iteration on one GPU (FP64 path).
+//
+// Formulation (arXiv 2501.10515, Sec. II.A): the working equations are the
+// ground-state CC equations over Hbar = exp(S^+) H exp(-S^+).  Both S^+ and
+// T1 act as one-body orbital transforms, so per iteration the engine forms
+//     B-hat^P = L B^P R,   L = (1 - t1)(1 + x),  R = (1 - x)(1 + t1),
+// (x[h][p] = 1/sqrt2, Eq. 1CSF-S) and evaluates the closed-shell doubles-only
+// CC equations of that non-Hermitian two-body Hamiltonian.  All blocks except
+// the particle-particle ladder come from B-hat by density fitting; the
+// ladder uses the bare (xc|bd) integrals, built once per molecule, with the
+// L and R dressings applied to the output and to the amplitudes.
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "engine.h"
+#include "kernels.h"
+
+namespace ascc {
+
+namespace {
+std::vector<int64_t> row_major_strides(const std::vector<int64_t>& shape) {
+  std::vector<int64_t> st(shape.size());
+  int64_t acc = 1;
+  for (int d = (int)shape.size() - 1; d >= 0; --d) {
+    st[d] = acc;
+    acc *= shape[d];
+  }
+  return st;
+}
+
+struct Spec {
+  std::string a, b, c;
+};
+
+Spec parse(const char* spec, bool two) {
+  std::string s(spec);
+  Spec r;
+  auto arrow = s.find("->");
+  ASCC_REQUIRE(arrow != std::string::npos, "einsum: missing ->");
+  r.c = s.substr(arrow + 2);
+  std::string lhs = s.substr(0, arrow);
+  if (two) {
+    auto comma = lhs.find(',');
+    ASCC_REQUIRE(comma != std::string::npos, "einsum: two operands expected");
+    r.a = lhs.substr(0, comma);
+    r.b = lhs.substr(comma + 1);
+  } else {
+    r.a = lhs;
+  }
+  return r;
+}
+}  // namespace
+
+void box_copy(cudaStream_t s, double* out, std::vector<int64_t> ostride, const double* in,
+              std::vector<int64_t> istride, std::vector<int64_t> shape, double alpha,
+              double beta) {
+  k::strided_copy(s, out, ostride.data(), in, istride.data(), (int)shape.size(), shape.data(),
+                  alpha, beta);
+}
+
+void Einsum::perm(const char* spec, double alpha, const T& A, double beta, const T& C) const {
+  Spec sp = parse(spec, false);
+  ASCC_REQUIRE((int)sp.a.size() == A.nd() && (int)sp.c.size() == C.nd(), "perm: rank");
+  auto ast = row_major_strides(A.shape);
+  std::vector<int64_t> istride, shape;
+  for (char ch : sp.c) {
+    auto pos = sp.a.find(ch);
+    ASCC_REQUIRE(pos != std::string::npos, "perm: label");
+    istride.push_back(ast[pos]);
+    shape.push_back(A.shape[pos]);
+  }
+  for (int d = 0; d < C.nd(); ++d) ASCC_REQUIRE(C.shape[d] == shape[d], "perm: shape");
+  box_copy(s_, C.p, row_major_strides(C.shape), A.p, istride, shape, alpha, beta);
+}
+
+void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, double beta,
+                        const T& C) const {
+  Spec sp = parse(spec, true);
+  ASCC_REQUIRE((int)sp.a.size() == A.nd() && (int)sp.b.size() == B.nd() &&
+                   (int)sp.c.size() == C.nd(),
+               std::string("einsum rank mismatch: ") + spec);
+  std::map<char, int64_t> size;
+  for (int d = 0; d < A.nd(); ++d) size[sp.a[d]] = A.shape[d];
+  for (int d = 0; d < B.nd(); ++d) {
+    auto it = size.find(sp.b[d]);
+    ASCC_REQUIRE(it == size.end() || it->second == B.shape[d], std::string("einsum size: ") + spec);
+    size[sp.b[d]] = B.shape[d];
+  }
+  for (int d = 0; d < C.nd(); ++d)
+    ASCC_REQUIRE(size.count(sp.c[d]) && size[sp.c[d]] == C.shape[d],
+                 std::string("einsum out: ") + spec);
+  auto in = [](const std::string& s, char c) { return s.find(c) != std::string::npos; };
+  std::string bat, Ml, Nl, Kl;
+  for (char ch : sp.c) {
+    if (in(sp.a, ch) && in(sp.b, ch)) bat += ch;
+    else if (in(sp.a, ch)) Ml += ch;
+    else Nl += ch;
+  }
+  for (char ch : sp.a) {
+    if (in(sp.b, ch) && !in(sp.c, ch)) Kl += ch;
+    ASCC_REQUIRE(in(sp.b, ch) || in(sp.c, ch), std::string("einsum: lone label in ") + spec);
+  }
+  for (char ch : sp.b)
+    ASCC_REQUIRE(in(sp.a, ch) || in(sp.c, ch), std::string("einsum: lone label in ") + spec);
+  auto prod = [&](const std::string& l) {
+    int64_t p = 1;
+    for (char ch : l) p *= size[ch];
+    return p;
+  };
+  const int64_t nb = prod(bat), Ms = prod(Ml), Ns = prod(Nl), Ks = prod(Kl);
+  auto shape_of = [&](const std::string& l) {
+    std::vector<int64_t> sh;
+    for (char ch : l) sh.push_back(size[ch]);
+    return sh;
+  };
+
+  // operand A in (bat, M, K) or (bat, K, M)
+  bool ta = false;
+  const double* Ap = A.p;
+  OT Atmp;
+  if (sp.a == bat + Ml + Kl) {
+    ta = false;
+  } else if (sp.a == bat + Kl + Ml) {
+    ta = true;
+  } else {
+    std::string want = bat + Ml + Kl;
+    Atmp.make(shape_of(want), s_);
+    perm((sp.a + "->" + want).c_str(), 1.0, A, 0.0, Atmp.t);
+    Ap = Atmp.p();
+  }
+  bool tb = false;
+  const double* Bp = B.p;
+  OT Btmp;
+  if (sp.b == bat + Kl + Nl) {
+    tb = false;
+  } else if (sp.b == bat + Nl + Kl) {
+    tb = true;
+  } else {
+    std::string want = bat + Kl + Nl;
+    Btmp.make(shape_of(want), s_);
+    perm((sp.b + "->" + want).c_str(), 1.0, B, 0.0, Btmp.t);
+    Bp = Btmp.p();
+  }
+  const int64_t lda = ta ? Ms : Ks, ldb = tb ? Ks : Ns;
+  const std::string cl = bat + Ml + Nl;
+  if (sp.c == cl) {
+    k::gemm_f64(s_, ta, tb, Ms, Ns, Ks, alpha, Ap, lda, Ms * Ks, Bp, ldb, Ks * Ns, beta, C.p, Ns,
+                Ms * Ns, nb);
+  } else {
+    OT Ct(shape_of(cl), s_);
+    k::gemm_f64(s_, ta, tb, Ms, Ns, Ks, 1.0, Ap, lda, Ms * Ks, Bp, ldb, Ks * Ns, 0.0, Ct.p(), Ns,
+                Ms * Ns, nb);
+    perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
+  }
+}
+
+// ---------------------------------------------------------------- Molecule
+Molecule::Molecule(int o_, int v_, int naux_, const double* eps_h, const double* B_src,
+                   bool on_device, cudaStream_t s)
+    : o(o_), v(v_), n(o_ + v_), naux(naux_), stream(s) {
+  eps_host.assign(eps_h, eps_h + n);
+  eps.make({n}, s);
+  ASCC_CUDA(cudaMemcpyAsync(eps.p(), eps_h, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  B.make({naux, n, n}, s);
+  ASCC_CUDA(cudaMemcpyAsync(B.p(), B_src, sizeof(double) * (size_t)naux * n * n,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  Einsum es(s);
+  // core Hamiltonian: h = diag(eps) - sum_i [2 (pq|ii) - (pi|iq)]
+  OT d({naux}, s), J({n, n}, s), K({n, n}, s), Bno({naux, n, o}, s), Bon({naux, o, n}, s);
+  k::diag_sum(s, d.p(), B.p(), naux, n, o);
+  es("Ppq,P->pq", 1.0, B.t, d.t, 0.0, J.t);
+  box_copy(s, Bno.p(), {(int64_t)n * o, o, 1}, B.p(), {(int64_t)n * n, n, 1}, {naux, n, o});
+  box_copy(s, Bon.p(), {(int64_t)o * n, n, 1}, B.p(), {(int64_t)n * n, n, 1}, {naux, o, n});
+  es("Ppk,Pkq->pq", 1.0, Bno.t, Bon.t, 0.0, K.t);
+  hcore.make({n, n}, s);
+  k::fill(s, hcore.p(), 0.0, (int64_t)n * n);
+  box_copy(s, hcore.p(), {n + 1}, eps.p(), {1}, {n});  // diagonal
+  k::axpby(s, hcore.p(), J.p(), -2.0, 1.0, (int64_t)n * n);
+  k::axpby(s, hcore.p(), K.p(), 1.0, 1.0, (int64_t)n * n);
+  // bare blocks for the ladder
+  Bvv.make({naux, v, v}, s);
+  box_copy(s, Bvv.p(), {(int64_t)v * v, v, 1}, B.p() + (int64_t)o * n + o, {(int64_t)n * n, n, 1},
+           {naux, v, v});
+  Bnv.make({naux, n, v}, s);
+  box_copy(s, Bnv.p(), {(int64_t)n * v, v, 1}, B.p() + o, {(int64_t)n * n, n, 1}, {naux, n, v});
+  // Gext[x][b][c][d] = (xc|bd) = sum_P B[P][x][o+c] B[P][o+b][o+d]
+  Gext.make({n, v, v, v}, s);
+  es("Pxc,Pbd->xbcd", 1.0, Bnv.t, Bvv.t, 0.0, Gext.t);
+}
+
+size_t Molecule::bytes() const {
+  return eps.buf.bytes() + B.buf.bytes() + hcore.buf.bytes() + Bvv.buf.bytes() +
+         Bnv.buf.bytes() + Gext.buf.bytes();
+}
+
+// ---------------------------------------------------------------- State
+namespace {
+std::vector<int32_t> t3p_index(int o, int v, int h, int p) {
+  // alpha-beta-beta triples (i, j<k, a, b<c) with >= 3 primary spin orbitals
+  // (Sec. II.B.1), in lexicographic order of (i, j, k, a, b, c).
+  std::vector<int32_t> out;
+  if (h < 0) return out;
+  for (int i = 0; i < o; ++i)
+    for (int j = 0; j < o; ++j)
+      for (int kk = j + 1; kk < o; ++kk) {
+        const int occ = (i == h) + (j == h || kk == h);
+        if (occ == 0) continue;
+        for (int a = 0; a < v; ++a) {
+          const int have = occ + (a == p);
+          if (have < 2) continue;
+          for (int b = 0; b < v; ++b)
+            for (int c = b + 1; c < v; ++c) {
+              if (have >= 3 || b == p || c == p) {
+                const int32_t row[6] = {i, j, kk, a, b, c};
+                out.insert(out.end(), row, row + 6);
+              }
+            }
+        }
+      }
+  return out;
+}
+}  // namespace
+
+State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
+             const Options& opt, cudaStream_t s)
+    : mol_(std::move(mol)), opt_(opt), s_(s), es_(s) {
+  o_ = mol_->o; v_ = mol_->v; n_ = mol_->n; naux_ = mol_->naux;
+  hole_ = hole; particle_ = particle;
+  beta_ = beta == 0.0 ? 1.0 : beta;
+  xval_ = hole_ >= 0 ? 1.0 / std::sqrt(2.0) : 0.0;
+  lh_ = hole_ >= 0 ? hole_ : opt_.pl_hole;
+  lp_ = hole_ >= 0 ? particle_ : opt_.pl_particle;
+  if (lh_ < 0) opt_.linearize = 0;
+  ASCC_REQUIRE(opt_.precision == ASCC_FP64, "this build runs the FP64 path only");
+  ASCC_REQUIRE(opt_.diis_dim >= 1 && opt_.diis_dim <= 16, "diis_dim in 1..16");
+  if (opt_.triples && hole_ >= 0) {
+    t3idx_host_ = t3p_index(o_, v_, hole_, particle_);
+    ASCC_REQUIRE(n3() == 0, "the T3' slice is not available in this build");
+  }
+  nu_ = v_ + (hole_ >= 0 ? 1 : 0);
+  const int64_t N = namp();
+  t_.make({N}, s);
+  r_.make({N}, s);
+  hist_t_.make({opt_.diis_dim, N}, s);
+  hist_e_.make({opt_.diis_dim, N}, s);
+  scal_.make({64}, s);
+  work_.make({(int64_t)16 * 4 * 152 + 64}, s);
+  coef_.make({16}, s);
+  const int o = o_, v = v_, n = n_, P = naux_;
+  L_.make({n, n}, s); R_.make({n, n}, s);
+  tmpB_.make({P, n, n}, s); Bhat_.make({P, n, n}, s);
+  hhat_.make({n, n}, s); tmpnn_.make({n, n}, s); F_.make({n, n}, s);
+  dP_.make({P}, s); J_.make({n, n}, s); K_.make({n, n}, s);
+  Boo_.make({P, o, o}, s); Bov_.make({P, o, v}, s); Bvo_.make({P, v, o}, s);
+  Bvv_.make({P, v, v}, s); Bno_.make({P, n, o}, s); Bon_.make({P, o, n}, s);
+  goooo_.make({o, o, o, o}, s); gooov_.make({o, o, o, v}, s); goovv_.make({o, o, v, v}, s);
+  govov_.make({o, v, o, v}, s); gvovo_.make({v, o, v, o}, s); gvoov_.make({v, o, o, v}, s);
+  gvvoo_.make({v, v, o, o}, s); Lvoov_.make({v, o, o, v}, s); Lovov_.make({o, v, o, v}, s);
+  u_.make({o, o, v, v}, s); Z_.make({o, o, v, v}, s);
+  WC_.make({o, o, v, v}, s); WD_.make({v, o, o, v}, s); Wq_.make({o, o, o, o}, s);
+  Fvv_.make({v, v}, s); Foo_.make({o, o}, s); X_.make({P, o, v}, s);
+  Y_.make({o, o, n, v}, s); Yfull_.make({o, o, n, n}, s); Z1_.make({o, o, n, v}, s);
+  tt_.make({o, o, nu_, nu_}, s); Yoo_.make({o, o, o, o}, s);
+  if (opt_.linearize) {
+    m_.make({o, o, v, v}, s);
+    um_.make({o, o, v, v}, s);
+  }
+  build_state_integrals();
+}
+
+State::~State() = default;
+
+void State::build_state_integrals() {
+  const int o = o_, v = v_, n = n_, P = naux_, nu = nu_;
+  Molecule& M = *mol_;
+  // Goo[k][l][u][w] = (k u | l w), u, w over the virtuals plus the hole slot
+  OT Bou({P, o, nu}, s_);
+  box_copy(s_, Bou.p(), {(int64_t)o * nu, nu, 1}, M.B.p() + o, {(int64_t)n * n, n, 1}, {P, o, v});
+  if (hole_ >= 0)
+    box_copy(s_, Bou.p() + v, {(int64_t)o * nu, nu}, M.B.p() + hole_, {(int64_t)n * n, n},
+             {P, o});
+  GooP.make({o, o, nu, nu}, s_);
+  es_("Pku,Plw->kluw", 1.0, Bou.t, Bou.t, 0.0, GooP.t);
+  if (hole_ < 0) return;
+  const int h = hole_;
+  // Bh[P][x] = B[P][x][h]; Bvh[P][b] = B[P][o+b][h]
+  OT Bh({P, n}, s_), Bvh({P, v}, s_);
+  box_copy(s_, Bh.p(), {n, 1}, M.B.p() + h, {(int64_t)n * n, n}, {P, n});
+  box_copy(s_, Bvh.p(), {v, 1}, M.B.p() + (int64_t)o * n + h, {(int64_t)n * n, n}, {P, v});
+  Gh1.make({n, v, v}, s_);  // (x h | b d)
+  es_("Px,Pbd->xbd", 1.0, Bh.t, M.Bvv.t, 0.0, Gh1.t);
+  Gh2.make({n, v, v}, s_);  // (x c | b h) at [x][b][c]
+  es_("Pxc,Pb->xbc", 1.0, M.Bnv.t, Bvh.t, 0.0, Gh2.t);
+  Gh3.make({n, v}, s_);     // (x h | b h)
+  es_("Px,Pb->xb", 1.0, Bh.t, Bvh.t, 0.0, Gh3.t);
+}
+
+void State::initial_guess(std::vector<double>& t) const {
+  // Eq. TP-guess: t1[h][p] = beta/sqrt2, t2[h][h][p][p] = -beta^2/2; else 0.
+  t.assign((size_t)namp(), 0.0);
+  if (hole_ < 0) return;
+  t[(size_t)hole_ * v_ + particle_] = beta_ / std::sqrt(2.0);
+  const int64_t i2 = (((int64_t)hole_ * o_ + hole_) * v_ + particle_) * v_ + particle_;
+  t[(size_t)(n1() + i2)] = -0.5 * beta_ * beta_;
+}
+
+// B-hat = L B R and h-hat = L h R with the S^+ and T1 orbital transforms.
+void State::dress(const double* t1) {
+  const int n = n_, P = naux_;
+  Molecule& M = *mol_;
+  k::build_LR(s_, L_.p(), R_.p(), t1, o_, v_, hole_, particle_, xval_);
+  const int64_t nn = (int64_t)n * n;
+  k::gemm_f64(s_, false, false, n, n, n, 1.0, L_.p(), n, 0, M.B.p(), n, nn, 0.0, tmpB_.p(), n, nn,
+              P);
+  k::gemm_f64(s_, false, false, n, n, n, 1.0, tmpB_.p(), n, nn, R_.p(), n, 0, 0.0, Bhat_.p(), n,
+              nn, P);
+  k::gemm_f64(s_, false, false, n, n, n, 1.0, L_.p(), n, 0, M.hcore.p(), n, 0, 0.0, tmpnn_.p(),
+              n, 0, 1);
+  k::gemm_f64(s_, false, false, n, n, n, 1.0, tmpnn_.p(), n, 0, R_.p(), n, 0, 0.0, hhat_.p(), n,
+              0, 1);
+  const int o = o_, v = v_;
+  const std::vector<int64_t> bs = {nn, n, 1};
+  box_copy(s_, Boo_.p(), {(int64_t)o * o, o, 1}, Bhat_.p(), bs, {P, o, o});
+  box_copy(s_, Bov_.p(), {(int64_t)o * v, v, 1}, Bhat_.p() + o, bs, {P, o, v});
+  box_copy(s_, Bvo_.p(), {(int64_t)v * o, o, 1}, Bhat_.p() + (int64_t)o * n, bs, {P, v, o});
+  box_copy(s_, Bvv_.p(), {(int64_t)v * v, v, 1}, Bhat_.p() + (int64_t)o * n + o, bs, {P, v, v});
+  box_copy(s_, Bno_.p(), {(int64_t)n * o, o, 1}, Bhat_.p(), bs, {P, n, o});
+  box_copy(s_, Bon_.p(), {(int64_t)o * n, n, 1}, Bhat_.p(), bs, {P, o, n});
+  // Fock matrix of H-hat: F = h + 2 J - K
+  k::diag_sum(s_, dP_.p(), Bhat_.p(), P, n, o);
+  es_("Ppq,P->pq", 1.0, Bhat_.t, dP_.t, 0.0, J_.t);
+  es_("Ppk,Pkq->pq", 1.0, Bno_.t, Bon_.t, 0.0, K_.t);
+  k::axpby(s_, F_.p(), hhat_.p(), 1.0, 0.0, nn);
+  k::axpby(s_, F_.p(), J_.p(), 2.0, 1.0, nn);
+  k::axpby(s_, F_.p(), K_.p(), -1.0, 1.0, nn);
+  // integral blocks (pq|rs)-hat = sum_P B-hat[P][p][q] B-hat[P][r][s]
+  es_("Pij,Pkl->ijkl", 1.0, Boo_.t, Boo_.t, 0.0, goooo_.t);
+  es_("Pij,Pka->ijka", 1.0, Boo_.t, Bov_.t, 0.0, gooov_.t);
+  es_("Pij,Pab->ijab", 1.0, Boo_.t, Bvv_.t, 0.0, goovv_.t);
+  es_("Pia,Pjb->iajb", 1.0, Bov_.t, Bov_.t, 0.0, govov_.t);
+  es_("Pai,Pbj->aibj", 1.0, Bvo_.t, Bvo_.t, 0.0, gvovo_.t);
+  es_("Pai,Pjb->aijb", 1.0, Bvo_.t, Bov_.t, 0.0, gvoov_.t);
+  es_("Pab,Pij->abij", 1.0, Bvv_.t, Boo_.t, 0.0, gvvoo_.t);
+  // L_aikc = 2 g_aikc - g_acki ; L_ldkc = 2 g_ldkc - g_lckd
+  k::axpby(s_, Lvoov_.p(), gvoov_.p(), 2.0, 0.0, gvoov_.t.size());
+  es_.perm("acki->aikc", -1.0, gvvoo_.t, 1.0, Lvoov_.t);
+  k::axpby(s_, Lovov_.p(), govov_.p(), 2.0, 0.0, govov_.t.size());
+  es_.perm("lckd->ldkc", -1.0, govov_.t, 1.0, Lovov_.t);
+}
+
+// Particle-particle ladder sum_cd g-hat_acbd t_ij^cd with g-hat dressed by L
+// (output indices a, b) and R (summed indices c, d): the bare (xc|bd) carry
+// the dense O(o^2 v^4) part, the hole-slot terms of R (c or d = p, Eq.
+// 1CSF-S) and the occupied rows of L are O(N^5) corrections.
+void State::ladder(const T& t2, const T& r2) {
+  const int o = o_, v = v_, n = n_, nu = nu_;
+  Molecule& M = *mol_;
+  const int64_t vv = (int64_t)v * v;
+  // Y[i][j][x][b] = sum_cd t[i][j][c][d] (xc|bd)
+  es_("ijcd,xbcd->ijxb", 1.0, t2, M.Gext.t, 0.0, Y_.t);
+  // R-dressed amplitudes tt[i][j][u][w], u, w over the virtuals (+ hole slot)
+  const int64_t s4[4] = {(int64_t)o * vv, vv, v, 1};
+  box_copy(s_, tt_.p(), {(int64_t)o * nu * nu, (int64_t)nu * nu, nu, 1}, t2.p,
+           {s4[0], s4[1], s4[2], s4[3]}, {o, o, v, v});
+  if (hole_ >= 0) {
+    const int p = particle_;
+    const double x = xval_;
+    OT tpd({o, o, v}, s_), tcp({o, o, v}, s_), tpp({o, o}, s_);
+    box_copy(s_, tpd.p(), {(int64_t)o * v, v, 1}, t2.p + (int64_t)p * v, {s4[0], s4[1], 1},
+             {o, o, v});
+    box_copy(s_, tcp.p(), {(int64_t)o * v, v, 1}, t2.p + p, {s4[0], s4[1], v}, {o, o, v});
+    box_copy(s_, tpp.p(), {o, 1}, t2.p + (int64_t)p * v + p, {s4[0], s4[1]}, {o, o});
+    es_("ijd,xbd->ijxb", -x, tpd.t, Gh1.t, 1.0, Y_.t);
+    es_("ijc,xbc->ijxb", -x, tcp.t, Gh2.t, 1.0, Y_.t);
+    es_("ij,xb->ijxb", x * x, tpp.t, Gh3.t, 1.0, Y_.t);
+    const int64_t so = (int64_t)o * nu * nu;
+    box_copy(s_, tt_.p() + (int64_t)v * nu, {so, (int64_t)nu * nu, 1}, tpd.p(),
+             {(int64_t)o * v, v, 1}, {o, o, v}, -x);
+    box_copy(s_, tt_.p() + v, {so, (int64_t)nu * nu, nu}, tcp.p(), {(int64_t)o * v, v, 1},
+             {o, o, v}, -x);
+    box_copy(s_, tt_.p() + (int64_t)v * nu + v, {so, (int64_t)nu * nu}, tpp.p(), {o, 1}, {o, o},
+             x * x);
+  }
+  // Y_oo[i][j][k][l] = sum_uw tt[i][j][u][w] (k u | l w)
+  es_("ijuw,kluw->ijkl", 1.0, tt_.t, GooP.t, 0.0, Yoo_.t);
+  // Yfull[i][j][t][v'] over all orbitals t, v'
+  const int64_t fs[4] = {(int64_t)o * n * n, (int64_t)n * n, n, 1};
+  box_copy(s_, Yfull_.p() + o, {fs[0], fs[1], fs[2], 1}, Y_.p(),
+           {(int64_t)o * n * v, (int64_t)n * v, v, 1}, {o, o, n, v});
+  // Yfull[i][j][o+a][l] = Y[j][i][l][a]
+  box_copy(s_, Yfull_.p() + (int64_t)o * n, {fs[0], fs[1], n, 1}, Y_.p(),
+           {(int64_t)n * v, (int64_t)o * n * v, 1, v}, {o, o, v, o});
+  box_copy(s_, Yfull_.p(), {fs[0], fs[1], n, 1}, Yoo_.p(),
+           {(int64_t)o * o * o, (int64_t)o * o, o, 1}, {o, o, o, o});
+  // r2[i][j][a][b] += sum_{t,v'} L[o+a][t] L[o+b][v'] Yfull[i][j][t][v']
+  const double* LV = L_.p() + (int64_t)o * n;
+  k::gemm_f64(s_, false, true, (int64_t)o * o * n, v, n, 1.0, Yfull_.p(), n, 0, LV, n, 0, 0.0,
+              Z1_.p(), v, 0, 1);
+  k::gemm_f64(s_, false, false, v, v, n, 1.0, LV, n, 0, Z1_.p(), v, (int64_t)n * v, 1.0, r2.p, v,
+              vv, (int64_t)o * o);
+}
+
+// Terms bilinear in T2 with intermediates built from (t, u = 2t - t^T) and
+// contracted with t; added to Z (permuted part) and r2 with factor sign.
+void State::quad_terms(const T& t, const T& u, const T& Z, const T& r2, double sign) {
+  // hole-hole ladder, quadratic part: sum_kl t_kl^ab sum_cd t_ij^cd g_kcld
+  es_("ijcd,kcld->klij", 1.0, t, govov_.t, 0.0, Wq_.t);
+  es_("klab,klij->ijab", sign, t, Wq_.t, 1.0, r2);
+  // crossed ring: X_kiac = -1/2 sum_ld t_li^ad g_kdlc
+  es_("liad,kdlc->kiac", -0.5, t, govov_.t, 0.0, WC_.t);
+  es_("kjbc,kiac->ijab", -0.5 * sign, t, WC_.t, 1.0, Z);
+  es_("kibc,kjac->ijab", -1.0 * sign, t, WC_.t, 1.0, Z);
+  // ring: Y_aikc = 1/2 sum_ld u_il^ad L_ldkc
+  es_("ilad,ldkc->aikc", 0.5, u, Lovov_.t, 0.0, WD_.t);
+  es_("jkbc,aikc->ijab", 0.5 * sign, u, WD_.t, 1.0, Z);
+  // Fock-like: F'_bc = -sum u_kl^bd g_ldkc, F'_kj = sum u_lj^cd g_kdlc
+  es_("klbd,ldkc->bc", -1.0, u, govov_.t, 0.0, Fvv_.t);
+  es_("ljcd,kdlc->kj", 1.0, u, govov_.t, 0.0, Foo_.t);
+  es_("ijac,bc->ijab", sign, t, Fvv_.t, 1.0, Z);
+  es_("ikab,kj->ijab", -sign, t, Foo_.t, 1.0, Z);
+}
+
+void State::residual(const double* tv, double* rv, double* energy) {
+  const int o = o_, v = v_;
+  const int64_t n1 = this->n1(), n2 = this->n2();
+  T t1((double*)tv, {o, v}), t2((double*)tv + n1, {o, o, v, v});
+  T r1(rv, {o, v}), r2(rv + n1, {o, o, v, v});
+  dress(t1.p);
+  k::tilde(s_, u_.p(), t2.p, o, v);
+  const int n = n_;
+  // ---- singles (alpha projection)
+  box_copy(s_, r1.p, {v, 1}, F_.p() + (int64_t)o * n, {1, n}, {o, v});  // F_ai
+  es_("Pkc,kicd->Pid", 1.0, Bov_.t, u_.t, 0.0, X_.t);
+  es_("Pad,Pid->ia", 1.0, Bvv_.t, X_.t, 1.0, r1);                         // sum u g_adkc
+  es_("klac,kilc->ia", -1.0, u_.t, gooov_.t, 1.0, r1);
+  {
+    OT Fov({o, v}, s_);
+    box_copy(s_, Fov.p(), {v, 1}, F_.p() + o, {n, 1}, {o, v});
+    es_("ikac,kc->ia", 1.0, u_.t, Fov.t, 1.0, r1);
+  }
+  // ---- doubles (alpha-beta projection)
+  es_.perm("aibj->ijab", 1.0, gvovo_.t, 0.0, r2);
+  ladder(t2, r2);
+  es_("klab,kilj->ijab", 1.0, t2, goooo_.t, 1.0, r2);
+  k::fill(s_, Z_.p(), 0.0, n2);
+  es_("kjbc,kiac->ijab", -0.5, t2, goovv_.t, 1.0, Z_.t);
+  es_("kibc,kjac->ijab", -1.0, t2, goovv_.t, 1.0, Z_.t);
+  es_("jkbc,aikc->ijab", 0.5, u_.t, Lvoov_.t, 1.0, Z_.t);
+  {
+    OT Fvv({v, v}, s_), Foo({o, o}, s_);
+    box_copy(s_, Fvv.p(), {v, 1}, F_.p() + (int64_t)o * n + o, {n, 1}, {v, v});
+    box_copy(s_, Foo.p(), {o, 1}, F_.p(), {n, 1}, {o, o});
+    es_("ijac,bc->ijab", 1.0, t2, Fvv.t, 1.0, Z_.t);
+    es_("ikab,kj->ijab", -1.0, t2, Foo.t, 1.0, Z_.t);
+  }
+  quad_terms(t2, u_.t, Z_.t, r2, 1.0);
+  if (opt_.linearize) {
+    // PLASCC (Sec. II.C): remove the terms bilinear in the mixed doubles
+    k::mixed_mask(s_, m_.p(), t2.p, o, v, lh_, lp_);
+    k::tilde(s_, um_.p(), m_.p(), o, v);
+    quad_terms(m_.t, um_.t, Z_.t, r2, -1.0);
+  }
+  es_.perm("ijab->jiba", 1.0, Z_.t, 1.0, r2);
+  k::axpby(s_, r2.p, Z_.p(), 1.0, 1.0, n2);
+  // ---- energy: <phi0|H-hat|phi0> + sum t_ij^ab L_iajb
+  k::reference_energy(s_, scal_.p() + 8, hhat_.p(), n, goooo_.p(), o);
+  {
+    OT Lp({o, o, v, v}, s_);
+    es_.perm("iajb->ijab", 1.0, Lovov_.t, 0.0, Lp.t);
+    k::dot_rows(s_, t2.p, Lp.p(), 0, 1, n2, scal_.p() + 9, work_.p());
+  }
+  k::axpby(s_, energy, scal_.p() + 8, 1.0, 0.0, 1);
+  k::axpby(s_, energy, scal_.p() + 9, 1.0, 1.0, 1);
+}
+
+double State::reference_energy() {
+  OT z({n1()}, s_);
+  k::fill(s_, z.p(), 0.0, n1());
+  dress(z.p());
+  k::reference_energy(s_, scal_.p() + 10, hhat_.p(), n_, goooo_.p(), o_);
+  double e = 0.0;
+  ASCC_CUDA(cudaMemcpyAsync(&e, scal_.p() + 10, sizeof(double), cudaMemcpyDeviceToHost, s_));
+  ASCC_CUDA(cudaStreamSynchronize(s_));
+  return e;
+}
+
+namespace {
+// DIIS coefficients: bordered system [[G/s + 1e-12 I, 1], [1, 0]] [c; l] = [0; 1]
+// with s = max diag G, Gaussian elimination with partial pivoting.
+bool bordered_solve(const std::vector<double>& G, int m, std::vector<double>& c) {
+  double scale = 0.0;
+  for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(G[i * m + i]));
+  if (!(scale > 0.0) || !std::isfinite(scale)) return false;
+  const int nn = m + 1;
+  std::vector<double> A((size_t)nn * nn, 0.0), b(nn, 0.0);
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) A[i * nn + j] = G[i * m + j] / scale + (i == j ? 1e-12 : 0.0);
+    A[i * nn + m] = 1.0;
+    A[m * nn + i] = 1.0;
+  }
+  b[m] = 1.0;
+  for (int col = 0; col < nn; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < nn; ++r)
+      if (std::fabs(A[r * nn + col]) > std::fabs(A[piv * nn + col])) piv = r;
+    if (std::fabs(A[piv * nn + col]) < 1e-300) return false;
+    if (piv != col) {
+      for (int j = 0; j < nn; ++j) std::swap(A[col * nn + j], A[piv * nn + j]);
+      std::swap(b[col], b[piv]);
+    }
+    for (int r = col + 1; r < nn; ++r) {
+      const double f = A[r * nn + col] / A[col * nn + col];
+      for (int j = col; j < nn; ++j) A[r * nn + j] -= f * A[col * nn + j];
+      b[r] -= f * b[col];
+    }
+  }
+  std::vector<double> x(nn, 0.0);
+  for (int r = nn - 1; r >= 0; --r) {
+    double acc = b[r];
+    for (int j = r + 1; j < nn; ++j) acc -= A[r * nn + j] * x[j];
+    x[r] = acc / A[r * nn + r];
+  }
+  for (double xi : x)
+    if (!std::isfinite(xi)) return false;
+  c.assign(x.begin(), x.begin() + m);
+  return true;
+}
+}  // namespace
+
+ascc_status State::solve(ascc_result* res) {
+  const int64_t N = namp();
+  std::vector<double> guess;
+  initial_guess(guess);
+  ASCC_CUDA(cudaMemcpyAsync(t_.p(), guess.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s_));
+  const int m = opt_.diis_dim;
+  k::fill(s_, hist_t_.p(), 0.0, (int64_t)m * N);
+  k::fill(s_, hist_e_.p(), 0.0, (int64_t)m * N);
+  std::vector<int> slots;          // history slots, oldest first
+  std::vector<double> G(m * m, 0.0);  // Gram matrix by slot
+  int next_slot = 0;
+  double e_prev = 0.0, e = 0.0, rmax = 0.0;
+  bool have_prev = false;
+  ascc_status st = ASCC_ERR_NOT_CONVERGED;
+  int it = 0;
+  for (it = 0; it <= opt_.max_iter; ++it) {
+    residual(t_.p(), r_.p(), scal_.p());
+    k::maxabs(s_, r_.p(), N, scal_.p() + 1, work_.p());
+    double h2[2];
+    ASCC_CUDA(cudaMemcpyAsync(h2, scal_.p(), 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+    ASCC_CUDA(cudaStreamSynchronize(s_));
+    e = h2[0];
+    rmax = h2[1];
+    if (!std::isfinite(e) || !std::isfinite(rmax)) {
+      st = ASCC_ERR_DIVERGED;
+      break;
+    }
+    if (have_prev && rmax <= opt_.r_tol && std::fabs(e - e_prev) <= opt_.e_tol) {
+      st = ASCC_OK;
+      break;
+    }
+    if (it == opt_.max_iter) break;
+    e_prev = e;
+    have_prev = true;
+    // Jacobi step into a history slot
+    int slot;
+    if ((int)slots.size() < m) {
+      slot = next_slot++;
+    } else {
+      slot = slots.front();
+      slots.erase(slots.begin());
+    }
+    slots.push_back(slot);
+    double* tn = hist_t_.p() + (int64_t)slot * N;
+    double* en = hist_e_.p() + (int64_t)slot * N;
+    k::jacobi(s_, tn, en, t_.p(), r_.p(), mol_->eps.p(), o_, v_,
+              n3() ? reinterpret_cast<const int32_t*>(t3idx_.p()) : nullptr, n3());
+    // Gram row of the new error against the whole history (by slot)
+    k::dot_rows(s_, en, hist_e_.p(), N, m, N, scal_.p() + 16, work_.p());
+    std::vector<double> row(m);
+    ASCC_CUDA(cudaMemcpyAsync(row.data(), scal_.p() + 16, m * sizeof(double),
+                              cudaMemcpyDeviceToHost, s_));
+    ASCC_CUDA(cudaStreamSynchronize(s_));
+    for (int q : slots) {
+      G[slot * m + q] = row[q];
+      G[q * m + slot] = row[q];
+    }
+    bool extrapolated = false;
+    if ((int)slots.size() >= opt_.diis_start) {
+      const int cnt = (int)slots.size();
+      std::vector<double> Gs(cnt * cnt), c;
+      for (int a = 0; a < cnt; ++a)
+        for (int b = 0; b < cnt; ++b) Gs[a * cnt + b] = G[slots[a] * m + slots[b]];
+      if (bordered_solve(Gs, cnt, c)) {
+        std::vector<double> cs(m, 0.0);
+        for (int a = 0; a < cnt; ++a) cs[slots[a]] = c[a];
+        ASCC_CUDA(cudaMemcpyAsync(coef_.p(), cs.data(), m * sizeof(double),
+                                  cudaMemcpyHostToDevice, s_));
+        k::lincomb(s_, t_.p(), hist_t_.p(), N, coef_.p(), m, N);
+        extrapolated = true;
+      } else {
+        slots.assign(1, slot);
+      }
+    }
+    if (!extrapolated) k::axpby(s_, t_.p(), tn, 1.0, 0.0, N);
+  }
+  if (res) {
+    res->energy = e;
+    res->max_resid = rmax;
+    res->iterations = it;
+    res->status = st;
+    res->iterations_low = 0;
+    res->e_ref = 0.0;
+  }
+  return st;
+}
+
+}  // namespace ascc

@@ -1,0 +1,113 @@
+// Residual engine of libascc: the einsum planner, the per-molecule bare
+// integrals, the per-state amplitude iteration.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+namespace ascc {
+
+// Contracts two dense row-major tensors on the device: C = alpha A.B + beta C
+// with single-character index labels ("ijcd,acbd->ijab").  Labels shared by
+// A, B and C are batched, labels of A and C (B and C) form the GEMM rows
+// (columns), labels of A and B only are summed.  Operands are permuted into
+// GEMM order only when their layout is not already usable.
+class Einsum {
+ public:
+  explicit Einsum(cudaStream_t s) : s_(s) {}
+  void operator()(const char* spec, double alpha, const T& A, const T& B, double beta,
+                  const T& C) const;
+  // C = alpha * permute(A) + beta * C, spec "kilj->klij"
+  void perm(const char* spec, double alpha, const T& A, double beta, const T& C) const;
+
+ private:
+  cudaStream_t s_;
+};
+
+// Copies a strided box of `in` into `out` (both with explicit strides).
+void box_copy(cudaStream_t s, double* out, std::vector<int64_t> ostride, const double* in,
+              std::vector<int64_t> istride, std::vector<int64_t> shape, double alpha = 1.0,
+              double beta = 0.0);
+
+// Bare integrals of one molecule, shared by all of its states.
+struct Molecule {
+  int o = 0, v = 0, n = 0, naux = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<double> eps_host;
+  OT eps;    // [n]
+  OT B;      // [naux][n][n] bare DF factor
+  OT hcore;  // [n][n] core Hamiltonian with diag(eps) as Fock matrix
+  OT Bvv;    // [naux][v][v]
+  OT Bnv;    // [naux][n][v]
+  OT Gext;   // [n][v][v][v], Gext[x][b][c][d] = (xc|bd)
+  Molecule(int o, int v, int naux, const double* eps_h, const double* B_src, bool on_device,
+           cudaStream_t s);
+  size_t bytes() const;
+};
+
+struct Options {
+  int precision = ASCC_FP64;
+  int linearize = 1;
+  int triples = 0;
+  int pl_hole = -1, pl_particle = -1;
+  double r_tol = 1e-8, e_tol = 1e-10;
+  int max_iter = 200, diis_dim = 8, diis_start = 3;
+  int polish_iter = 50;
+  double polish_tol = 1e-6;
+};
+
+// One state (ground or one-CSF excited) of a molecule.
+class State {
+ public:
+  State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta, const Options& opt,
+        cudaStream_t s);
+  ~State();
+
+  int64_t n1() const { return (int64_t)o_ * v_; }
+  int64_t n2() const { return (int64_t)o_ * o_ * v_ * v_; }
+  int64_t n3() const { return (int64_t)t3idx_host_.size() / 6; }
+  int64_t namp() const { return n1() + n2() + n3(); }
+  const std::vector<int32_t>& t3_indices() const { return t3idx_host_; }
+
+  // Residual of packed device amplitudes t -> packed device residual r and
+  // device scalar energy.
+  void residual(const double* t, double* r, double* energy);
+  ascc_status solve(ascc_result* res);
+  void initial_guess(std::vector<double>& t) const;
+
+  double* amplitudes() { return t_.p(); }
+  cudaStream_t stream() const { return s_; }
+  std::shared_ptr<Molecule> molecule() const { return mol_; }
+  const Options& options() const { return opt_; }
+  double reference_energy();
+
+ private:
+  void build_state_integrals();
+  void dress(const double* t1);
+  void ladder(const T& t2, const T& r2);
+  void quad_terms(const T& t, const T& u, const T& Z, const T& r2, double sign);
+
+  std::shared_ptr<Molecule> mol_;
+  Options opt_;
+  cudaStream_t s_;
+  int o_, v_, n_, naux_;
+  int hole_, particle_;  // -1 for the ground state
+  int lh_, lp_;          // primary labels used by the partial linearisation
+  double beta_, xval_;
+  int nu_;               // v (+1 with the hole slot of an excited state)
+  Einsum es_;
+  std::vector<int32_t> t3idx_host_;
+  OT t3idx_;             // int32 [n3][6] stored in a double-sized buffer
+  // per-state constant integrals of the ladder corrections
+  OT Gh1, Gh2, Gh3, GooP;
+  // amplitudes, residual, DIIS
+  OT t_, r_, hist_t_, hist_e_, scal_, work_, coef_;
+  // per-iteration workspace
+  OT L_, R_, tmpB_, Bhat_, hhat_, tmpnn_, F_, dP_, J_, K_, Boo_, Bov_, Bvo_, Bvv_, Bno_, Bon_;
+  OT goooo_, gooov_, goovv_, govov_, gvovo_, gvoov_, gvvoo_, Lvoov_, Lovov_;
+  OT u_, m_, um_, Z_, WC_, WD_, Wq_, Fvv_, Foo_, X_, Y_, Yfull_, Z1_, tt_, Yoo_;
+};
+
+}  // namespace ascc

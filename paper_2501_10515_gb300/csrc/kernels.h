@@ -1,0 +1,61 @@
+// Launchers of the FP64 device kernels used by the residual engine.
+#pragma once
+
+#include "common.h"
+
+namespace ascc {
+namespace k {
+
+// C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b], row-major, batch strides in
+// elements (stride 0 broadcasts an operand).  op(A) is M x K, op(B) is K x N.
+void gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
+              double alpha, const double* A, int64_t lda, int64_t sA,
+              const double* B, int64_t ldb, int64_t sB, double beta, double* C,
+              int64_t ldc, int64_t sC, int64_t batch);
+
+// out[strided] = alpha * in[strided] + beta * out over an nd-dimensional
+// index box `shape` (strides in elements, one per dimension).
+void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride,
+                  const double* in, const int64_t* in_stride, int nd,
+                  const int64_t* shape, double alpha, double beta);
+
+void fill(cudaStream_t s, double* x, double v, int64_t n);
+void axpby(cudaStream_t s, double* y, const double* x, double a, double b, int64_t n);  // y = a x + b y
+
+// Deterministic reductions; results land in device memory.
+void dot_rows(cudaStream_t s, const double* x, const double* Y, int64_t ldy,
+              int rows, int64_t n, double* out, double* work);  // out[r] = x . Y[r]
+void maxabs(cudaStream_t s, const double* x, int64_t n, double* out, double* work);
+
+// y = sum_k c[k] * X[k]  (c in device memory)
+void lincomb(cudaStream_t s, double* y, const double* X, int64_t ldx,
+             const double* c, int m, int64_t n);
+
+// Dressing matrices L = (1 - t1)(1 + x), R = (1 - x)(1 + t1) as n x n row-major
+// (x[h][o+p] = xval; hole < 0 means x = 0).
+void build_LR(cudaStream_t s, double* L, double* R, const double* t1, int o,
+              int v, int hole, int particle, double xval);
+
+// u = 2 t - t^(i<->j) for t[o][o][v][v]
+void tilde(cudaStream_t s, double* u, const double* t, int o, int v);
+
+// m = t where 1 <= #primary spatial indices <= 3, else 0 (Eq. pnm split).
+void mixed_mask(cudaStream_t s, double* m, const double* t, int o, int v,
+                int hole, int particle);
+
+// Jacobi step (Sec. III.B): tn = t + r / D with bare-eps denominators and
+// e = tn - t, over the packed vector [t1 | t2 | t3'].
+void jacobi(cudaStream_t s, double* tn, double* e, const double* t,
+            const double* r, const double* eps, int o, int v,
+            const int32_t* t3idx, int64_t n3);
+
+// d[P] = sum_k B[P][k][k]
+void diag_sum(cudaStream_t s, double* d, const double* B, int naux, int n, int o);
+
+// out[0] = 2 sum_i h[i][i] + sum_ij (2 g[i][i][j][j] - g[i][j][j][i]) for
+// g = oooo block (o^4) and h n x n.
+void reference_energy(cudaStream_t s, double* out, const double* h, int n,
+                      const double* goooo, int o);
+
+}  // namespace k
+}  // namespace ascc

@@ -1,0 +1,453 @@
+// FP64 kernels of the residual engine: a tiled DFMA GEMM, strided copies,
+// reductions and the elementwise steps of the amplitude update.
+#include <atomic>
+
+#include "kernels.h"
+
+namespace ascc {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int64_t n) { g_launches += n; }
+int64_t launch_total() { return g_launches.load(); }
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    throw Error(ASCC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace k {
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
+
+// 64x64 output tile per block, 4x4 per thread (strided), K in steps of 16.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(NT)
+gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                const double* __restrict__ A, int64_t lda, int64_t sA,
+                const double* __restrict__ B, int64_t ldb, int64_t sB,
+                double beta, double* __restrict__ C, int64_t ldc, int64_t sC) {
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+  const int64_t bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int64_t m0 = (int64_t)blockIdx.y * TM, n0 = (int64_t)blockIdx.x * TN;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int64_t k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int idx = tid + NT * r;
+      int mm, kk;
+      if (!TA) { mm = idx / TK; kk = idx % TK; } else { kk = idx / TM; mm = idx % TM; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      double val = 0.0;
+      if (gm < M && gk < K) val = TA ? A[gk * lda + gm] : A[gm * lda + gk];
+      As[kk][mm] = val;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int idx = tid + NT * r;
+      int nn, kk;
+      if (!TB) { kk = idx / TN; nn = idx % TN; } else { nn = idx / TK; kk = idx % TK; }
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      double val = 0.0;
+      if (gn < N && gk < K) val = TB ? B[gn * ldb + gk] : B[gk * ldb + gn];
+      Bs[kk][nn] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      double* c = C + gm * ldc + gn;
+      *c = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+    }
+  }
+}
+
+struct Strides {
+  int nd;
+  int64_t shape[8];
+  int64_t istride[8];
+  int64_t ostride[8];
+};
+
+__global__ void strided_copy_kernel(double* __restrict__ out, const double* __restrict__ in,
+                                    int64_t total, Strides st, double alpha, double beta) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = idx, ioff = 0, ooff = 0;
+    for (int d = st.nd - 1; d >= 0; --d) {
+      const int64_t c = rem % st.shape[d];
+      rem /= st.shape[d];
+      ioff += c * st.istride[d];
+      ooff += c * st.ostride[d];
+    }
+    const double val = alpha * in[ioff];
+    out[ooff] = (beta == 0.0) ? val : val + beta * out[ooff];
+  }
+}
+
+__global__ void fill_kernel(double* x, double v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+__global__ void axpby_kernel(double* y, const double* x, double a, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * y[i]);
+}
+
+constexpr int RB = 256;       // reduction block
+constexpr int RG = 4 * 152;   // reduction grid (4 blocks per SM)
+
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double nanmax(double a, double b) {
+  return (b > a || b != b) ? b : a;  // keeps NaN
+}
+
+__device__ double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// partial[row][block] = sum over this block's grid-stride share of x . Y[row]
+__global__ void dot_rows_partial(const double* __restrict__ x, const double* __restrict__ Y,
+                                 int64_t ldy, int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int row = blockIdx.y;
+  const double* y = Y + row * ldy;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(x[i], y[i], acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[row * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void sum_partials(const double* __restrict__ partial, int parts, double* out) {
+  __shared__ double sh[32];
+  const int row = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < parts; i += blockDim.x) acc += partial[row * parts + i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[row] = acc;
+}
+
+__global__ void maxabs_partial(const double* __restrict__ x, int64_t n, double* partial) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = fabs(x[i]);
+    m = (a > m || a != a) ? a : m;  // propagate NaN
+  }
+  m = block_max(m, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = m;
+}
+
+__global__ void max_partials(const double* partial, int parts, double* out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < parts; i += blockDim.x) {
+    const double a = partial[i];
+    m = (a > m || a != a) ? a : m;
+  }
+  m = block_max(m, sh);
+  if (threadIdx.x == 0) out[0] = m;
+}
+
+__global__ void lincomb_kernel(double* y, const double* X, int64_t ldx, const double* c,
+                               int m, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int kk = 0; kk < m; ++kk) acc = fma(c[kk], X[kk * ldx + i], acc);
+    y[i] = acc;
+  }
+}
+
+// L = 1 + x - t1m - t1m x ;  R = 1 - x + t1m - x t1m   (t1m[o+a][i] = t1[i][a])
+__global__ void build_LR_kernel(double* L, double* R, const double* t1, int o, int v,
+                                int hole, int particle, double xv) {
+  const int n = o + v;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+       idx += gridDim.x * blockDim.x) {
+    const int r = idx / n, c = idx % n;
+    double l = (r == c) ? 1.0 : 0.0, rr = l;
+    if (r >= o && c < o) {  // virtual row, occupied column: -t1m / +t1m
+      const double t = t1[c * v + (r - o)];
+      l -= t;
+      rr += t;
+    }
+    if (hole >= 0) {
+      const int p = o + particle;
+      if (r == hole && c == p) { l += xv; rr -= xv; }
+      if (r >= o && c == p) l -= t1[hole * v + (r - o)] * xv;      // (t1m x)[o+a][p]
+      if (r == hole && c < o) rr -= xv * t1[c * v + particle];     // (x t1m)[h][i]
+    }
+    L[idx] = l;
+    R[idx] = rr;
+  }
+}
+
+__global__ void tilde_kernel(double* u, const double* t, int o, int v) {
+  const int64_t vv = (int64_t)v * v, total = (int64_t)o * o * vv;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ab = idx % vv, ij = idx / vv;
+    const int64_t i = ij / o, j = ij % o;
+    u[idx] = 2.0 * t[idx] - t[(j * o + i) * vv + ab];
+  }
+}
+
+__global__ void mixed_mask_kernel(double* m, const double* t, int o, int v, int hole,
+                                  int particle) {
+  const int64_t total = (int64_t)o * o * v * v;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx;
+    const int b = (int)(r % v); r /= v;
+    const int a = (int)(r % v); r /= v;
+    const int j = (int)(r % o); r /= o;
+    const int i = (int)r;
+    const int cnt = (i == hole) + (j == hole) + (a == particle) + (b == particle);
+    m[idx] = (cnt >= 1 && cnt <= 3) ? t[idx] : 0.0;
+  }
+}
+
+__global__ void jacobi_kernel(double* tn, double* e, const double* t, const double* r,
+                              const double* eps, int o, int v, const int32_t* t3idx,
+                              int64_t n3) {
+  const int64_t n1 = (int64_t)o * v, n2 = n1 * n1, total = n1 + n2 + n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double D;
+    if (idx < n1) {
+      const int i = (int)(idx / v), a = (int)(idx % v);
+      D = eps[i] - eps[o + a];
+    } else if (idx < n1 + n2) {
+      int64_t q = idx - n1;
+      const int b = (int)(q % v); q /= v;
+      const int a = (int)(q % v); q /= v;
+      const int j = (int)(q % o); q /= o;
+      const int i = (int)q;
+      D = eps[i] + eps[j] - eps[o + a] - eps[o + b];
+    } else {
+      const int32_t* ix = t3idx + 6 * (idx - n1 - n2);
+      D = eps[ix[0]] + eps[ix[1]] + eps[ix[2]] - eps[o + ix[3]] - eps[o + ix[4]] - eps[o + ix[5]];
+    }
+    const double step = r[idx] / D;
+    tn[idx] = t[idx] + step;
+    e[idx] = step;
+  }
+}
+
+__global__ void diag_sum_kernel(double* d, const double* B, int naux, int n, int o) {
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= naux) return;
+  const double* b = B + (int64_t)P * n * n;
+  double acc = 0.0;
+  for (int kk = 0; kk < o; ++kk) acc += b[kk * n + kk];
+  d[P] = acc;
+}
+
+__global__ void reference_energy_kernel(double* out, const double* h, int n, const double* g,
+                                        int o) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const int64_t o2 = (int64_t)o * o;
+  for (int64_t idx = threadIdx.x; idx < o2; idx += blockDim.x) {
+    const int64_t i = idx / o, j = idx % o;
+    // g[i][i][j][j] and g[i][j][j][i] of an o^4 block
+    acc += 2.0 * g[((i * o + i) * o + j) * o + j] - g[((i * o + j) * o + j) * o + i];
+  }
+  for (int i = threadIdx.x; i < o; i += blockDim.x) acc += 2.0 * h[(int64_t)i * n + i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[0] = acc;
+}
+
+int grid_for(int64_t n, int block = 256) {
+  int64_t g = (n + block - 1) / block;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+void gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+              const double* A, int64_t lda, int64_t sA, const double* B, int64_t ldb,
+              int64_t sB, double beta, double* C, int64_t ldc, int64_t sC, int64_t batch) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (K <= 0) {
+    // an empty contraction: C = beta C on a contiguous batch of M x N blocks
+    ASCC_REQUIRE(ldc == N && (batch == 1 || sC == M * N), "gemm_f64: K = 0 needs contiguous C");
+    if (beta == 0.0) fill(s, C, 0.0, M * N * batch);
+    else axpby(s, C, C, 0.0, beta, M * N * batch);
+    return;
+  }
+  dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM), 1);
+  for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
+    const int64_t nb = std::min<int64_t>(65535, batch - b0);
+    grid.z = (unsigned)nb;
+    const double* Ab = A + b0 * sA;
+    const double* Bb = B + b0 * sB;
+    double* Cb = C + b0 * sC;
+    if (!ta && !tb)
+      gemm_f64_kernel<false, false><<<grid, NT, 0, s>>>(M, N, K, alpha, Ab, lda, sA, Bb, ldb, sB, beta, Cb, ldc, sC);
+    else if (ta && !tb)
+      gemm_f64_kernel<true, false><<<grid, NT, 0, s>>>(M, N, K, alpha, Ab, lda, sA, Bb, ldb, sB, beta, Cb, ldc, sC);
+    else if (!ta && tb)
+      gemm_f64_kernel<false, true><<<grid, NT, 0, s>>>(M, N, K, alpha, Ab, lda, sA, Bb, ldb, sB, beta, Cb, ldc, sC);
+    else
+      gemm_f64_kernel<true, true><<<grid, NT, 0, s>>>(M, N, K, alpha, Ab, lda, sA, Bb, ldb, sB, beta, Cb, ldc, sC);
+    count_launch();
+  }
+  check_launch("gemm_f64");
+}
+
+void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const double* in,
+                  const int64_t* in_stride, int nd, const int64_t* shape, double alpha,
+                  double beta) {
+  ASCC_REQUIRE(nd >= 1 && nd <= 8, "strided_copy: 1..8 dimensions");
+  Strides st;
+  st.nd = nd;
+  int64_t total = 1;
+  for (int d = 0; d < nd; ++d) {
+    st.shape[d] = shape[d];
+    st.istride[d] = in_stride[d];
+    st.ostride[d] = out_stride[d];
+    total *= shape[d];
+  }
+  if (total == 0) return;
+  strided_copy_kernel<<<grid_for(total), 256, 0, s>>>(out, in, total, st, alpha, beta);
+  count_launch();
+  check_launch("strided_copy");
+}
+
+void fill(cudaStream_t s, double* x, double v, int64_t n) {
+  if (n <= 0) return;
+  fill_kernel<<<grid_for(n), 256, 0, s>>>(x, v, n);
+  count_launch();
+  check_launch("fill");
+}
+
+void axpby(cudaStream_t s, double* y, const double* x, double a, double b, int64_t n) {
+  if (n <= 0) return;
+  axpby_kernel<<<grid_for(n), 256, 0, s>>>(y, x, a, b, n);
+  count_launch();
+  check_launch("axpby");
+}
+
+void dot_rows(cudaStream_t s, const double* x, const double* Y, int64_t ldy, int rows, int64_t n,
+              double* out, double* work) {
+  if (rows <= 0) return;
+  dim3 g(RG, rows);
+  dot_rows_partial<<<g, RB, 0, s>>>(x, Y, ldy, n, work);
+  sum_partials<<<rows, RB, 0, s>>>(work, RG, out);
+  count_launch(2);
+  check_launch("dot_rows");
+}
+
+void maxabs(cudaStream_t s, const double* x, int64_t n, double* out, double* work) {
+  maxabs_partial<<<RG, RB, 0, s>>>(x, n, work);
+  max_partials<<<1, RB, 0, s>>>(work, RG, out);
+  count_launch(2);
+  check_launch("maxabs");
+}
+
+void lincomb(cudaStream_t s, double* y, const double* X, int64_t ldx, const double* c, int m,
+             int64_t n) {
+  lincomb_kernel<<<grid_for(n), 256, 0, s>>>(y, X, ldx, c, m, n);
+  count_launch();
+  check_launch("lincomb");
+}
+
+void build_LR(cudaStream_t s, double* L, double* R, const double* t1, int o, int v, int hole,
+              int particle, double xval) {
+  const int n = o + v;
+  build_LR_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(L, R, t1, o, v, hole, particle, xval);
+  count_launch();
+  check_launch("build_LR");
+}
+
+void tilde(cudaStream_t s, double* u, const double* t, int o, int v) {
+  tilde_kernel<<<grid_for((int64_t)o * o * v * v), 256, 0, s>>>(u, t, o, v);
+  count_launch();
+  check_launch("tilde");
+}
+
+void mixed_mask(cudaStream_t s, double* m, const double* t, int o, int v, int hole, int particle) {
+  mixed_mask_kernel<<<grid_for((int64_t)o * o * v * v), 256, 0, s>>>(m, t, o, v, hole, particle);
+  count_launch();
+  check_launch("mixed_mask");
+}
+
+void jacobi(cudaStream_t s, double* tn, double* e, const double* t, const double* r,
+            const double* eps, int o, int v, const int32_t* t3idx, int64_t n3) {
+  const int64_t total = (int64_t)o * v + (int64_t)o * o * v * v + n3;
+  jacobi_kernel<<<grid_for(total), 256, 0, s>>>(tn, e, t, r, eps, o, v, t3idx, n3);
+  count_launch();
+  check_launch("jacobi");
+}
+
+void diag_sum(cudaStream_t s, double* d, const double* B, int naux, int n, int o) {
+  diag_sum_kernel<<<(naux + 127) / 128, 128, 0, s>>>(d, B, naux, n, o);
+  count_launch();
+  check_launch("diag_sum");
+}
+
+void reference_energy(cudaStream_t s, double* out, const double* h, int n, const double* goooo,
+                      int o) {
+  reference_energy_kernel<<<1, 256, 0, s>>>(out, h, n, goooo, o);
+  count_launch();
+  check_launch("reference_energy");
+}
+
+}  // namespace k
+}  // namespace ascc

@@ -1,0 +1,103 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Bars (FP64 path): relative residual norm <= 1e-9 and energy within 1e-10 Eh
+per evaluation; converged solve energies within 1e-10 Eh.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import amplitudes as amp
+from oracle import ascc as oracle_ascc
+from oracle import spinadapted as sa
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-9
+E_TOL = 1e-10
+
+
+def _ctx(s, hole, part, **kw):
+    import paper_2501_10515_gb300 as pkg
+    return pkg.Context(s.o, s.v, s.naux, s.eps, s.B, hole=hole, particle=part, **kw)
+
+
+def _oracle_residual(s, hole, part, t1, t2, linearize, lh, lp):
+    hbar, Bbar, _ = oracle_ascc.prepare(s.eps, s.B, s.o, hole, part)
+    return sa.residual(hbar, Bbar, s.o, t1, t2, linearize=linearize, hole=lh, particle=lp)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = [
+    # (o, v, seed, excitation or None, linearize)
+    (1, 4, 0, (0, 0), False),
+    (3, 1, 1, None, False),
+    (4, 20, 0, None, False),
+    (4, 20, 0, (3, 0), False),
+    (4, 20, 0, (3, 0), True),
+    (5, 23, 2, (1, 7), True),
+    (9, 70, 3, (8, 2), True),
+    (9, 70, 3, None, True),
+]
+
+
+@pytest.mark.parametrize("o,v,seed,exc,lin", CASES)
+def test_residual_matches_oracle(o, v, seed, exc, lin):
+    s = synth.make_system(o, v, seed=seed)
+    hole, part = exc if exc else (None, None)
+    lh, lp = exc if exc else (o - 1, 0)
+    t1, t2, _ = synth.random_amplitudes(o, v, seed=seed + 100, scale=0.05)
+    if exc:
+        g1, g2, _ = amp.initial_guess(o, v, hole, part)
+        t1 = t1 + g1; t2 = t2 + g2
+    kw = dict(linearize=int(lin), pl_hole=lh if exc is None else -1, pl_particle=lp if exc is None else -1)
+    ctx = _ctx(s, hole, part, **kw)
+    E, r1, r2, _ = ctx.residual(t1, t2)
+    Eo, r1o, r2o, _ = _oracle_residual(s, hole, part, t1, t2, lin, lh, lp)
+    R = np.concatenate([r1.ravel(), r2.ravel()]); Ro = np.concatenate([r1o.ravel(), r2o.ravel()])
+    assert _rel(R, Ro) <= REL_TOL, (_rel(r1, r1o), _rel(r2, r2o))
+    assert abs(E - Eo) <= E_TOL
+    assert ctx.launches() > 0
+
+
+@pytest.mark.parametrize("exc,lin", [(None, False), ((3, 0), False), ((3, 0), True), (None, True)])
+def test_solve_matches_oracle(exc, lin):
+    o, v = 4, 20
+    s = synth.make_system(o, v, seed=0)
+    hole, part = exc if exc else (None, None)
+    kw = dict(linearize=int(lin), pl_hole=3 if exc is None else -1, pl_particle=0 if exc is None else -1)
+    ctx = _ctx(s, hole, part, **kw)
+    res = ctx.solve()
+    ref = oracle_ascc.solve_state(s.eps, s.B, o, hole, part, linearize=lin, pl_hole=3, pl_particle=0)
+    assert ref.converged and res.status == 0
+    assert abs(res.energy - ref.energy) <= E_TOL
+    t1, t2, _ = ctx.get_state()
+    assert np.abs(t2 - ref.t2).max() < 1e-7
+
+
+def test_checkpoint_roundtrip_and_energy():
+    o, v = 4, 12
+    s = synth.make_system(o, v, seed=5)
+    ctx = _ctx(s, 3, 1, linearize=1)
+    t1, t2, _ = synth.random_amplitudes(o, v, seed=9, scale=0.05)
+    ctx.set_state(t1, t2)
+    a1, a2, _ = ctx.get_state()
+    assert np.array_equal(a1, t1) and np.array_equal(a2, t2)
+    E, _, _, _ = ctx.residual(t1, t2)
+    assert ctx.energy(t1, t2) == E
+
+
+def test_sibling_state_shares_molecule():
+    o, v = 4, 16
+    s = synth.make_system(o, v, seed=4)
+    gs = _ctx(s, None, None, linearize=1, pl_hole=3, pl_particle=0)
+    import paper_2501_10515_gb300 as pkg
+    ex = pkg.Context(o, v, s.naux, None, None, hole=3, particle=0, base=gs, linearize=1)
+    t1, t2, _ = synth.random_amplitudes(o, v, seed=3, scale=0.05)
+    E, r1, r2, _ = ex.residual(t1, t2)
+    ref = _ctx(s, 3, 0, linearize=1)
+    E2, q1, q2, _ = ref.residual(t1, t2)
+    assert E == E2 and np.array_equal(r2, q2)
