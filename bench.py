@@ -1,0 +1,288 @@
+"""Benchmark of the ASCC/PLASCC residual hot path on GB300.
+
+Workload (default): the o=20, v=200 FP64 state -- naux = 660, seed 0,
+charge-transfer-like excitation from occupied 19 to virtual 3, PLASCC,
+synthetic integrals (see synth/).  One step is one pass of the whole hot
+path: the residual (integral dressing, Fock and ring/ladder intermediates,
+particle-particle ladder, partial linearisation, energy), the convergence
+test, the Jacobi update and the DIIS extrapolation of one solve iteration.
+Warm-up steps continue the same solve.  `value` is the residual throughput in
+TFLOP/s (algorithmic flops of the contractions the path performs, summed over
+ranks, over the max-over-ranks step time); `e2e` is the same through the
+host-buffer C-ABI call with the copies inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = ("ASCC solves/sec & residual TFLOP/s vs plain FP64 at 1e-6 Eh; "
+          "p50/p99 latency")
+WORKLOADS = {
+    "c2": dict(o=20, v=200, seed=0, hole=19, particle=3,
+               name="ascc-fp64 o=20 v=200 naux=660 excitation 19->3 (PLASCC)"),
+    "c1": dict(o=4, v=20, seed=0, hole=3, particle=0,
+               name="ascc-fp64 o=4 v=20 naux=72 excitation 3->0 (PLASCC)"),
+}
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def rank_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[5 + k].lower() in ("active", "1")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def oracle_residual_timer(wl, steps, warmup):
+    """The CPU oracle's residual at the same state; returns (seconds per step list, flops ref)."""
+    import synth
+    from oracle import amplitudes as amp
+    from oracle import ascc as oracle_ascc
+    from oracle import spinadapted as sa
+    o, v = wl["o"], wl["v"]
+    s = synth.make_system(o, v, seed=wl["seed"])
+    hbar, Bbar, _ = oracle_ascc.prepare(s.eps, s.B, o, wl["hole"], wl["particle"])
+    t1, t2, _ = amp.initial_guess(o, v, wl["hole"], wl["particle"])
+    times = []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        sa.residual(hbar, Bbar, o, t1, t2, linearize=True, hole=wl["hole"], particle=wl["particle"])
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+    return times
+
+
+def flops_per_residual(o, v, naux, excited=True, linearize=True):
+    """Algorithmic flops of one residual of this path (2 per multiply-add).
+
+    Counts the contractions the CUDA path performs (the same count the
+    library accumulates in ascc_profile.gemm_flops), so the CPU baseline and
+    the reference arm can be put on the same scale without a GPU.
+    """
+    n = o + v
+    P = naux
+    f = 0.0
+    f += 2 * 2 * P * n ** 3 + 4 * n ** 3              # dressing L B R, L h R
+    f += 2 * n * n * P + 2 * n * n * o * P             # J, K
+    f += 2 * P * (o ** 4 + o ** 3 * v + 5 * o * o * v * v)  # DF blocks
+    f += 2 * P * o * v * o * v + 2 * P * v * v * o      # singles DF term
+    f += 2 * o ** 3 * v * v * 2                         # singles ooov, Fov
+    f += 2 * o * o * v * v * n * v                      # dense ladder (xc|bd)
+    nu = v + (1 if excited else 0)
+    if excited:
+        f += 3 * 2 * o * o * n * v * v                  # hole-slot corrections
+    f += 2 * o * o * nu * nu * o * o                    # occupied ladder rows
+    f += 2 * o * o * n * n * v + 2 * o * o * v * v * n  # L (x) L dressing
+    f += 2 * o ** 4 * v * v                             # oooo x t
+    f += 3 * 2 * o ** 3 * v ** 3                        # linear ring / crossed ring
+    f += 2 * o * o * v ** 3 + 2 * o ** 3 * v * v        # linear Fock-like
+    quad = 2 * o ** 4 * v * v * 2 + 2 * o ** 3 * v ** 3 * 5 + 2 * o ** 3 * v * v * 2 \
+        + 2 * o * o * v ** 3 + 2 * o ** 3 * v * v
+    f += quad * (2 if linearize else 1)
+    f += 2 * o * o * v * v                              # energy
+    return f
+
+
+def run_reference(args, wl):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return 0
+    cores = len(os.sched_getaffinity(0))
+    times = oracle_residual_timer(wl, args.steps, args.warmup)
+    naux = 3 * (wl["o"] + wl["v"])
+    fl = flops_per_residual(wl["o"], wl["v"], naux)
+    ms = 1e3 * sum(times) / len(times)
+    value = fl / (sum(times) / len(times)) / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "o": wl["o"], "v": wl["v"], "naux": naux,
+                   "excitation": [wl["hole"], wl["particle"]], "method": "PLASCC",
+                   "step": "one oracle residual evaluation at the zeroth-order guess"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": "one residual evaluation of the same state per step"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    rank, world, local = rank_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import synth
+    import paper_2501_10515_gb300 as pkg
+
+    o, v = wl["o"], wl["v"]
+    s = synth.make_system(o, v, seed=wl["seed"])
+    stream = torch.cuda.current_stream()
+    ctx = pkg.Context(o, v, s.naux, s.eps, s.B, hole=wl["hole"], particle=wl["particle"],
+                      linearize=1, stream=stream.cuda_stream)
+    ctx.reset()
+    ctx.iterate(args.warmup)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    p0 = ctx.profile()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    res = ctx.iterate(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ctx.set_profiling(False)
+    p1 = ctx.profile()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops_step = (p1.gemm_flops - p0.gemm_flops) / args.steps
+    value = world * flops_step * args.steps / (ms / 1e3) / 1e12
+    launches = int(p1.launches - p0.launches)
+    lad_ms = (p1.ladder_ms - p0.ladder_ms) / max(1, p1.ladder_launches - p0.ladder_launches)
+    lad_fl = (p1.ladder_flops - p0.ladder_flops) / max(1, p1.ladder_launches - p0.ladder_launches)
+    achieved = lad_fl / (lad_ms / 1e3) / 1e12
+
+    # end to end through the host-buffer call (copies inside the timed region)
+    pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    t1h, t2h, _ = ctx.get_state()
+    t1p, t2p = pin(t1h.shape), pin(t2h.shape)
+    t1p[...] = t1h; t2p[...] = t2h
+    ctx.residual(t1p, t2p)
+    torch.cuda.synchronize()
+    f0 = ctx.profile().gemm_flops
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        E, r1, r2, _ = ctx.residual(t1p, t2p)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_fl = (ctx.profile().gemm_flops - f0) / args.e2e_steps
+    bytes_in = t1p.nbytes + t2p.nbytes
+    bytes_out = r1.nbytes + r2.nbytes + 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "o": o, "v": v, "naux": s.naux,
+                   "excitation": [wl["hole"], wl["particle"]], "method": "PLASCC",
+                   "precision": "fp64", "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2: the 14 GB (xc|bd) block is streamed every step",
+                   "step": "one solve iteration (residual + convergence test + Jacobi + DIIS)"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_fl / e2e_s / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "kernel": "gemm_f64 (dense particle-particle ladder)",
+                     "peak_source": "nominal FP64 rate of the recipe table (no measured FP64 peak)"},
+        "iteration_energy": res.energy, "iteration_max_resid": res.max_resid,
+        "flops_per_step": flops_step, "flops_per_step_model": flops_per_residual(o, v, s.naux),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = len(os.sched_getaffinity(0))
+        times = oracle_residual_timer(wl, 1, 0)
+        line["cpu_baseline"] = {"value": flops_step / times[0] / 1e12, "unit": "TFLOP/s",
+                                "cores": cores, "kind": "oracle",
+                                "sample": "one oracle residual evaluation of the same state "
+                                          "(flops counted as the GPU step's)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

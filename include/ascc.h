@@ -151,6 +151,44 @@ ascc_status ascc_energy(ascc_ctx* ctx, const double* t1, const double* t2,
  * ASCC_ERR_DIVERGED otherwise (res is filled in every case). */
 ascc_status ascc_solve(ascc_ctx* ctx, ascc_result* res);
 
+/* Step-wise solve (Sec. III.B).  ascc_reset loads the zeroth-order guess
+ * (Eq. TP-guess) and clears the DIIS history; ascc_iterate continues from the
+ * current amplitudes and history for at most max_steps residual evaluations
+ * and fills *res.  Returns ASCC_OK once converged, ASCC_ERR_NOT_CONVERGED
+ * while still iterating or at the cap, ASCC_ERR_DIVERGED on non-finite
+ * values.  ascc_solve = ascc_reset + ascc_iterate(max_iter + 1). */
+ascc_status ascc_reset(ascc_ctx* ctx);
+ascc_status ascc_iterate(ascc_ctx* ctx, int32_t max_steps, ascc_result* res);
+
+/* Profiling of the dense particle-particle ladder contraction: when enabled,
+ * each launch is bracketed by CUDA events on the context's stream.
+ * ascc_get_profile reports the summed event time (ms), the number of
+ * launches and their algorithmic flops (2 o^2 v^2 (o+v) v each). */
+typedef struct {
+  double ladder_ms;
+  double ladder_flops;
+  int64_t ladder_launches;
+  int64_t launches;   /* kernel launches of this library since the context was made */
+  double gemm_flops;  /* flops (2 m n k) of all contractions since the context was made */
+} ascc_profile;
+ascc_status ascc_set_profiling(ascc_ctx* ctx, int32_t enable);
+ascc_status ascc_get_profile(ascc_ctx* ctx, ascc_profile* out);
+
+/* Split-precision tensor-core GEMM used by the mixed-precision residual:
+ *   C = alpha * A B^T + beta * C,
+ * A [M][K], B [N][K], C [M][N]: row-major FP64 device buffers.  Each operand
+ * is split into `level` BF16 planes (x = x0 + x1 + ..., level 1..3) and the
+ * 1, 3 or 6 leading plane products run as tcgen05 BF16 MMAs with FP32
+ * accumulation; relative accuracy is about 4e-3, 2e-5 and 1e-7 respectively
+ * (the paper's own code is FP64 NumPy; this is the GB300 precision device
+ * behind ASCC_MIXED_BF16).  stream: cudaStream_t or NULL (default stream);
+ * the call does not synchronise.  Returns ASCC_ERR_TIMEOUT if a bounded wait
+ * inside the kernel gave up (checked at the next call on the same stream
+ * after synchronisation by the caller). */
+ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level,
+                                 double alpha, const double* A, const double* B,
+                                 double beta, double* C, void* stream);
+
 /* Checkpoint / resume of the amplitudes (host buffers, FP64). */
 ascc_status ascc_get_state(ascc_ctx* ctx, double* t1, double* t2, double* t3p);
 ascc_status ascc_set_state(ascc_ctx* ctx, const double* t1, const double* t2,

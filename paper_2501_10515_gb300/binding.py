@@ -36,6 +36,12 @@ class Result(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class Profile(C.Structure):
+    _fields_ = [("ladder_ms", C.c_double), ("ladder_flops", C.c_double),
+                ("ladder_launches", C.c_int64), ("launches", C.c_int64),
+                ("gemm_flops", C.c_double)]
+
+
 class AsccError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -67,6 +73,12 @@ def load():
         "ascc_residual_device": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "ascc_energy": (C.c_int, [vp, dp, dp, dp]),
         "ascc_solve": (C.c_int, [vp, P(Result)]),
+        "ascc_reset": (C.c_int, [vp]),
+        "ascc_iterate": (C.c_int, [vp, C.c_int32, P(Result)]),
+        "ascc_set_profiling": (C.c_int, [vp, C.c_int32]),
+        "ascc_get_profile": (C.c_int, [vp, P(Profile)]),
+        "ascc_gemm_split_bf16": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_double,
+                                           vp, vp, C.c_double, vp, vp]),
         "ascc_get_state": (C.c_int, [vp, dp, dp, dp]),
         "ascc_set_state": (C.c_int, [vp, dp, dp, dp]),
         "ascc_footprint_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, P(Options)]),
@@ -92,6 +104,19 @@ def symbols():
 def _check(st):
     if st != 0:
         raise AsccError(st, load().ascc_last_error().decode())
+
+
+def gemm_split_bf16(A, B, out, level, alpha=1.0, beta=0.0, stream=None):
+    """out = alpha A B^T + beta out on device FP64 tensors (split-BF16 tensor cores)."""
+    M, K = A.shape
+    N = B.shape[0]
+    assert tuple(out.shape) == (M, N) and B.shape[1] == K
+    _check(load().ascc_gemm_split_bf16(M, N, K, level, alpha, C_void(A), C_void(B), beta,
+                                       C_void(out), C.c_void_p(stream) if stream else None))
+
+
+def C_void(x):
+    return C.c_void_p(x.data_ptr())
 
 
 def default_options(**kw) -> Options:
@@ -188,6 +213,24 @@ class Context:
         elif st not in (0, 4, 5):
             _check(st)
         return res
+
+    def reset(self):
+        _check(load().ascc_reset(self._h))
+
+    def iterate(self, max_steps) -> Result:
+        res = Result()
+        st = load().ascc_iterate(self._h, int(max_steps), C.byref(res))
+        if st not in (0, 4, 5):
+            _check(st)
+        return res
+
+    def set_profiling(self, on=True):
+        _check(load().ascc_set_profiling(self._h, int(bool(on))))
+
+    def profile(self) -> Profile:
+        p = Profile()
+        _check(load().ascc_get_profile(self._h, C.byref(p)))
+        return p
 
     def get_state(self):
         o, v = self.o, self.v

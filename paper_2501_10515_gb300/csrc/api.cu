@@ -4,6 +4,7 @@
 #include <memory>
 
 #include "engine.h"
+#include "gemm_tc.h"
 #include "kernels.h"
 
 using namespace ascc;
@@ -13,6 +14,7 @@ struct ascc_ctx {
   bool own_stream = false;
   std::unique_ptr<State> state;
   int64_t launches0 = 0;
+  double flops0 = 0.0;
   ~ascc_ctx() {
     if (stream) cudaStreamSynchronize(stream);
     state.reset();
@@ -87,6 +89,7 @@ ascc_status make_ctx(ascc_ctx** out, std::shared_ptr<Molecule> mol, const ascc_e
   ctx->stream = stream;
   ctx->own_stream = own;
   ctx->launches0 = launch_total();
+  ctx->flops0 = flop_total();
   int hole, particle;
   double beta;
   check_exc(exc, mol->o, mol->v, hole, particle, beta);
@@ -187,6 +190,7 @@ ascc_status ascc_residual_device(ascc_ctx* ctx, const double* t1, const double* 
     ASCC_CUDA(cudaMemcpyAsync(tv.p(), t1, n1 * 8, cudaMemcpyDeviceToDevice, s));
     ASCC_CUDA(cudaMemcpyAsync(tv.p() + n1, t2, n2 * 8, cudaMemcpyDeviceToDevice, s));
     if (n3) ASCC_CUDA(cudaMemcpyAsync(tv.p() + n1 + n2, t3p, n3 * 8, cudaMemcpyDeviceToDevice, s));
+    S.prepare_eval();
     S.residual(tv.p(), rv.p(), e.p());
     if (r1) ASCC_CUDA(cudaMemcpyAsync(r1, rv.p(), n1 * 8, cudaMemcpyDeviceToDevice, s));
     if (r2) ASCC_CUDA(cudaMemcpyAsync(r2, rv.p() + n1, n2 * 8, cudaMemcpyDeviceToDevice, s));
@@ -209,6 +213,7 @@ ascc_status ascc_residual(ascc_ctx* ctx, const double* t1, const double* t2, con
     ASCC_CUDA(cudaMemcpyAsync(tv.p(), t1, n1 * 8, cudaMemcpyHostToDevice, s));
     ASCC_CUDA(cudaMemcpyAsync(tv.p() + n1, t2, n2 * 8, cudaMemcpyHostToDevice, s));
     if (n3) ASCC_CUDA(cudaMemcpyAsync(tv.p() + n1 + n2, t3p, n3 * 8, cudaMemcpyHostToDevice, s));
+    S.prepare_eval();
     S.residual(tv.p(), rv.p(), e.p());
     if (r1) ASCC_CUDA(cudaMemcpyAsync(r1, rv.p(), n1 * 8, cudaMemcpyDeviceToHost, s));
     if (r2) ASCC_CUDA(cudaMemcpyAsync(r2, rv.p() + n1, n2 * 8, cudaMemcpyDeviceToHost, s));
@@ -244,6 +249,68 @@ ascc_status ascc_solve(ascc_ctx* ctx, ascc_result* res) {
     if (res) res->e_ref = eref;
     if (st != ASCC_OK) g_err = st == ASCC_ERR_DIVERGED ? "diverged" : "not converged";
     return st;
+  });
+}
+
+ascc_status ascc_reset(ascc_ctx* ctx) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state, "null argument");
+    ctx->state->reset();
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_iterate(ascc_ctx* ctx, int32_t max_steps, ascc_result* res) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && max_steps >= 0, "bad argument");
+    return ctx->state->iterate(max_steps, res);
+  });
+}
+
+ascc_status ascc_set_profiling(ascc_ctx* ctx, int32_t enable) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state, "null argument");
+    ctx->state->set_profiling(enable != 0);
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_get_profile(ascc_ctx* ctx, ascc_profile* out) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && out, "null argument");
+    ctx->state->profile(&out->ladder_ms, &out->ladder_launches, &out->ladder_flops);
+    out->launches = launch_total() - ctx->launches0;
+    out->gemm_flops = flop_total() - ctx->flops0;
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level, double alpha,
+                                 const double* A, const double* B, double beta, double* C,
+                                 void* stream) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(A && B && C && M > 0 && N > 0 && K > 0, "bad argument");
+    ASCC_REQUIRE(level >= 1 && level <= 3, "level must be 1, 2 or 3");
+    cudaStream_t s = (cudaStream_t)stream;
+    static int* err = nullptr;
+    if (!err) {
+      ASCC_CUDA(cudaMalloc(&err, sizeof(int)));
+      ASCC_CUDA(cudaMemset(err, 0, sizeof(int)));
+    }
+    int h = 0;
+    ASCC_CUDA(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+      cudaMemset(err, 0, sizeof(int));
+      throw Error(ASCC_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+    }
+    const int64_t Kp = tc::padded_k(K);
+    DevBuf pa(sizeof(__nv_bfloat16) * (size_t)(level * M * Kp), s);
+    DevBuf pb(sizeof(__nv_bfloat16) * (size_t)(level * N * Kp), s);
+    tc::split_bf16(s, pa.as<__nv_bfloat16>(), A, M, K, K, level);
+    tc::split_bf16(s, pb.as<__nv_bfloat16>(), B, N, K, K, level);
+    tc::gemm_split(s, M, N, K, level, alpha, pa.as<__nv_bfloat16>(), pb.as<__nv_bfloat16>(), beta,
+                   C, N, err);
+    return ASCC_OK;
   });
 }
 

@@ -41,6 +41,8 @@ struct Error : std::runtime_error {
 // context can report how many of its own kernels ran.
 void count_launch(int64_t n = 1);
 int64_t launch_total();
+void count_flops(double f);
+double flop_total();
 void check_launch(const char* what);
 
 // Stream-ordered device buffer.

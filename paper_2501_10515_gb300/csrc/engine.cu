@@ -15,6 +15,7 @@
 #include <map>
 
 #include "engine.h"
+#include "gemm_tc.h"
 #include "kernels.h"
 
 namespace ascc {
@@ -143,8 +144,39 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
     perm((sp.b + "->" + want).c_str(), 1.0, B, 0.0, Btmp.t);
     Bp = Btmp.p();
   }
-  const int64_t lda = ta ? Ms : Ks, ldb = tb ? Ks : Ns;
   const std::string cl = bat + Ml + Nl;
+  if (level_ > 0 && nb == 1 && 2.0 * Ms * Ns * Ks >= min_flops_) {
+    // tensor-core path: A as [M][K], B as [N][K] (K contiguous), split into BF16 planes
+    const double* Am = A.p;
+    OT Am_t, Bn_t;
+    if (sp.a != Ml + Kl) {
+      Am_t.make(shape_of(Ml + Kl), s_);
+      perm((sp.a + "->" + Ml + Kl).c_str(), 1.0, A, 0.0, Am_t.t);
+      Am = Am_t.p();
+    }
+    const double* Bn = B.p;
+    if (sp.b != Nl + Kl) {
+      Bn_t.make(shape_of(Nl + Kl), s_);
+      perm((sp.b + "->" + Nl + Kl).c_str(), 1.0, B, 0.0, Bn_t.t);
+      Bn = Bn_t.p();
+    }
+    const int64_t Kp = tc::padded_k(Ks);
+    DevBuf pa(sizeof(__nv_bfloat16) * (size_t)(level_ * Ms * Kp), s_);
+    DevBuf pb(sizeof(__nv_bfloat16) * (size_t)(level_ * Ns * Kp), s_);
+    tc::split_bf16(s_, pa.as<__nv_bfloat16>(), Am, Ms, Ks, Ks, level_);
+    tc::split_bf16(s_, pb.as<__nv_bfloat16>(), Bn, Ns, Ks, Ks, level_);
+    if (sp.c == cl) {
+      tc::gemm_split(s_, Ms, Ns, Ks, level_, alpha, pa.as<__nv_bfloat16>(),
+                     pb.as<__nv_bfloat16>(), beta, C.p, Ns, err_);
+    } else {
+      OT Ct(shape_of(cl), s_);
+      tc::gemm_split(s_, Ms, Ns, Ks, level_, 1.0, pa.as<__nv_bfloat16>(), pb.as<__nv_bfloat16>(),
+                     0.0, Ct.p(), Ns, err_);
+      perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
+    }
+    return;
+  }
+  const int64_t lda = ta ? Ms : Ks, ldb = tb ? Ks : Ns;
   if (sp.c == cl) {
     k::gemm_f64(s_, ta, tb, Ms, Ns, Ks, alpha, Ap, lda, Ms * Ks, Bp, ldb, Ks * Ns, beta, C.p, Ns,
                 Ms * Ns, nb);
@@ -190,6 +222,13 @@ Molecule::Molecule(int o_, int v_, int naux_, const double* eps_h, const double*
   es("Pxc,Pbd->xbcd", 1.0, Bnv.t, Bvv.t, 0.0, Gext.t);
 }
 
+void Molecule::make_bf16_planes() {
+  if (Gext_bf16.bytes()) return;
+  const int64_t rows = (int64_t)n * v, K = (int64_t)v * v, Kp = tc::padded_k(K);
+  Gext_bf16.alloc(sizeof(__nv_bfloat16) * (size_t)(3 * rows * Kp), stream);
+  tc::split_bf16(stream, Gext_bf16.as<__nv_bfloat16>(), Gext.p(), rows, K, K, 3);
+}
+
 size_t Molecule::bytes() const {
   return eps.buf.bytes() + B.buf.bytes() + hcore.buf.bytes() + Bvv.buf.bytes() +
          Bnv.buf.bytes() + Gext.buf.bytes();
@@ -233,7 +272,8 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   lh_ = hole_ >= 0 ? hole_ : opt_.pl_hole;
   lp_ = hole_ >= 0 ? particle_ : opt_.pl_particle;
   if (lh_ < 0) opt_.linearize = 0;
-  ASCC_REQUIRE(opt_.precision == ASCC_FP64, "this build runs the FP64 path only");
+  ASCC_REQUIRE(opt_.precision == ASCC_FP64 || opt_.precision == ASCC_MIXED_BF16,
+               "precision must be ASCC_FP64 or ASCC_MIXED_BF16");
   ASCC_REQUIRE(opt_.diis_dim >= 1 && opt_.diis_dim <= 16, "diis_dim in 1..16");
   if (opt_.triples && hole_ >= 0) {
     t3idx_host_ = t3p_index(o_, v_, hole_, particle_);
@@ -267,10 +307,29 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
     m_.make({o, o, v, v}, s);
     um_.make({o, o, v, v}, s);
   }
+  err_.alloc(sizeof(int), s);
+  err_.zero();
+  if (opt_.precision == ASCC_MIXED_BF16) {
+    ASCC_CUDA(cudaStreamSynchronize(mol_->stream));
+    mol_->make_bf16_planes();
+    ASCC_CUDA(cudaStreamSynchronize(mol_->stream));
+  }
   build_state_integrals();
 }
 
-State::~State() = default;
+// Mixed precision: 3 BF16 products (16 significant bits) until max|R| reaches
+// polish_tol, then 6 products (24 bits) for the polishing iterations.
+int State::level_for_phase() const {
+  if (opt_.precision != ASCC_MIXED_BF16) return 0;
+  return polish_ ? 3 : 2;
+}
+
+State::~State() {
+  for (auto& ev : events_) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+}
 
 void State::build_state_integrals() {
   const int o = o_, v = v_, n = n_, P = naux_, nu = nu_;
@@ -359,7 +418,30 @@ void State::ladder(const T& t2, const T& r2) {
   Molecule& M = *mol_;
   const int64_t vv = (int64_t)v * v;
   // Y[i][j][x][b] = sum_cd t[i][j][c][d] (xc|bd)
-  es_("ijcd,xbcd->ijxb", 1.0, t2, M.Gext.t, 0.0, Y_.t);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (profile_) {
+    ASCC_CUDA(cudaEventCreate(&ev0));
+    ASCC_CUDA(cudaEventCreate(&ev1));
+    ASCC_CUDA(cudaEventRecord(ev0, s_));
+  }
+  if (es_.level() > 0) {
+    const int lev = es_.level();
+    const int64_t K = vv, Kp = tc::padded_k(K), rows = (int64_t)n * v;
+    DevBuf pa(sizeof(__nv_bfloat16) * (size_t)(lev * (int64_t)o * o * Kp), s_);
+    tc::split_bf16(s_, pa.as<__nv_bfloat16>(), t2.p, (int64_t)o * o, K, K, lev);
+    // planes of Gext are stored [3][rows][Kp]; the kernel reads planes 0..lev-1
+    tc::gemm_split(s_, (int64_t)o * o, rows, K, lev, 1.0, pa.as<__nv_bfloat16>(),
+                   M.Gext_bf16.as<__nv_bfloat16>(), 0.0, Y_.p(), rows, err_.as<int>());
+  } else {
+    es_("ijcd,xbcd->ijxb", 1.0, t2, M.Gext.t, 0.0, Y_.t);
+  }
+  if (profile_) {
+    ASCC_CUDA(cudaEventRecord(ev1, s_));
+    events_.push_back({ev0, ev1});
+    ladder_launches_ += 1;
+    ladder_flops_ += 2.0 * o * o * (double)vv * n * v *
+                     (es_.level() > 0 ? tc::products_for(es_.level()) : 1);
+  }
   // R-dressed amplitudes tt[i][j][u][w], u, w over the virtuals (+ hole slot)
   const int64_t s4[4] = {(int64_t)o * vv, vv, v, 1};
   box_copy(s_, tt_.p(), {(int64_t)o * nu * nu, (int64_t)nu * nu, nu, 1}, t2.p,
@@ -529,7 +611,7 @@ bool bordered_solve(const std::vector<double>& G, int m, std::vector<double>& c)
 }
 }  // namespace
 
-ascc_status State::solve(ascc_result* res) {
+void State::reset() {
   const int64_t N = namp();
   std::vector<double> guess;
   initial_guess(guess);
@@ -537,83 +619,131 @@ ascc_status State::solve(ascc_result* res) {
   const int m = opt_.diis_dim;
   k::fill(s_, hist_t_.p(), 0.0, (int64_t)m * N);
   k::fill(s_, hist_e_.p(), 0.0, (int64_t)m * N);
-  std::vector<int> slots;          // history slots, oldest first
-  std::vector<double> G(m * m, 0.0);  // Gram matrix by slot
-  int next_slot = 0;
-  double e_prev = 0.0, e = 0.0, rmax = 0.0;
-  bool have_prev = false;
-  ascc_status st = ASCC_ERR_NOT_CONVERGED;
-  int it = 0;
-  for (it = 0; it <= opt_.max_iter; ++it) {
+  slots_.clear();
+  gram_.assign((size_t)m * m, 0.0);
+  next_slot_ = 0;
+  iter_ = 0;
+  iter_low_ = 0;
+  polish_ = false;
+  have_prev_ = false;
+  done_ = false;
+  status_ = ASCC_ERR_NOT_CONVERGED;
+  ASCC_CUDA(cudaStreamSynchronize(s_));
+}
+
+// One pass per residual evaluation: residual, convergence test, Jacobi step,
+// DIIS extrapolation (rules fixed in the oracle's solver docstring).
+ascc_status State::iterate(int max_steps, ascc_result* res) {
+  const int64_t N = namp();
+  const int m = opt_.diis_dim;
+  for (int step = 0; step < max_steps && !done_; ++step) {
+    const int lev = level_for_phase();
+    es_.set_split(lev, err_.as<int>());
     residual(t_.p(), r_.p(), scal_.p());
     k::maxabs(s_, r_.p(), N, scal_.p() + 1, work_.p());
     double h2[2];
+    int kerr = 0;
     ASCC_CUDA(cudaMemcpyAsync(h2, scal_.p(), 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+    ASCC_CUDA(cudaMemcpyAsync(&kerr, err_.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s_));
     ASCC_CUDA(cudaStreamSynchronize(s_));
-    e = h2[0];
-    rmax = h2[1];
-    if (!std::isfinite(e) || !std::isfinite(rmax)) {
-      st = ASCC_ERR_DIVERGED;
+    if (kerr != 0)
+      throw Error(ASCC_ERR_TIMEOUT, "tensor-core GEMM wait timed out (code " +
+                                        std::to_string(kerr) + ")");
+    e_last_ = h2[0];
+    r_last_ = h2[1];
+    const int it = iter_++;
+    if (lev == 2) ++iter_low_;
+    if (lev == 2 && std::isfinite(r_last_) && r_last_ <= opt_.polish_tol) {
+      // hand over to the polishing precision and re-evaluate before testing convergence
+      polish_ = true;
+      have_prev_ = false;
+    }
+    if (!std::isfinite(e_last_) || !std::isfinite(r_last_)) {
+      status_ = ASCC_ERR_DIVERGED;
+      done_ = true;
       break;
     }
-    if (have_prev && rmax <= opt_.r_tol && std::fabs(e - e_prev) <= opt_.e_tol) {
-      st = ASCC_OK;
+    if (have_prev_ && r_last_ <= opt_.r_tol && std::fabs(e_last_ - e_prev_) <= opt_.e_tol) {
+      status_ = ASCC_OK;
+      done_ = true;
       break;
     }
-    if (it == opt_.max_iter) break;
-    e_prev = e;
-    have_prev = true;
-    // Jacobi step into a history slot
+    if (it >= opt_.max_iter) {
+      status_ = ASCC_ERR_NOT_CONVERGED;
+      done_ = true;
+      break;
+    }
+    e_prev_ = e_last_;
+    have_prev_ = true;
     int slot;
-    if ((int)slots.size() < m) {
-      slot = next_slot++;
+    if ((int)slots_.size() < m) {
+      slot = next_slot_++;
     } else {
-      slot = slots.front();
-      slots.erase(slots.begin());
+      slot = slots_.front();
+      slots_.erase(slots_.begin());
     }
-    slots.push_back(slot);
+    slots_.push_back(slot);
     double* tn = hist_t_.p() + (int64_t)slot * N;
     double* en = hist_e_.p() + (int64_t)slot * N;
     k::jacobi(s_, tn, en, t_.p(), r_.p(), mol_->eps.p(), o_, v_,
               n3() ? reinterpret_cast<const int32_t*>(t3idx_.p()) : nullptr, n3());
-    // Gram row of the new error against the whole history (by slot)
     k::dot_rows(s_, en, hist_e_.p(), N, m, N, scal_.p() + 16, work_.p());
     std::vector<double> row(m);
     ASCC_CUDA(cudaMemcpyAsync(row.data(), scal_.p() + 16, m * sizeof(double),
                               cudaMemcpyDeviceToHost, s_));
     ASCC_CUDA(cudaStreamSynchronize(s_));
-    for (int q : slots) {
-      G[slot * m + q] = row[q];
-      G[q * m + slot] = row[q];
+    for (int q : slots_) {
+      gram_[slot * m + q] = row[q];
+      gram_[q * m + slot] = row[q];
     }
     bool extrapolated = false;
-    if ((int)slots.size() >= opt_.diis_start) {
-      const int cnt = (int)slots.size();
+    if ((int)slots_.size() >= opt_.diis_start) {
+      const int cnt = (int)slots_.size();
       std::vector<double> Gs(cnt * cnt), c;
       for (int a = 0; a < cnt; ++a)
-        for (int b = 0; b < cnt; ++b) Gs[a * cnt + b] = G[slots[a] * m + slots[b]];
+        for (int b = 0; b < cnt; ++b) Gs[a * cnt + b] = gram_[slots_[a] * m + slots_[b]];
       if (bordered_solve(Gs, cnt, c)) {
         std::vector<double> cs(m, 0.0);
-        for (int a = 0; a < cnt; ++a) cs[slots[a]] = c[a];
+        for (int a = 0; a < cnt; ++a) cs[slots_[a]] = c[a];
         ASCC_CUDA(cudaMemcpyAsync(coef_.p(), cs.data(), m * sizeof(double),
                                   cudaMemcpyHostToDevice, s_));
         k::lincomb(s_, t_.p(), hist_t_.p(), N, coef_.p(), m, N);
         extrapolated = true;
       } else {
-        slots.assign(1, slot);
+        slots_.assign(1, slot);
       }
     }
     if (!extrapolated) k::axpby(s_, t_.p(), tn, 1.0, 0.0, N);
   }
   if (res) {
-    res->energy = e;
-    res->max_resid = rmax;
-    res->iterations = it;
-    res->status = st;
-    res->iterations_low = 0;
+    res->energy = e_last_;
+    res->max_resid = r_last_;
+    res->iterations = iter_;
+    res->status = done_ ? status_ : ASCC_ERR_NOT_CONVERGED;
+    res->iterations_low = iter_low_;
     res->e_ref = 0.0;
   }
-  return st;
+  return done_ ? status_ : ASCC_ERR_NOT_CONVERGED;
+}
+
+ascc_status State::solve(ascc_result* res) {
+  reset();
+  return iterate(opt_.max_iter + 1, res);
+}
+
+void State::profile(double* ladder_ms, int64_t* ladder_launches, double* ladder_flops) {
+  for (auto& ev : events_) {
+    ASCC_CUDA(cudaEventSynchronize(ev.second));
+    float ms = 0.f;
+    ASCC_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
+    ladder_ms_ += ms;
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+  events_.clear();
+  if (ladder_ms) *ladder_ms = ladder_ms_;
+  if (ladder_launches) *ladder_launches = ladder_launches_;
+  if (ladder_flops) *ladder_flops = ladder_flops_;
 }
 
 }  // namespace ascc

@@ -21,9 +21,21 @@ class Einsum {
                   const T& C) const;
   // C = alpha * permute(A) + beta * C, spec "kilj->klij"
   void perm(const char* spec, double alpha, const T& A, double beta, const T& C) const;
+  // level 0: FP64 DFMA GEMM.  level 1..3: unbatched contractions of at least
+  // min_flops run on the BF16 tensor cores with operands split into `level`
+  // BF16 planes (1, 3 or 6 products); err receives kernel timeout codes.
+  void set_split(int level, int* err, double min_flops = 4e7) {
+    level_ = level;
+    err_ = err;
+    min_flops_ = min_flops;
+  }
+  int level() const { return level_; }
 
  private:
   cudaStream_t s_;
+  int level_ = 0;
+  int* err_ = nullptr;
+  double min_flops_ = 4e7;
 };
 
 // Copies a strided box of `in` into `out` (both with explicit strides).
@@ -42,6 +54,8 @@ struct Molecule {
   OT Bvv;    // [naux][v][v]
   OT Bnv;    // [naux][n][v]
   OT Gext;   // [n][v][v][v], Gext[x][b][c][d] = (xc|bd)
+  DevBuf Gext_bf16;  // [3][n v][v^2 padded] BF16 planes of Gext (mixed precision)
+  void make_bf16_planes();
   Molecule(int o, int v, int naux, const double* eps_h, const double* B_src, bool on_device,
            cudaStream_t s);
   size_t bytes() const;
@@ -74,7 +88,18 @@ class State {
   // Residual of packed device amplitudes t -> packed device residual r and
   // device scalar energy.
   void residual(const double* t, double* r, double* energy);
+  // Precision of a stand-alone residual call: FP64, or the polishing split
+  // level in mixed precision.
+  void prepare_eval() { es_.set_split(opt_.precision == ASCC_MIXED_BF16 ? 3 : 0, err_.as<int>()); }
   ascc_status solve(ascc_result* res);
+  // Iteration control: reset() loads the zeroth-order guess and clears the
+  // DIIS history; iterate() runs up to max_steps residual evaluations from
+  // the current amplitudes and history (Sec. III.B).
+  void reset();
+  ascc_status iterate(int max_steps, ascc_result* res);
+  // Profiling of the dense ladder GEMM (CUDA events on the state's stream).
+  void set_profiling(bool on) { profile_ = on; }
+  void profile(double* ladder_ms, int64_t* ladder_launches, double* ladder_flops);
   void initial_guess(std::vector<double>& t) const;
 
   double* amplitudes() { return t_.p(); }
@@ -91,6 +116,18 @@ class State {
 
   std::shared_ptr<Molecule> mol_;
   Options opt_;
+  // iteration state
+  std::vector<int> slots_;
+  std::vector<double> gram_;
+  int next_slot_ = 0, iter_ = 0;
+  bool have_prev_ = false, done_ = false;
+  double e_prev_ = 0.0, e_last_ = 0.0, r_last_ = 0.0;
+  ascc_status status_ = ASCC_ERR_NOT_CONVERGED;
+  // profiling
+  bool profile_ = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events_;
+  double ladder_ms_ = 0.0, ladder_flops_ = 0.0;
+  int64_t ladder_launches_ = 0;
   cudaStream_t s_;
   int o_, v_, n_, naux_;
   int hole_, particle_;  // -1 for the ground state
@@ -104,6 +141,10 @@ class State {
   OT Gh1, Gh2, Gh3, GooP;
   // amplitudes, residual, DIIS
   OT t_, r_, hist_t_, hist_e_, scal_, work_, coef_;
+  DevBuf err_;           // int: device-side timeout codes of the tensor-core GEMM
+  bool polish_ = false;
+  int iter_low_ = 0;
+  int level_for_phase() const;
   // per-iteration workspace
   OT L_, R_, tmpB_, Bhat_, hhat_, tmpnn_, F_, dP_, J_, K_, Boo_, Bov_, Bvo_, Bvv_, Bno_, Bon_;
   OT goooo_, gooov_, goovv_, govov_, gvovo_, gvoov_, gvvoo_, Lvoov_, Lovov_;

@@ -1,0 +1,350 @@
+// Split-precision tensor-core GEMM for sm_103a (tcgen05 + TMA + TMEM).
+//
+//   C (FP64, row-major) = alpha * sum_{(u,w) in segs} A_u B_w^T + beta * C
+//
+// A_u [M][Kp] and B_w [N][Kp] are BF16, K-major (row-major with K
+// contiguous), Kp a multiple of 64.  A FP64 operand x is carried as
+// x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1));
+// the products x0 y0, x0 y1, x1 y0 (, x0 y2, x1 y1, x2 y0) recover 16 (24)
+// significant bits, each product exact in the FP32 accumulator.
+//
+// One CTA computes a 128 x BN tile: warp 0 issues TMA loads into a
+// STAGES-deep shared-memory ring, warp 1 issues tcgen05.mma (M=128, N=BN,
+// K=16) into a TMEM accumulator, and all four warps read TMEM back
+// (tcgen05.ld 32x32b) for the FP64 epilogue.  Every wait is bounded by a
+// 2-second %globaltimer budget; on expiry the kernel records an error code,
+// skips the remaining work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "gemm_tc.h"
+
+namespace ascc {
+namespace tc {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, NTHREADS = 128;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+struct Segs {
+  int n;
+  int a[6];
+  int b[6];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and records code) when the budget runs out.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (gtime() - t0 > WAIT_NS) {
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), start address in 16-byte units.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 x BF16 -> F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
+               const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap b0,
+               const __grid_constant__ CUtensorMap b1, const __grid_constant__ CUtensorMap b2,
+               Segs segs, int M, int N, int num_kt, double alpha, double beta,
+               double* __restrict__ C, long long ldc, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 2);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                 done = smem_u32(bars + 2 * STAGES);
+  __shared__ int abort_flag;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+  const int total = segs.n * num_kt;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    const CUtensorMap* am[3] = {&a0, &a1, &a2};
+    const CUtensorMap* bm[3] = {&b0, &b1, &b2};
+    for (int it = 0; it < total; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err, 1)) {
+        abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      const int seg = it / num_kt, kt = it % num_kt;
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+      tma_load_2d(sa, am[segs.a[seg]], full0 + 8 * s, kt * BK, m0);
+      tma_load_2d(sa + A_BYTES, bm[segs.b[seg]], full0 + 8 * s, kt * BK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int it = 0; it < total; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      if (!mbar_wait(full0 + 8 * s, ph, err, 2)) {
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t ad = sw128_desc(sa + kk * 32);
+        const uint64_t bd = sw128_desc(sa + A_BYTES + kk * 32);
+        mma_bf16(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  // epilogue: TMEM lanes [32 warp, 32 warp + 32) hold rows m0 + 32 warp + lane
+  const bool ok = mbar_wait(done, 0, err, 3);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // tcgen05.ld is warp-collective: take the decision per warp
+  const bool go = __all_sync(0xffffffffu, ok) && !*(volatile int*)&abort_flag;
+  if (go) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(taddr + c0, r);
+      if (row < M) {
+        double* crow = C + (long long)row * ldc;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < N) {
+            const double acc = (double)__uint_as_float(r[j]);
+            crow[col] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * crow[col]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// FP64 [rows][K] (row stride ld) -> nsplit BF16 planes [nsplit][rows][Kp], zero padded.
+__global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double* __restrict__ in,
+                                  long long rows, long long K, long long ld, long long Kp,
+                                  int nsplit) {
+  const long long total = rows * Kp;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / Kp, k = idx % Kp;
+    double x = (k < K) ? in[r * ld + k] : 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+      const __nv_bfloat16 h = __double2bfloat16(x);
+      out[(long long)s * total + idx] = h;
+      x -= (double)__bfloat162float(h);
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  if (!fn) throw Error(ASCC_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  return fn;
+}
+
+CUtensorMap make_map(const __nv_bfloat16* base, int64_t rows, int64_t Kp, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(Kp * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(ASCC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+}  // namespace
+
+int64_t padded_k(int64_t K) { return (K + BK - 1) / BK * BK; }
+
+void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t rows, int64_t K,
+                int64_t ld, int nsplit) {
+  const int64_t Kp = padded_k(K), total = rows * Kp;
+  if (total == 0) return;
+  int64_t g = (total + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  split_bf16_kernel<<<(int)g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit);
+  count_launch();
+  check_launch("split_bf16");
+}
+
+int products_for(int level) { return level == 1 ? 1 : level == 2 ? 3 : 6; }
+
+void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
+                const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C, int64_t ldc,
+                int* err) {
+  ASCC_REQUIRE(level >= 1 && level <= 3, "split level 1..3");
+  ASCC_REQUIRE(M > 0 && N > 0 && K > 0, "gemm_split: empty");
+  static bool attr_set = false;
+  if (!attr_set) {
+    ASCC_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   SMEM_BYTES));
+    attr_set = true;
+  }
+  const int64_t Kp = padded_k(K);
+  CUtensorMap am[3], bm[3];
+  for (int u = 0; u < 3; ++u) {
+    const int uu = u < level ? u : 0;
+    am[u] = make_map(A + (int64_t)uu * M * Kp, M, Kp, BM);
+    bm[u] = make_map(B + (int64_t)uu * N * Kp, N, Kp, BN);
+  }
+  // products with the small planes first (accumulated before the large ones)
+  Segs sg;
+  if (level == 1) {
+    sg = {1, {0}, {0}};
+  } else if (level == 2) {
+    sg = {3, {1, 0, 0}, {0, 1, 0}};
+  } else {
+    sg = {6, {2, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
+  }
+  count_flops(2.0 * (double)M * N * K * sg.n);
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN));
+  ASCC_REQUIRE(grid.y <= 65535, "gemm_split: N too large");
+  gemm_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(am[0], am[1], am[2], bm[0], bm[1], bm[2], sg,
+                                                    (int)M, (int)N, (int)(Kp / BK), alpha, beta, C,
+                                                    (long long)ldc, err);
+  count_launch();
+  check_launch("gemm_tc");
+}
+
+}  // namespace tc
+}  // namespace ascc

@@ -1,0 +1,30 @@
+// Split-precision BF16 tensor-core GEMM (tcgen05/TMA/TMEM) for sm_103a.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.h"
+
+namespace ascc {
+namespace tc {
+
+// Kp: K rounded up to the 64-element K tile of the kernel.
+int64_t padded_k(int64_t K);
+
+// Number of BF16 x BF16 products a split level uses (1, 3 or 6).
+int products_for(int level);
+
+// out[s][r][0..Kp) = s-th BF16 plane of in[r][0..K) (row stride ld), zero
+// padded to Kp; s < nsplit.  x = sum_s plane_s up to the last plane's rounding.
+void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t rows, int64_t K,
+                int64_t ld, int nsplit);
+
+// C[M][N] (FP64, row stride ldc) = alpha * A B^T + beta * C with A [level][M][Kp] and
+// B [level][N][Kp] BF16 planes from split_bf16 (K-major).  err: device int that
+// receives a nonzero code if a bounded wait inside the kernel gives up.
+void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
+                const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C,
+                int64_t ldc, int* err);
+
+}  // namespace tc
+}  // namespace ascc

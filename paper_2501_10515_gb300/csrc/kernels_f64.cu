@@ -7,8 +7,15 @@
 namespace ascc {
 
 static std::atomic<int64_t> g_launches{0};
+static std::atomic<double> g_flops{0.0};
 void count_launch(int64_t n) { g_launches += n; }
 int64_t launch_total() { return g_launches.load(); }
+void count_flops(double f) {
+  double cur = g_flops.load();
+  while (!g_flops.compare_exchange_weak(cur, cur + f)) {
+  }
+}
+double flop_total() { return g_flops.load(); }
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
@@ -331,6 +338,7 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
     else axpby(s, C, C, 0.0, beta, M * N * batch);
     return;
   }
+  count_flops(2.0 * (double)M * (double)N * (double)K * (double)batch);
   dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM), 1);
   for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
     const int64_t nb = std::min<int64_t>(65535, batch - b0);

@@ -1,0 +1,86 @@
+"""Mixed precision: split-BF16 tensor-core GEMM and the ASCC_MIXED_BF16 path.
+
+The GEMM is checked against an FP64 product of the same device operands; the
+mixed-precision solve is checked against the CPU oracle's FP64 solve
+(energy within 1e-6 Eh per result, the bar the method's use sets).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ascc as oracle_ascc
+
+pytestmark = pytest.mark.gpu
+
+# relative error bars of the split levels (16-bit and 24-bit mantissas, FP32 accumulation)
+LEVEL_TOL = {1: 1e-2, 2: 1e-4, 3: 2e-6}
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 300, 100), (128, 256, 64), (400, 2100, 4096),
+                                   (77, 5, 3000)])
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_split_gemm_matches_fp64(M, N, K, level):
+    import torch
+    import paper_2501_10515_gb300 as pkg
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N * 3 + K + level)
+    A = torch.randn(M, K, device="cuda", dtype=torch.float64, generator=g)
+    B = torch.randn(N, K, device="cuda", dtype=torch.float64, generator=g)
+    C0 = torch.randn(M, N, device="cuda", dtype=torch.float64, generator=g)
+    C = C0.clone()
+    pkg.gemm_split_bf16(A, B, C, level, alpha=0.5, beta=-1.0)
+    torch.cuda.synchronize()
+    ref = 0.5 * (A @ B.T) - C0
+    err = (C - ref).abs().max().item()
+    scale = (0.5 * (A.abs() @ B.abs().T)).max().item() + 1.0
+    assert err / scale < LEVEL_TOL[level], (err, scale)
+
+
+def test_split_gemm_levels_improve():
+    import torch
+    import paper_2501_10515_gb300 as pkg
+    g = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randn(256, 1024, device="cuda", dtype=torch.float64, generator=g)
+    B = torch.randn(512, 1024, device="cuda", dtype=torch.float64, generator=g)
+    ref = A @ B.T
+    errs = []
+    for lev in (1, 2, 3):
+        C = torch.zeros(256, 512, device="cuda", dtype=torch.float64)
+        pkg.gemm_split_bf16(A, B, C, lev)
+        torch.cuda.synchronize()
+        errs.append((C - ref).abs().max().item())
+    assert errs[0] > 30 * errs[1] and errs[1] > 10 * errs[2]
+
+
+def _mixed_ctx(s, hole, part, **kw):
+    import paper_2501_10515_gb300 as pkg
+    return pkg.Context(s.o, s.v, s.naux, s.eps, s.B, hole=hole, particle=part,
+                       precision=pkg.ASCC_MIXED_BF16, **kw)
+
+
+@pytest.mark.parametrize("o,v,exc,lin", [(4, 20, (3, 0), True), (4, 20, None, False),
+                                         (6, 40, (5, 1), True), (6, 40, (5, 1), False)])
+def test_mixed_solve_matches_fp64_oracle(o, v, exc, lin):
+    s = synth.make_system(o, v, seed=1)
+    hole, part = exc if exc else (None, None)
+    ctx = _mixed_ctx(s, hole, part, linearize=int(lin),
+                     pl_hole=o - 1 if exc is None else -1, pl_particle=0 if exc is None else -1)
+    res = ctx.solve()
+    ref = oracle_ascc.solve_state(s.eps, s.B, o, hole, part, linearize=lin, pl_hole=o - 1,
+                                  pl_particle=0)
+    assert ref.converged and res.status == 0
+    assert abs(res.energy - ref.energy) < 1e-6, (res.energy, ref.energy)
+    assert res.iterations_low > 0
+
+
+def test_mixed_residual_close_to_oracle():
+    o, v = 6, 40
+    s = synth.make_system(o, v, seed=2)
+    t1, t2, _ = synth.random_amplitudes(o, v, seed=4, scale=0.05)
+    ctx = _mixed_ctx(s, 5, 2, linearize=1)
+    E, r1, r2, _ = ctx.residual(t1, t2)
+    hbar, Bbar, _ = oracle_ascc.prepare(s.eps, s.B, o, 5, 2)
+    from oracle import spinadapted as sa
+    Eo, r1o, r2o, _ = sa.residual(hbar, Bbar, o, t1, t2, linearize=True, hole=5, particle=2)
+    R = np.concatenate([r1.ravel(), r2.ravel()]); Ro = np.concatenate([r1o.ravel(), r2o.ravel()])
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) < 1e-6
+    assert abs(E - Eo) < 1e-7
