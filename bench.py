@@ -143,30 +143,55 @@ def flops_per_residual(o, v, naux, excited=True, linearize=True):
     return f
 
 
+def oracle_iterations(name, default=50):
+    path = os.path.join(ROOT, "tests", "golden", "reference_energies.txt")
+    if os.path.exists(path):
+        for line in open(path):
+            if line.split() and line.split()[0] == name:
+                return int(line.split()[8])
+    return default
+
+
 def run_reference(args, wl):
+    """The CPU oracle as it stands; each step is one oracle residual of the state
+    (a bounded sample of a solve), scaled to solves/s by the oracle's own
+    iteration count for this state."""
     rank, world, _ = rank_env()
     if rank != 0:
         return 0
     cores = len(os.sched_getaffinity(0))
     times = oracle_residual_timer(wl, args.steps, args.warmup)
     naux = 3 * (wl["o"] + wl["v"])
-    fl = flops_per_residual(wl["o"], wl["v"], naux)
-    ms = 1e3 * sum(times) / len(times)
-    value = fl / (sum(times) / len(times)) / 1e12
+    iters = oracle_iterations(f"{args.workload}_plascc_excited")
+    per = sum(times) / len(times)
+    ms = 1e3 * per * iters
+    value = 1.0 / (per * iters)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl["name"], "o": wl["o"], "v": wl["v"], "naux": naux,
                    "excitation": [wl["hole"], wl["particle"]], "method": "PLASCC",
-                   "step": "one oracle residual evaluation at the zeroth-order guess"},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": "one residual evaluation of the same state per step"},
-        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                   "step": "one oracle residual evaluation at the zeroth-order guess",
+                   "iterations_per_solve": iters},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one residual evaluation of the same state per step, x {iters} "
+                                   "iterations (the oracle's own count for this state)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def golden_energy(name):
+    path = os.path.join(ROOT, "tests", "golden", "reference_energies.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.split() and line.split()[0] == name:
+            return float(line.split()[7])
+    return None
 
 
 def main():
@@ -176,7 +201,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--step", default="solve", choices=["solve", "iteration"])
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp64-iterations", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -197,10 +225,21 @@ def main():
     o, v = wl["o"], wl["v"]
     s = synth.make_system(o, v, seed=wl["seed"])
     stream = torch.cuda.current_stream()
+    mixed = args.precision == "mixed"
+    prec = pkg.ASCC_MIXED_BF16 if mixed else pkg.ASCC_FP64
     ctx = pkg.Context(o, v, s.naux, s.eps, s.B, hole=wl["hole"], particle=wl["particle"],
-                      linearize=1, stream=stream.cuda_stream)
-    ctx.reset()
-    ctx.iterate(args.warmup)
+                      linearize=1, stream=stream.cuda_stream, precision=prec)
+
+    def one_unit():
+        if args.step == "solve":
+            ctx.reset()
+            return ctx.iterate(ctx.options.max_iter + 1)
+        return ctx.iterate(1)
+
+    if args.step == "iteration":
+        ctx.reset()
+    for _ in range(args.warmup):
+        one_unit()
     torch.cuda.synchronize()
     ctx.set_profiling(True)
     p0 = ctx.profile()
@@ -209,73 +248,118 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    res = ctx.iterate(args.steps)
-    ev1.record(stream)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    results = []
+    evs[0].record(stream)
+    for k in range(args.steps):
+        results.append(one_unit())
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
     ctx.set_profiling(False)
     p1 = ctx.profile()
-    ms = ev0.elapsed_time(ev1)
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    ms = sum(per)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    flops_step = (p1.gemm_flops - p0.gemm_flops) / args.steps
-    value = world * flops_step * args.steps / (ms / 1e3) / 1e12
-    launches = int(p1.launches - p0.launches)
-    lad_ms = (p1.ladder_ms - p0.ladder_ms) / max(1, p1.ladder_launches - p0.ladder_launches)
-    lad_fl = (p1.ladder_flops - p0.ladder_flops) / max(1, p1.ladder_launches - p0.ladder_launches)
+    units = world * args.steps
+    flops = p1.gemm_flops - p0.gemm_flops
+    tflops = world * flops / (ms / 1e3) / 1e12
+    nlad = max(1, p1.ladder_launches - p0.ladder_launches)
+    lad_ms = (p1.ladder_ms - p0.ladder_ms) / nlad
+    lad_fl = (p1.ladder_flops - p0.ladder_flops) / nlad
     achieved = lad_fl / (lad_ms / 1e3) / 1e12
+    if mixed:
+        peak, bound, unit_note = 1977.2, "tensor", "BF16 dense burst, measured (MEASURED_PEAKS.json)"
+    else:
+        peak, bound, unit_note = FP64_NOMINAL_TFLOPS, "alu", "nominal FP64 rate of the recipe table"
+    last = results[-1]
+    iters = last.iterations
+    value = units / (ms / 1e3) if args.step == "solve" else tflops
+    unit = "solves/s" if args.step == "solve" else "TFLOP/s"
+    ref_e = golden_energy(f"{args.workload}_plascc_excited")
 
-    # end to end through the host-buffer call (copies inside the timed region)
-    pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
-    t1h, t2h, _ = ctx.get_state()
-    t1p, t2p = pin(t1h.shape), pin(t2h.shape)
-    t1p[...] = t1h; t2p[...] = t2h
-    ctx.residual(t1p, t2p)
+    # end to end: one solve request through the host-buffer C ABI (context
+    # creation from host eps/B, integral setup, solve, energy back to host)
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    eps_p, B_p = pin(s.eps), pin(s.B)
     torch.cuda.synchronize()
-    f0 = ctx.profile().gemm_flops
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        E, r1, r2, _ = ctx.residual(t1p, t2p)
+        c2 = pkg.Context(o, v, s.naux, eps_p, B_p, hole=wl["hole"], particle=wl["particle"],
+                         linearize=1, precision=prec)
+        r2 = c2.solve()
+        e2e_energy = r2.energy
+        c2.close()
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    e2e_fl = (ctx.profile().gemm_flops - f0) / args.e2e_steps
-    bytes_in = t1p.nbytes + t2p.nbytes
-    bytes_out = r1.nbytes + r2.nbytes + 8
+
+    # the plain FP64 path on the same state: a few iterations, for the comparison
+    fp64 = None
+    if mixed and args.fp64_iterations > 0 and args.step == "solve":
+        cf = pkg.Context(o, v, s.naux, None, None, hole=wl["hole"], particle=wl["particle"],
+                         base=ctx, linearize=1, stream=stream.cuda_stream, precision=pkg.ASCC_FP64)
+        cf.reset()
+        cf.iterate(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cf.iterate(args.fp64_iterations)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1) / args.fp64_iterations
+        fp64 = {"ms_per_iteration": fms, "solve_s_estimate": fms * iters / 1e3,
+                "solves_per_s_estimate": 1e3 / (fms * iters),
+                "note": "FP64 time per iteration measured on this state; x the mixed solve's iterations"}
+        cf.close()
 
     line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3-split/f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "o": o, "v": v, "naux": s.naux,
                    "excitation": [wl["hole"], wl["particle"]], "method": "PLASCC",
-                   "precision": "fp64", "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2: the 14 GB (xc|bd) block is streamed every step",
-                   "step": "one solve iteration (residual + convergence test + Jacobi + DIIS)"},
+                   "precision": args.precision, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2: the (xc|bd) block (10.6 GB BF16 / 14 GB FP64) is streamed every iteration",
+                   "step": ("one complete solve from the zeroth-order guess to max|R| <= 1e-8, |dE| <= 1e-10"
+                            if args.step == "solve" else
+                            "one solve iteration (residual + convergence test + Jacobi + DIIS)")},
         "clocks": clocks,
-        "e2e": {"value": e2e_fl / e2e_s / 1e12, "unit": "TFLOP/s",
-                "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out},
-        "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
-                     "kernel": "gemm_f64 (dense particle-particle ladder)",
-                     "peak_source": "nominal FP64 rate of the recipe table (no measured FP64 peak)"},
-        "iteration_energy": res.energy, "iteration_max_resid": res.max_resid,
-        "flops_per_step": flops_step, "flops_per_step_model": flops_per_residual(o, v, s.naux),
+        "e2e": {"value": (1.0 / e2e_s) if args.step == "solve" else None,
+                "unit": "solves/s",
+                "h2d_bytes_per_step": int(eps_p.nbytes + B_p.nbytes), "d2h_bytes_per_step": 56},
+        "gpu_launches": int(p1.launches - p0.launches),
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": ("gemm_tc_kernel" if mixed else "gemm_f64_kernel") +
+                               " (dense particle-particle ladder launch)",
+                     "peak_source": unit_note},
+        "residual_tflops": tflops,
+        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+        "iterations": iters, "iterations_low_precision": last.iterations_low,
+        "status": int(last.status), "energy": last.energy,
+        "energy_error_vs_oracle": (abs(last.energy - ref_e) if ref_e is not None else None),
+        "e2e_energy": e2e_energy,
+        "fp64_path": fp64,
     }
     if rank == 0 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0))
         times = oracle_residual_timer(wl, 1, 0)
-        line["cpu_baseline"] = {"value": flops_step / times[0] / 1e12, "unit": "TFLOP/s",
-                                "cores": cores, "kind": "oracle",
-                                "sample": "one oracle residual evaluation of the same state "
-                                          "(flops counted as the GPU step's)"}
+        fl = flops_per_residual(o, v, s.naux)
+        ores = times[0]
+        cb = {"cores": cores, "kind": "oracle",
+              "sample": "one oracle residual evaluation of the same state; "
+                        "scaled by the solve's iteration count"}
+        if args.step == "solve":
+            cb.update(value=1.0 / (ores * iters), unit="solves/s")
+        else:
+            cb.update(value=fl / ores / 1e12, unit="TFLOP/s")
+        cb["seconds_per_residual"] = ores
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

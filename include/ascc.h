@@ -75,7 +75,7 @@ typedef struct {
   double r_tol;        /* convergence: max |R| <= r_tol ...                     */
   double e_tol;        /*   ... and |E - E_prev| <= e_tol (Sec. III.A)          */
   int32_t max_iter;    /* iteration cap                                         */
-  int32_t diis_dim;    /* DIIS history length (<= 16)                           */
+  int32_t diis_dim;    /* DIIS history length (<= 32)                           */
   int32_t diis_start;  /* pairs needed before extrapolating                     */
   int32_t polish_iter; /* mixed precision: FP64 iterations after the low-      */
                        /*   precision phase converges to polish_tol            */
@@ -92,8 +92,8 @@ typedef struct {
   int32_t reserved;
 } ascc_result;
 
-/* Fills *opt with defaults: FP64, PLASCC, triples on, r_tol 1e-8, e_tol 1e-10,
- * max_iter 200, DIIS 8 / start 3, polish 1e-6.  Returns ASCC_OK. */
+/* Fills *opt with defaults: FP64, PLASCC, triples off, r_tol 1e-8, e_tol 1e-10,
+ * max_iter 200, DIIS 16 / start 3, polish 1e-6.  Returns ASCC_OK. */
 ascc_status ascc_default_options(ascc_options* opt);
 
 /* Creates a context for one state of one molecule (Secs. II.A-II.B).

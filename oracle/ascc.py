@@ -23,7 +23,7 @@ def prepare(eps, B, o, hole=None, particle=None):
 
 def solve_state(eps, B, o, hole=None, particle=None, linearize=True, triples=False,
                 pl_hole=None, pl_particle=None, beta=1.0, r_tol=1e-8, e_tol=1e-10,
-                max_iter=200, diis_dim=8, diis_start=3, verbose=False):
+                max_iter=200, diis_dim=16, diis_start=3, verbose=False):
     v = len(eps) - o
     hbar, Bbar, _ = prepare(eps, B, o, hole, particle)
     lh, lp = (hole, particle) if hole is not None else (pl_hole, pl_particle)
@@ -39,5 +39,5 @@ def solve_state(eps, B, o, hole=None, particle=None, linearize=True, triples=Fal
 
     res = solver.solve(fn, eps, o, t1, t2, t3, t3_idx=idx, r_tol=r_tol, e_tol=e_tol,
                        max_iter=max_iter, diis_dim=diis_dim, diis_start=diis_start,
-                       verbose=verbose)
+                       verbose=verbose, hole=hole, particle=particle)
     return res

@@ -6,12 +6,18 @@ residual and the energy change fall below thresholds (Sec. III.A).  The
 paper does not spell out the DIIS details; the rules below are the ones this
 project fixes, and the CUDA solver follows the same rules:
 
-* denominators from the bare orbital energies:
+* denominators from orbital energies:
     D1[i,a] = e_i - e_a,  D2[i,j,a,b] = e_i + e_j - e_a - e_b,
-    D3[i,j,k,a,b,c] = e_i + e_j + e_k - e_a - e_b - e_c;
+    D3[i,j,k,a,b,c] = e_i + e_j + e_k - e_a - e_b - e_c,
+  with the bare e for the ground state and for the primary (P) amplitudes of
+  a one-CSF state; for its other amplitudes both primary orbitals take the
+  mean (e_h + e_p)/2.  In the excited reference S phi0 the hole and the
+  particle are each half occupied, and this zeroth-order diagonal matches the
+  measured diagonal of the Jacobian of the mixed amplitudes (for the P
+  amplitudes it would vanish, so they keep the bare values);
 * Jacobi step t' = t + R / D;
 * DIIS over the vector (t1, t2, t3'): the error is e = t' - t, the history
-  keeps the last `diis_dim` pairs (t', e); once it holds `diis_start` pairs
+  keeps the last `diis_dim` (default 16) pairs (t', e); once it holds `diis_start` pairs
   the new amplitudes are sum_k c_k t'_k with c solving the bordered system
   [[G, 1], [1, 0]] [c; l] = [0; 1], G_kl = e_k . e_l scaled by 1/max diag G
   plus a 1e-12 ridge, solved by Gaussian elimination with partial pivoting;
@@ -69,7 +75,7 @@ def bordered_solve(G: np.ndarray):
     return x[:m]
 
 
-def denominators(eps, o, t3_idx=None):
+def _raw_denominators(eps, o, t3_idx):
     eo, ev = eps[:o], eps[o:]
     D1 = eo[:, None] - ev[None, :]
     D2 = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
@@ -81,10 +87,30 @@ def denominators(eps, o, t3_idx=None):
     return D1, D2, D3
 
 
+def denominators(eps, o, t3_idx=None, hole=None, particle=None):
+    D1, D2, D3 = _raw_denominators(eps, o, t3_idx)
+    if hole is None:
+        return D1, D2, D3
+    from .amplitudes import t1_class_masks, t2_class_masks
+    v = len(eps) - o
+    e = np.array(eps, dtype=float)
+    m = 0.5 * (e[hole] + e[o + particle])
+    e[hole] = m
+    e[o + particle] = m
+    E1, E2, E3 = _raw_denominators(e, o, t3_idx)
+    P1, _, _ = t1_class_masks(o, v, hole, particle)
+    P2, _, _ = t2_class_masks(o, v, hole, particle)
+    return np.where(P1, D1, E1), np.where(P2, D2, E2), E3
+
+
 def solve(resid_fn, eps, o, t1, t2, t3, t3_idx=None, r_tol=1e-8, e_tol=1e-10,
-          max_iter=200, diis_dim=8, diis_start=3, verbose=False):
-    """Iterate resid_fn(t1, t2, t3) -> (E, R1, R2, R3) to convergence."""
-    D1, D2, D3 = denominators(eps, o, t3_idx)
+          max_iter=200, diis_dim=16, diis_start=3, verbose=False, hole=None, particle=None):
+    """Iterate resid_fn(t1, t2, t3) -> (E, R1, R2, R3) to convergence.
+
+    hole/particle: the primary orbitals of a one-CSF state (None for the
+    ground state), which select the denominators described above.
+    """
+    D1, D2, D3 = denominators(eps, o, t3_idx, hole, particle)
     shapes = [t1.shape, t2.shape, t3.shape]
     sizes = [t1.size, t2.size, t3.size]
 

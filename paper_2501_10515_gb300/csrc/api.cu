@@ -25,6 +25,11 @@ struct ascc_ctx {
 
 namespace {
 thread_local std::string g_err;
+}  // namespace
+
+void ascc::record_error(const std::string& msg) { g_err = msg; }
+
+namespace {
 
 template <class F>
 ascc_status guard(F&& f) {
@@ -115,7 +120,7 @@ ascc_status ascc_default_options(ascc_options* opt) {
   opt->r_tol = 1e-8;
   opt->e_tol = 1e-10;
   opt->max_iter = 200;
-  opt->diis_dim = 8;
+  opt->diis_dim = 16;
   opt->diis_start = 3;
   opt->polish_iter = 50;
   opt->polish_tol = 1e-6;
@@ -137,7 +142,8 @@ ascc_status ascc_create(ascc_ctx** out, int32_t o, int32_t v, int32_t naux, cons
       own = true;
     }
     try {
-      auto mol = std::make_shared<Molecule>(o, v, naux, eps, B, b_on_device != 0, s);
+      const int build_level = (opt && opt->precision == ASCC_MIXED_BF16) ? 3 : 0;
+      auto mol = std::make_shared<Molecule>(o, v, naux, eps, B, b_on_device != 0, s, build_level);
       return make_ctx(out, std::move(mol), exc, opt, s, own);
     } catch (...) {
       if (own) {

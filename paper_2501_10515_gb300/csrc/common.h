@@ -44,6 +44,8 @@ int64_t launch_total();
 void count_flops(double f);
 double flop_total();
 void check_launch(const char* what);
+// Stores the message returned by ascc_last_error() on this thread.
+void record_error(const std::string& msg);
 
 // Stream-ordered device buffer.
 class DevBuf {

@@ -190,8 +190,10 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
 
 // ---------------------------------------------------------------- Molecule
 Molecule::Molecule(int o_, int v_, int naux_, const double* eps_h, const double* B_src,
-                   bool on_device, cudaStream_t s)
+                   bool on_device, cudaStream_t s, int build_level)
     : o(o_), v(v_), n(o_ + v_), naux(naux_), stream(s) {
+  err.alloc(sizeof(int), s);
+  err.zero();
   eps_host.assign(eps_h, eps_h + n);
   eps.make({n}, s);
   ASCC_CUDA(cudaMemcpyAsync(eps.p(), eps_h, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -219,7 +221,12 @@ Molecule::Molecule(int o_, int v_, int naux_, const double* eps_h, const double*
   box_copy(s, Bnv.p(), {(int64_t)n * v, v, 1}, B.p() + o, {(int64_t)n * n, n, 1}, {naux, n, v});
   // Gext[x][b][c][d] = (xc|bd) = sum_P B[P][x][o+c] B[P][o+b][o+d]
   Gext.make({n, v, v, v}, s);
+  es.set_split(build_level, err.as<int>(), 0.0);
   es("Pxc,Pbd->xbcd", 1.0, Bnv.t, Bvv.t, 0.0, Gext.t);
+  int h = 0;
+  ASCC_CUDA(cudaMemcpyAsync(&h, err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  ASCC_CUDA(cudaStreamSynchronize(s));
+  if (h) throw Error(ASCC_ERR_TIMEOUT, "tensor-core GEMM wait timed out while building (xc|bd)");
 }
 
 void Molecule::make_bf16_planes() {
@@ -274,7 +281,7 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   if (lh_ < 0) opt_.linearize = 0;
   ASCC_REQUIRE(opt_.precision == ASCC_FP64 || opt_.precision == ASCC_MIXED_BF16,
                "precision must be ASCC_FP64 or ASCC_MIXED_BF16");
-  ASCC_REQUIRE(opt_.diis_dim >= 1 && opt_.diis_dim <= 16, "diis_dim in 1..16");
+  ASCC_REQUIRE(opt_.diis_dim >= 1 && opt_.diis_dim <= 32, "diis_dim in 1..32");
   if (opt_.triples && hole_ >= 0) {
     t3idx_host_ = t3p_index(o_, v_, hole_, particle_);
     ASCC_REQUIRE(n3() == 0, "the T3' slice is not available in this build");
@@ -286,8 +293,8 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   hist_t_.make({opt_.diis_dim, N}, s);
   hist_e_.make({opt_.diis_dim, N}, s);
   scal_.make({64}, s);
-  work_.make({(int64_t)16 * 4 * 152 + 64}, s);
-  coef_.make({16}, s);
+  work_.make({(int64_t)32 * 4 * 152 + 64}, s);
+  coef_.make({32}, s);
   const int o = o_, v = v_, n = n_, P = naux_;
   L_.make({n, n}, s); R_.make({n, n}, s);
   tmpB_.make({P, n, n}, s); Bhat_.make({P, n, n}, s);
@@ -309,6 +316,19 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   }
   err_.alloc(sizeof(int), s);
   err_.zero();
+  {
+    // Jacobi denominators: the hole and particle of a one-CSF state are half
+    // occupied in S phi0; their mean energy enters the non-primary amplitudes.
+    std::vector<double> ee = mol_->eps_host;
+    if (hole_ >= 0) {
+      const double m = 0.5 * (ee[hole_] + ee[o_ + particle_]);
+      ee[hole_] = m;
+      ee[o_ + particle_] = m;
+    }
+    eps_eff_.make({n_}, s);
+    ASCC_CUDA(cudaMemcpyAsync(eps_eff_.p(), ee.data(), sizeof(double) * n_, cudaMemcpyHostToDevice, s));
+    ASCC_CUDA(cudaStreamSynchronize(s));
+  }
   if (opt_.precision == ASCC_MIXED_BF16) {
     ASCC_CUDA(cudaStreamSynchronize(mol_->stream));
     mol_->make_bf16_planes();
@@ -387,15 +407,20 @@ void State::dress(const double* t1) {
   box_copy(s_, Bvv_.p(), {(int64_t)v * v, v, 1}, Bhat_.p() + (int64_t)o * n + o, bs, {P, v, v});
   box_copy(s_, Bno_.p(), {(int64_t)n * o, o, 1}, Bhat_.p(), bs, {P, n, o});
   box_copy(s_, Bon_.p(), {(int64_t)o * n, n, 1}, Bhat_.p(), bs, {P, o, n});
-  // Fock matrix of H-hat: F = h + 2 J - K
+  // Fock matrix of H-hat: F = h + 2 J - K.  F enters R1 and R2 with O(1)
+  // weight, so it (and the oooo block of the reference energy) stays FP64 in
+  // every precision mode.
+  const int lev = es_.level();
+  es_.set_split(0, err_.as<int>());
   k::diag_sum(s_, dP_.p(), Bhat_.p(), P, n, o);
   es_("Ppq,P->pq", 1.0, Bhat_.t, dP_.t, 0.0, J_.t);
   es_("Ppk,Pkq->pq", 1.0, Bno_.t, Bon_.t, 0.0, K_.t);
+  es_("Pij,Pkl->ijkl", 1.0, Boo_.t, Boo_.t, 0.0, goooo_.t);
+  es_.set_split(lev, err_.as<int>());
   k::axpby(s_, F_.p(), hhat_.p(), 1.0, 0.0, nn);
   k::axpby(s_, F_.p(), J_.p(), 2.0, 1.0, nn);
   k::axpby(s_, F_.p(), K_.p(), -1.0, 1.0, nn);
   // integral blocks (pq|rs)-hat = sum_P B-hat[P][p][q] B-hat[P][r][s]
-  es_("Pij,Pkl->ijkl", 1.0, Boo_.t, Boo_.t, 0.0, goooo_.t);
   es_("Pij,Pka->ijka", 1.0, Boo_.t, Bov_.t, 0.0, gooov_.t);
   es_("Pij,Pab->ijab", 1.0, Boo_.t, Bvv_.t, 0.0, goovv_.t);
   es_("Pia,Pjb->iajb", 1.0, Bov_.t, Bov_.t, 0.0, govov_.t);
@@ -685,11 +710,11 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     slots_.push_back(slot);
     double* tn = hist_t_.p() + (int64_t)slot * N;
     double* en = hist_e_.p() + (int64_t)slot * N;
-    k::jacobi(s_, tn, en, t_.p(), r_.p(), mol_->eps.p(), o_, v_,
+    k::jacobi(s_, tn, en, t_.p(), r_.p(), mol_->eps.p(), eps_eff_.p(), o_, v_, hole_, particle_,
               n3() ? reinterpret_cast<const int32_t*>(t3idx_.p()) : nullptr, n3());
-    k::dot_rows(s_, en, hist_e_.p(), N, m, N, scal_.p() + 16, work_.p());
+    k::dot_rows(s_, en, hist_e_.p(), N, m, N, scal_.p() + 32, work_.p());
     std::vector<double> row(m);
-    ASCC_CUDA(cudaMemcpyAsync(row.data(), scal_.p() + 16, m * sizeof(double),
+    ASCC_CUDA(cudaMemcpyAsync(row.data(), scal_.p() + 32, m * sizeof(double),
                               cudaMemcpyDeviceToHost, s_));
     ASCC_CUDA(cudaStreamSynchronize(s_));
     for (int q : slots_) {

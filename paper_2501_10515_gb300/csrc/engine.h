@@ -56,8 +56,11 @@ struct Molecule {
   OT Gext;   // [n][v][v][v], Gext[x][b][c][d] = (xc|bd)
   DevBuf Gext_bf16;  // [3][n v][v^2 padded] BF16 planes of Gext (mixed precision)
   void make_bf16_planes();
+  // build_level 0 builds the bare integrals in FP64; 1..3 on the BF16 tensor
+  // cores with that split level (used when the first state is mixed precision).
   Molecule(int o, int v, int naux, const double* eps_h, const double* B_src, bool on_device,
-           cudaStream_t s);
+           cudaStream_t s, int build_level = 0);
+  DevBuf err;  // int: timeout codes of tensor-core launches made for the molecule
   size_t bytes() const;
 };
 
@@ -67,7 +70,7 @@ struct Options {
   int triples = 0;
   int pl_hole = -1, pl_particle = -1;
   double r_tol = 1e-8, e_tol = 1e-10;
-  int max_iter = 200, diis_dim = 8, diis_start = 3;
+  int max_iter = 200, diis_dim = 16, diis_start = 3;
   int polish_iter = 50;
   double polish_tol = 1e-6;
 };
@@ -140,7 +143,7 @@ class State {
   // per-state constant integrals of the ladder corrections
   OT Gh1, Gh2, Gh3, GooP;
   // amplitudes, residual, DIIS
-  OT t_, r_, hist_t_, hist_e_, scal_, work_, coef_;
+  OT t_, r_, hist_t_, hist_e_, scal_, work_, coef_, eps_eff_;
   DevBuf err_;           // int: device-side timeout codes of the tensor-core GEMM
   bool polish_ = false;
   int iter_low_ = 0;

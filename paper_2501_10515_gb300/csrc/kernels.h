@@ -43,11 +43,12 @@ void tilde(cudaStream_t s, double* u, const double* t, int o, int v);
 void mixed_mask(cudaStream_t s, double* m, const double* t, int o, int v,
                 int hole, int particle);
 
-// Jacobi step (Sec. III.B): tn = t + r / D with bare-eps denominators and
-// e = tn - t, over the packed vector [t1 | t2 | t3'].
+// Jacobi step (Sec. III.B): tn = t + r / D and e = tn - t over the packed
+// vector [t1 | t2 | t3'].  D uses eps for the primary amplitudes of a one-CSF
+// state (hole >= 0) and eps_eff (h and p at their mean) for the others.
 void jacobi(cudaStream_t s, double* tn, double* e, const double* t,
-            const double* r, const double* eps, int o, int v,
-            const int32_t* t3idx, int64_t n3);
+            const double* r, const double* eps, const double* eps_eff, int o,
+            int v, int hole, int particle, const int32_t* t3idx, int64_t n3);
 
 // d[P] = sum_k B[P][k][k]
 void diag_sum(cudaStream_t s, double* d, const double* B, int naux, int n, int o);

@@ -267,26 +267,33 @@ __global__ void mixed_mask_kernel(double* m, const double* t, int o, int v, int 
   }
 }
 
+// Denominators: bare eps for the primary amplitudes (every index h or p) of a
+// one-CSF state and for the ground state; eps_eff (h and p at their mean) for
+// all other amplitudes of a one-CSF state.
 __global__ void jacobi_kernel(double* tn, double* e, const double* t, const double* r,
-                              const double* eps, int o, int v, const int32_t* t3idx,
-                              int64_t n3) {
+                              const double* eps, const double* eps_eff, int o, int v, int hole,
+                              int particle, const int32_t* t3idx, int64_t n3) {
   const int64_t n1 = (int64_t)o * v, n2 = n1 * n1, total = n1 + n2 + n3;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     double D;
     if (idx < n1) {
       const int i = (int)(idx / v), a = (int)(idx % v);
-      D = eps[i] - eps[o + a];
+      const double* ee = (i == hole && a == particle) ? eps : eps_eff;
+      D = ee[i] - ee[o + a];
     } else if (idx < n1 + n2) {
       int64_t q = idx - n1;
       const int b = (int)(q % v); q /= v;
       const int a = (int)(q % v); q /= v;
       const int j = (int)(q % o); q /= o;
       const int i = (int)q;
-      D = eps[i] + eps[j] - eps[o + a] - eps[o + b];
+      const bool prim = i == hole && j == hole && a == particle && b == particle;
+      const double* ee = prim ? eps : eps_eff;
+      D = ee[i] + ee[j] - ee[o + a] - ee[o + b];
     } else {
       const int32_t* ix = t3idx + 6 * (idx - n1 - n2);
-      D = eps[ix[0]] + eps[ix[1]] + eps[ix[2]] - eps[o + ix[3]] - eps[o + ix[4]] - eps[o + ix[5]];
+      D = eps_eff[ix[0]] + eps_eff[ix[1]] + eps_eff[ix[2]] - eps_eff[o + ix[3]] -
+          eps_eff[o + ix[4]] - eps_eff[o + ix[5]];
     }
     const double step = r[idx] / D;
     tn[idx] = t[idx] + step;
@@ -437,9 +444,11 @@ void mixed_mask(cudaStream_t s, double* m, const double* t, int o, int v, int ho
 }
 
 void jacobi(cudaStream_t s, double* tn, double* e, const double* t, const double* r,
-            const double* eps, int o, int v, const int32_t* t3idx, int64_t n3) {
+            const double* eps, const double* eps_eff, int o, int v, int hole, int particle,
+            const int32_t* t3idx, int64_t n3) {
   const int64_t total = (int64_t)o * v + (int64_t)o * o * v * v + n3;
-  jacobi_kernel<<<grid_for(total), 256, 0, s>>>(tn, e, t, r, eps, o, v, t3idx, n3);
+  jacobi_kernel<<<grid_for(total), 256, 0, s>>>(tn, e, t, r, eps, eps_eff, o, v, hole, particle,
+                                                t3idx, n3);
   count_launch();
   check_launch("jacobi");
 }

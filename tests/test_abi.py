@@ -24,7 +24,7 @@ def test_status_strings_and_defaults(lib):
     assert lib.ascc_status_string(4) == b"not converged"
     opt = binding.default_options()
     assert opt.precision == binding.ASCC_FP64 and opt.linearize == 1
-    assert opt.r_tol == 1e-8 and opt.e_tol == 1e-10 and opt.diis_dim == 8
+    assert opt.r_tol == 1e-8 and opt.e_tol == 1e-10 and opt.diis_dim == 16
 
 
 def test_footprint_grows_with_size(lib):
