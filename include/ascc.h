@@ -189,6 +189,29 @@ ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level,
                                  double alpha, const double* A, const double* B,
                                  double beta, double* C, void* stream);
 
+/* The same product as ascc_gemm_split_bf16, for callers that cannot
+ * allocate device memory when they need it: work recorded inside a CUDA
+ * stream capture that must not gain allocation nodes, latency-critical loops
+ * where an allocator call may synchronise the device, or processes whose
+ * device memory has all been handed to another pool.  This entry point calls
+ * no cudaMalloc/cudaFree and no allocating library routine: the BF16 operand
+ * planes live in a fixed 32 MiB device array per GPU (held by every GPU that
+ * loads the library until the process exits).  The paper has no counterpart;
+ * it is a property of this library's tensor-core GEMM.
+ *   Limit: 2 * level * (M + N) * ceil(K / 64) * 64 bytes must not exceed
+ *   32 MiB; larger requests return ASCC_ERR_INVALID without touching the GPU.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   Each call first synchronises `stream` to report a timeout of the
+ *   previous call (ASCC_ERR_TIMEOUT) and clears the flag.
+ *   All calls share the array, which keeps the last call's contents: calls
+ *   that overlap on the GPU (different streams, or issued while an earlier
+ *   one is still running elsewhere) race on it. */
+ascc_status ascc_gemm_split_bf16_noalloc(int64_t M, int64_t N, int64_t K,
+                                         int32_t level, double alpha,
+                                         const double* A, const double* B,
+                                         double beta, double* C, void* stream);
+
 /* Checkpoint / resume of the amplitudes (host buffers, FP64). */
 ascc_status ascc_get_state(ascc_ctx* ctx, double* t1, double* t2, double* t3p);
 ascc_status ascc_set_state(ascc_ctx* ctx, const double* t1, const double* t2,

@@ -6,8 +6,9 @@ not load the library; `load()` (called by the first Context) does, and fails
 loudly when libascc.so has not been built.
 """
 from .binding import (ASCC_FP64, ASCC_MIXED_BF16, AsccError, Context, Excitation,
-                      Options, Profile, Result, default_options, gemm_split_bf16, load,
+                      Options, Profile, Result, default_options, gemm_split_bf16,
+                      gemm_split_bf16_noalloc, load,
                       symbols)
 
 __all__ = ["ASCC_FP64", "ASCC_MIXED_BF16", "AsccError", "Context", "Excitation",
-           "Options", "Profile", "Result", "default_options", "gemm_split_bf16", "load", "symbols"]
+           "Options", "Profile", "Result", "default_options", "gemm_split_bf16", "gemm_split_bf16_noalloc", "load", "symbols"]

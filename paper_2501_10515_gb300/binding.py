@@ -79,6 +79,8 @@ def load():
         "ascc_get_profile": (C.c_int, [vp, P(Profile)]),
         "ascc_gemm_split_bf16": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_double,
                                            vp, vp, C.c_double, vp, vp]),
+        "ascc_gemm_split_bf16_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                                   C.c_double, vp, vp, C.c_double, vp, vp]),
         "ascc_get_state": (C.c_int, [vp, dp, dp, dp]),
         "ascc_set_state": (C.c_int, [vp, dp, dp, dp]),
         "ascc_footprint_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, P(Options)]),
@@ -113,6 +115,16 @@ def gemm_split_bf16(A, B, out, level, alpha=1.0, beta=0.0, stream=None):
     assert tuple(out.shape) == (M, N) and B.shape[1] == K
     _check(load().ascc_gemm_split_bf16(M, N, K, level, alpha, C_void(A), C_void(B), beta,
                                        C_void(out), C.c_void_p(stream) if stream else None))
+
+
+def gemm_split_bf16_noalloc(A, B, out, level, alpha=1.0, beta=0.0, stream=None):
+    """As gemm_split_bf16, with the operand planes in the library's fixed device
+    scratch instead of newly allocated memory (see ascc_gemm_split_bf16_noalloc)."""
+    M, K = A.shape
+    N = B.shape[0]
+    assert tuple(out.shape) == (M, N) and B.shape[1] == K
+    _check(load().ascc_gemm_split_bf16_noalloc(M, N, K, level, alpha, C_void(A), C_void(B), beta,
+                                               C_void(out), C.c_void_p(stream) if stream else None))
 
 
 def C_void(x):
