@@ -31,6 +31,8 @@ import numpy as np  # noqa: E402
 
 METRIC = ("ASCC solves/sec & residual TFLOP/s vs plain FP64 at 1e-6 Eh; "
           "p50/p99 latency")
+SERVE_NOTE = ("scaled-down serving trace: o log-uniform [5,20], v log-uniform [50,160], 1-4 "
+              "excited states per molecule plus its ground state, Poisson arrivals")
 WORKLOADS = {
     "c2": dict(o=20, v=200, seed=0, hole=19, particle=3,
                name="ascc-fp64 o=20 v=200 naux=660 excitation 19->3 (PLASCC)"),
@@ -194,20 +196,85 @@ def golden_energy(name):
     return None
 
 
+def run_server_workload(args, kind):
+    """Batched (64 molecules) or streamed (Poisson arrivals) solves through ascc_server."""
+    import torch
+    import synth
+    import paper_2501_10515_gb300 as pkg
+    torch.cuda.set_device(0)
+    prec = pkg.ASCC_MIXED_BF16 if args.precision == "mixed" else pkg.ASCC_FP64
+    if kind == "batch":
+        reqs = []
+        for w in synth.batch_workload(args.requests or 64):
+            reqs.append(dict(o=w["o"], v=w["v"], seed=w["seed"], arrival=0.0,
+                             states=[None] + list(w["excitations"])))
+    else:
+        trace = synth.serving_trace(args.requests or 40, seed=12345, rate=args.rate,
+                                    o_range=(5, 20), v_range=(50, 160))
+        reqs = [dict(o=r["o"], v=r["v"], seed=r["seed"], arrival=r["arrival"],
+                     states=[None] + [(r["o"] - 1 - k % 2, k // 2) for k in range(len(r["excitations"]))])
+                for r in trace]
+    srv = pkg.Server(int(args.budget_gb * (1 << 30)), max_active=args.workers, precision=prec)
+    t0 = time.perf_counter()
+    sub = {}
+    for q, r in enumerate(reqs):
+        if kind == "serve":
+            dt = r["arrival"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+        s = synth.make_system(r["o"], r["v"], seed=r["seed"])
+        rid = srv.submit(r["o"], r["v"], s.naux, s.eps, s.B, r["states"])
+        sub[rid] = q
+    srv.drain()
+    wall = time.perf_counter() - t0
+    res = srv.results()
+    srv.close()
+    per_req = {}
+    for x in res:
+        a = per_req.setdefault(x["request_id"], [x["t_arrival"], x["t_end"], 0, 0])
+        a[1] = max(a[1], x["t_end"])
+        a[2] += 1
+        a[3] += int(x["status"] == 0)
+    lat = np.array([b - a for a, b, _, _ in per_req.values()])
+    solves = sum(v[2] for v in per_req.values())
+    ok = sum(v[3] for v in per_req.values())
+    line = {
+        "metric": METRIC, "value": ok / wall, "unit": "solves/s", "n_gpus": 1,
+        "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * wall / max(1, len(reqs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3-split/f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": ("batched launch of 64 independent molecules, o in [4,16], v in "
+                                "[40,160], 1-3 excitations each plus the ground state"
+                                if kind == "batch" else SERVE_NOTE),
+                   "workers": args.workers, "memory_budget_gb": args.budget_gb,
+                   "arrival_rate_per_s": args.rate if kind == "serve" else None},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "requests": len(reqs), "states": solves, "converged_states": ok, "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--step", default="solve", choices=["solve", "iteration"])
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-iterations", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=0)
+    ap.add_argument("--rate", type=float, default=1.0)
+    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=180.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload in ("batch", "serve"):
+        return run_server_workload(args, args.workload)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)

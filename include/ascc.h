@@ -63,7 +63,12 @@ typedef struct {
   int32_t hole;      /* occupied index h in [0, o) of S (n_csf = 1)              */
   int32_t particle;  /* virtual index p in [0, v) of S (n_csf = 1)               */
   double beta;       /* T^P(0) = beta S + gamma S^2, gamma = -beta^2/2 (Eq.
-                        TP-guess, Sec. II.D); 0 means beta = 1                   */
+                        TP-guess, Sec. II.D); 0 means: from alpha and ansatz   */
+  double alpha;      /* Aufbau weight of the target reference (Sec. II.D)       */
+  int32_t ansatz;    /* 0: beta = 1/(1+alpha) with S as given; 1: the second
+                        ansatz, the hole orbital's sign flipped (alpha -> -alpha,
+                        beta = 1/(1-alpha)), run as S -> -S in these orbitals   */
+  int32_t reserved;
 } ascc_excitation;
 
 typedef struct {
@@ -77,9 +82,9 @@ typedef struct {
   int32_t max_iter;    /* iteration cap                                         */
   int32_t diis_dim;    /* DIIS history length (<= 32)                           */
   int32_t diis_start;  /* pairs needed before extrapolating                     */
-  int32_t polish_iter; /* mixed precision: FP64 iterations after the low-      */
-                       /*   precision phase converges to polish_tol            */
-  double polish_tol;   /* mixed precision: hand-over threshold on max |R|       */
+  int32_t polish_iter; /* reserved                                             */
+  double polish_tol;   /* mixed precision: max |R| at which the 3-product phase */
+                       /*   hands over to the FP64-corrected polishing phase     */
 } ascc_options;
 
 typedef struct {
@@ -88,12 +93,12 @@ typedef struct {
   double max_resid;   /* max |R| at the last evaluation                        */
   int32_t iterations; /* residual evaluations performed                        */
   int32_t status;     /* ascc_status of the solve                              */
-  int32_t iterations_low; /* of which in low precision (mixed precision)      */
-  int32_t reserved;
+  int32_t iterations_low;   /* of which in low precision (mixed precision)     */
+  int32_t fp64_evaluations; /* FP64 residuals of the polishing phase (mixed)   */
 } ascc_result;
 
 /* Fills *opt with defaults: FP64, PLASCC, triples off, r_tol 1e-8, e_tol 1e-10,
- * max_iter 200, DIIS 16 / start 3, polish 1e-6.  Returns ASCC_OK. */
+ * max_iter 200, DIIS 16 / start 3, polish 1e-5.  Returns ASCC_OK. */
 ascc_status ascc_default_options(ascc_options* opt);
 
 /* Creates a context for one state of one molecule (Secs. II.A-II.B).
@@ -211,6 +216,44 @@ ascc_status ascc_gemm_split_bf16_noalloc(int64_t M, int64_t N, int64_t K,
                                          int32_t level, double alpha,
                                          const double* A, const double* B,
                                          double beta, double* C, void* stream);
+
+/* ------------------------------------------------------------------ serving
+ * A request server for streams of ASCC solves of different molecules and
+ * states on one GPU.  Worker threads, each on its own CUDA stream, admit the
+ * oldest queued request whose device footprint (ascc_footprint_bytes) fits
+ * beside the requests already running, build its bare integrals once, solve
+ * its states (ground state first if listed; a ground state takes the primary
+ * pair of the request's first excitation for PLASCC) and free the memory, so
+ * requests that arrive while others run are admitted as memory frees up and
+ * their work overlaps on the device.  Times are seconds since creation. */
+typedef struct ascc_server ascc_server;
+typedef struct {
+  int64_t request_id;
+  int32_t state_index; /* index into the request's state list; -1: request failed */
+  int32_t status;      /* ascc_status of the solve                              */
+  double energy;
+  int32_t iterations;
+  int32_t worker;
+  double t_arrival, t_start, t_end;
+} ascc_serve_result;
+
+/* memory_budget: device bytes the admitted requests may use together;
+ * max_active: worker threads (1..64); opt: solve options (NULL = defaults). */
+ascc_status ascc_server_create(ascc_server** out, size_t memory_budget,
+                               int32_t max_active, const ascc_options* opt);
+/* Queues one request (host eps [o+v] and B [naux][n][n] are copied; the
+ * arrival time is the submission time).  Thread-safe. */
+ascc_status ascc_server_submit(ascc_server* srv, int32_t o, int32_t v,
+                               int32_t naux, const double* eps, const double* B,
+                               int32_t n_states, const ascc_excitation* states,
+                               int64_t* request_id);
+/* Blocks until every submitted request has finished. */
+ascc_status ascc_server_drain(ascc_server* srv);
+int64_t ascc_server_result_count(ascc_server* srv);
+/* Copies the per-state results (completion order) to out[capacity]. */
+ascc_status ascc_server_results(ascc_server* srv, ascc_serve_result* out,
+                                int64_t capacity);
+void ascc_server_destroy(ascc_server* srv);
 
 /* Checkpoint / resume of the amplitudes (host buffers, FP64). */
 ascc_status ascc_get_state(ascc_ctx* ctx, double* t1, double* t2, double* t3p);

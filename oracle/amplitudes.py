@@ -104,16 +104,17 @@ def t3_gather(t, idx):
 
 
 # ------------------------------------------------------------ initial guess
-def initial_guess(o, v, hole=None, particle=None, beta=1.0, n_t3=0):
+def initial_guess(o, v, hole=None, particle=None, beta=1.0, n_t3=0, xsign=1.0):
     """Zeroth-order amplitudes (Eq. TP-guess): T^P = beta S + gamma S^2, gamma = -beta^2/2.
 
     S = (1/sqrt2)(p+_up h_up + p+_dn h_dn) gives t1[h,p] = beta/sqrt2 and, since
     S^2 = a+_{p up} a+_{p dn} a_{h dn} a_{h up}, t2[h,h,p,p] = gamma.  All other
     amplitudes (T^M, T^N, T3') start at zero.  The ground state starts at zero.
+    xsign = -1 is the same guess written for S -> -S (the second ansatz).
     """
     t1 = np.zeros((o, v)); t2 = np.zeros((o, o, v, v)); t3 = np.zeros(n_t3)
     if hole is not None:
-        t1[hole, particle] = beta * SQRT_HALF
+        t1[hole, particle] = xsign * beta * SQRT_HALF
         t2[hole, hole, particle, particle] = -0.5 * beta * beta
     return t1, t2, t3
 

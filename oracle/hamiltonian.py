@@ -64,10 +64,11 @@ def transform(h: np.ndarray, B: np.ndarray, U: np.ndarray, Uinv: np.ndarray):
     return hbar, Bbar
 
 
-def similarity_transform(h: np.ndarray, B: np.ndarray, o: int, hole=None, particle=None):
-    """H-bar = exp(S^+) H exp(-S^+) (Eq. sim) as (h-bar, B-bar)."""
+def similarity_transform(h: np.ndarray, B: np.ndarray, o: int, hole=None, particle=None,
+                         xsign: float = 1.0):
+    """H-bar = exp(S^+) H exp(-S^+) (Eq. sim) as (h-bar, B-bar); xsign = -1 uses -S."""
     n = h.shape[0]
-    x = suppression_generator(n, o, hole, particle)
+    x = suppression_generator(n, o, hole, particle, xsign * SQRT_HALF)
     eye = np.eye(n)
     return transform(h, B, eye + x, eye - x)
 

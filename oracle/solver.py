@@ -9,13 +9,21 @@ project fixes, and the CUDA solver follows the same rules:
 * denominators from orbital energies:
     D1[i,a] = e_i - e_a,  D2[i,j,a,b] = e_i + e_j - e_a - e_b,
     D3[i,j,k,a,b,c] = e_i + e_j + e_k - e_a - e_b - e_c,
-  with the bare e for the ground state and for the primary (P) amplitudes of
-  a one-CSF state; for its other amplitudes both primary orbitals take the
-  mean (e_h + e_p)/2.  In the excited reference S phi0 the hole and the
-  particle are each half occupied, and this zeroth-order diagonal matches the
-  measured diagonal of the Jacobian of the mixed amplitudes (for the P
-  amplitudes it would vanish, so they keep the bare values);
-* Jacobi step t' = t + R / D;
+  with the bare e for the ground state; for a one-CSF state both primary
+  orbitals take the mean (e_h + e_p)/2, since in the excited reference S phi0
+  the hole and the particle are each half occupied (this zeroth-order
+  diagonal matches the measured diagonal of the Jacobian);
+* Jacobi step t' = t + R / D, except, for a one-CSF state, the pairs
+  (t1[i,a], t2[i,h,a,p]) (with t2[h,i,p,a] = t2[i,h,a,p]).  Through the
+  zeroth-order T^P these pairs are coupled at O(1): R1[i,a] depends on
+  t2[i,h,a,p] through F_hp and, when i = h or a = p, R2[i,h,a,p] depends on
+  t1[i,a] through F_ph, where F is the Fock matrix of exp(-T1) Hbar exp(T1).
+  Their step solves the 2 x 2 model Jacobian
+      J = [[-D1[i,a], c F_hp], [q, -D2[i,h,a,p]]],   (dt1, dt2) = -J^-1 (R1[i,a], R2[i,h,a,p]),
+  c = 2, q = 0 for i != h and a != p; c = 1, q = F_ph when i = h or a = p
+  (not both); for the primary pair (h, p) J = [[0, F_hp], [2 F_hp, 0]] (its
+  mean-energy diagonal vanishes).  A near-singular J (|det| < 1e-12 max|J|^2)
+  falls back to the diagonal step (bare denominators for the primary pair);
 * DIIS over the vector (t1, t2, t3'): the error is e = t' - t, the history
   keeps the last `diis_dim` (default 16) pairs (t', e); once it holds `diis_start` pairs
   the new amplitudes are sum_k c_k t'_k with c solving the bordered system
@@ -88,27 +96,61 @@ def _raw_denominators(eps, o, t3_idx):
 
 
 def denominators(eps, o, t3_idx=None, hole=None, particle=None):
-    D1, D2, D3 = _raw_denominators(eps, o, t3_idx)
+    """Diagonal denominators; for a one-CSF state the primary amplitudes t1[h,p]
+    and t2[h,h,p,p] (zero with the mean energies) keep the bare values, which
+    only serve when their pair step falls back to the diagonal."""
     if hole is None:
-        return D1, D2, D3
-    from .amplitudes import t1_class_masks, t2_class_masks
-    v = len(eps) - o
+        return _raw_denominators(eps, o, t3_idx)
     e = np.array(eps, dtype=float)
     m = 0.5 * (e[hole] + e[o + particle])
     e[hole] = m
     e[o + particle] = m
-    E1, E2, E3 = _raw_denominators(e, o, t3_idx)
-    P1, _, _ = t1_class_masks(o, v, hole, particle)
-    P2, _, _ = t2_class_masks(o, v, hole, particle)
-    return np.where(P1, D1, E1), np.where(P2, D2, E2), E3
+    D1, D2, D3 = _raw_denominators(e, o, t3_idx)
+    B1, B2, _ = _raw_denominators(eps, o, None)
+    h, p = hole, particle
+    D1[h, p] = B1[h, p]
+    D2[h, h, p, p] = B2[h, h, p, p]
+    return D1, D2, D3
+
+
+def jacobi_step(R1, R2, R3, D1, D2, D3, hole=None, particle=None, fock=None):
+    """Update (dt1, dt2, dt3) of one iteration (see the module docstring)."""
+    d1 = R1 / D1
+    d2 = R2 / D2
+    d3 = R3 / D3 if R3.size else np.zeros(0)
+    if hole is None:
+        return d1, d2, d3
+    o, v = R1.shape
+    h, p = hole, particle
+    fhp, fph = fock
+    for i in range(o):
+        for a in range(v):
+            if i == h and a == p:
+                # both mean-energy diagonals vanish for the primary pair
+                J = np.array([[0.0, fhp], [2.0 * fhp, 0.0]])
+            else:
+                c, q = (1.0, fph) if (i == h or a == p) else (2.0, 0.0)
+                J = np.array([[-D1[i, a], c * fhp], [q, -D2[i, h, a, p]]])
+            det = J[0, 0] * J[1, 1] - J[0, 1] * J[1, 0]
+            if abs(det) <= 1e-12 * np.max(np.abs(J)) ** 2:
+                continue
+            r1, r2 = R1[i, a], R2[i, h, a, p]
+            x1 = (J[1, 1] * r1 - J[0, 1] * r2) / det
+            x2 = (-J[1, 0] * r1 + J[0, 0] * r2) / det
+            d1[i, a] = -x1
+            d2[i, h, a, p] = -x2
+            d2[h, i, p, a] = -x2
+    return d1, d2, d3
 
 
 def solve(resid_fn, eps, o, t1, t2, t3, t3_idx=None, r_tol=1e-8, e_tol=1e-10,
-          max_iter=200, diis_dim=16, diis_start=3, verbose=False, hole=None, particle=None):
+          max_iter=200, diis_dim=16, diis_start=3, verbose=False, hole=None, particle=None,
+          fock_fn=None):
     """Iterate resid_fn(t1, t2, t3) -> (E, R1, R2, R3) to convergence.
 
     hole/particle: the primary orbitals of a one-CSF state (None for the
-    ground state), which select the denominators described above.
+    ground state), which select the update described above; fock_fn(t1)
+    returns (F_hp, F_ph) of exp(-T1) Hbar exp(T1) for the pair step.
     """
     D1, D2, D3 = denominators(eps, o, t3_idx, hole, particle)
     shapes = [t1.shape, t2.shape, t3.shape]
@@ -139,7 +181,9 @@ def solve(resid_fn, eps, o, t1, t2, t3, t3_idx=None, r_tol=1e-8, e_tol=1e-10,
             break
         e_prev = En
         R3v = R3 if R3 is not None else np.zeros(0)
-        tn = pack(t1 + R1 / D1, t2 + R2 / D2, t3 + (R3v / D3 if R3v.size else 0.0))
+        fock = fock_fn(t1) if (hole is not None and fock_fn is not None) else None
+        d1, d2, d3 = jacobi_step(R1, R2, R3v, D1, D2, D3, hole if fock else None, particle, fock)
+        tn = pack(t1 + d1, t2 + d2, t3 + (d3 if R3v.size else 0.0))
         err = tn - pack(t1, t2, t3)
         hist_t.append(tn); hist_e.append(err)
         if len(hist_t) > diis_dim:

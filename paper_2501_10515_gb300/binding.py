@@ -20,7 +20,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA er
 
 class Excitation(C.Structure):
     _fields_ = [("n_csf", C.c_int32), ("hole", C.c_int32), ("particle", C.c_int32),
-                ("beta", C.c_double)]
+                ("beta", C.c_double), ("alpha", C.c_double), ("ansatz", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Options(C.Structure):
@@ -33,13 +34,19 @@ class Options(C.Structure):
 class Result(C.Structure):
     _fields_ = [("energy", C.c_double), ("e_ref", C.c_double), ("max_resid", C.c_double),
                 ("iterations", C.c_int32), ("status", C.c_int32), ("iterations_low", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("fp64_evaluations", C.c_int32)]
 
 
 class Profile(C.Structure):
     _fields_ = [("ladder_ms", C.c_double), ("ladder_flops", C.c_double),
                 ("ladder_launches", C.c_int64), ("launches", C.c_int64),
                 ("gemm_flops", C.c_double)]
+
+
+class ServeResult(C.Structure):
+    _fields_ = [("request_id", C.c_int64), ("state_index", C.c_int32), ("status", C.c_int32),
+                ("energy", C.c_double), ("iterations", C.c_int32), ("worker", C.c_int32),
+                ("t_arrival", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double)]
 
 
 class AsccError(RuntimeError):
@@ -81,6 +88,13 @@ def load():
                                            vp, vp, C.c_double, vp, vp]),
         "ascc_gemm_split_bf16_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                                    C.c_double, vp, vp, C.c_double, vp, vp]),
+        "ascc_server_create": (C.c_int, [P(vp), C.c_size_t, C.c_int32, P(Options)]),
+        "ascc_server_submit": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, dp, dp, C.c_int32,
+                                         P(Excitation), P(C.c_int64)]),
+        "ascc_server_drain": (C.c_int, [vp]),
+        "ascc_server_result_count": (C.c_int64, [vp]),
+        "ascc_server_results": (C.c_int, [vp, P(ServeResult), C.c_int64]),
+        "ascc_server_destroy": (None, [vp]),
         "ascc_get_state": (C.c_int, [vp, dp, dp, dp]),
         "ascc_set_state": (C.c_int, [vp, dp, dp, dp]),
         "ascc_footprint_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, P(Options)]),
@@ -127,6 +141,13 @@ def gemm_split_bf16_noalloc(A, B, out, level, alpha=1.0, beta=0.0, stream=None):
                                                C_void(out), C.c_void_p(stream) if stream else None))
 
 
+def two_ansatz_average(e_small, status_small, e_large, status_large):
+    """Reported energy of Sec. II.D: the mean of the two ansatz energies, or the one
+    that converged when the other did not (Sec. III.A); None if neither did."""
+    ok = [e for e, st in ((e_small, status_small), (e_large, status_large)) if st == 0]
+    return sum(ok) / len(ok) if ok else None
+
+
 def C_void(x):
     return C.c_void_p(x.data_ptr())
 
@@ -149,14 +170,15 @@ def _ptr(a):
 class Context:
     """One ASCC state (ground or one-CSF excited) of one molecule on the current GPU."""
 
-    def __init__(self, o, v, naux, eps, B, hole=None, particle=None, beta=1.0, options=None,
-                 stream=None, base=None, **opt_kw):
+    def __init__(self, o, v, naux, eps, B, hole=None, particle=None, beta=0.0, options=None,
+                 stream=None, base=None, alpha=0.0, ansatz=0, **opt_kw):
         lib = load()
         self.o, self.v, self.naux = o, v, naux
         opt = options if options is not None else default_options()
         for k, val in opt_kw.items():
             setattr(opt, k, val)
-        exc = Excitation(0, 0, 0, 0.0) if hole is None else Excitation(1, hole, particle, beta)
+        exc = (Excitation(0, 0, 0, 0.0, 0.0, 0, 0) if hole is None
+               else Excitation(1, hole, particle, beta, alpha, ansatz, 0))
         h = C.c_void_p()
         s = C.c_void_p(stream) if stream else None
         if base is not None:
@@ -257,3 +279,52 @@ class Context:
 
     def launches(self) -> int:
         return int(load().ascc_launch_count(self._h))
+
+
+class Server:
+    """Continuous-batching request server (ascc_server_*): queue solves, drain, read results."""
+
+    def __init__(self, memory_budget, max_active=4, options=None, **opt_kw):
+        opt = options if options is not None else default_options()
+        for k, val in opt_kw.items():
+            setattr(opt, k, val)
+        h = C.c_void_p()
+        _check(load().ascc_server_create(C.byref(h), int(memory_budget), int(max_active),
+                                         C.byref(opt)))
+        self._h = h
+
+    def submit(self, o, v, naux, eps, B, states):
+        """states: list of (hole, particle) or None (ground state)."""
+        eps = np.ascontiguousarray(eps, np.float64)
+        B = np.ascontiguousarray(B, np.float64)
+        arr = (Excitation * len(states))()
+        for k, st in enumerate(states):
+            arr[k] = (Excitation(0, 0, 0, 0.0, 0.0, 0, 0) if st is None
+                      else Excitation(1, st[0], st[1], 0.0, 0.0, 0, 0))
+        rid = C.c_int64()
+        _check(load().ascc_server_submit(self._h, o, v, naux, _ptr(eps), _ptr(B), len(states),
+                                         arr, C.byref(rid)))
+        return rid.value
+
+    def drain(self):
+        _check(load().ascc_server_drain(self._h))
+
+    def results(self):
+        n = int(load().ascc_server_result_count(self._h))
+        buf = (ServeResult * max(n, 1))()
+        _check(load().ascc_server_results(self._h, buf, n))
+        return [dict(request_id=r.request_id, state_index=r.state_index, status=r.status,
+                     energy=r.energy, iterations=r.iterations, worker=r.worker,
+                     t_arrival=r.t_arrival, t_start=r.t_start, t_end=r.t_end)
+                for r in buf[:n]]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ascc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,4 +1,5 @@
 // C ABI of libascc (declared in include/ascc.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -74,17 +75,25 @@ void prepare_pool() {
   ASCC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
 }
 
-void check_exc(const ascc_excitation* exc, int o, int v, int& hole, int& particle, double& beta) {
+void check_exc(const ascc_excitation* exc, int o, int v, int& hole, int& particle, double& beta,
+               double& xsign) {
   hole = -1;
   particle = -1;
   beta = 1.0;
+  xsign = 1.0;
   if (!exc || exc->n_csf == 0) return;
   ASCC_REQUIRE(exc->n_csf == 1, "only one-CSF excitations are supported");
   ASCC_REQUIRE(exc->hole >= 0 && exc->hole < o, "hole out of range");
   ASCC_REQUIRE(exc->particle >= 0 && exc->particle < v, "particle out of range");
+  ASCC_REQUIRE(exc->ansatz == 0 || exc->ansatz == 1, "ansatz must be 0 or 1");
+  ASCC_REQUIRE(std::isfinite(exc->alpha) && std::fabs(exc->alpha) < 1.0, "|alpha| must be < 1");
   hole = exc->hole;
   particle = exc->particle;
-  beta = exc->beta == 0.0 ? 1.0 : exc->beta;
+  xsign = exc->ansatz == 1 ? -1.0 : 1.0;
+  if (exc->beta != 0.0)
+    beta = exc->beta;
+  else
+    beta = exc->ansatz == 1 ? 1.0 / (1.0 - exc->alpha) : 1.0 / (1.0 + exc->alpha);
   ASCC_REQUIRE(std::isfinite(beta) && beta > 0.0, "beta must be positive");
 }
 
@@ -96,11 +105,11 @@ ascc_status make_ctx(ascc_ctx** out, std::shared_ptr<Molecule> mol, const ascc_e
   ctx->launches0 = launch_total();
   ctx->flops0 = flop_total();
   int hole, particle;
-  double beta;
-  check_exc(exc, mol->o, mol->v, hole, particle, beta);
+  double beta, xsign;
+  check_exc(exc, mol->o, mol->v, hole, particle, beta, xsign);
   Options o = to_options(opt);
   if (o.pl_hole >= mol->o || o.pl_particle >= mol->v) throw Error(ASCC_ERR_INVALID, "pl labels");
-  ctx->state = std::make_unique<State>(std::move(mol), hole, particle, beta, o, stream);
+  ctx->state = std::make_unique<State>(std::move(mol), hole, particle, beta, o, stream, xsign);
   ASCC_CUDA(cudaStreamSynchronize(stream));
   *out = ctx.release();
   return ASCC_OK;
@@ -123,7 +132,7 @@ ascc_status ascc_default_options(ascc_options* opt) {
   opt->diis_dim = 16;
   opt->diis_start = 3;
   opt->polish_iter = 50;
-  opt->polish_tol = 1e-6;
+  opt->polish_tol = 1e-5;
   return ASCC_OK;
 }
 
@@ -314,8 +323,10 @@ ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level,
     DevBuf pb(sizeof(__nv_bfloat16) * (size_t)(level * N * Kp), s);
     tc::split_bf16(s, pa.as<__nv_bfloat16>(), A, M, K, K, level);
     tc::split_bf16(s, pb.as<__nv_bfloat16>(), B, N, K, K, level);
+    const int z = tc::splitk_for(M, N, K);
+    DevBuf ws(z > 1 ? sizeof(float) * (size_t)(z * M * N) : 0, s);
     tc::gemm_split(s, M, N, K, level, alpha, pa.as<__nv_bfloat16>(), pb.as<__nv_bfloat16>(), beta,
-                   C, N, err);
+                   C, N, err, z, ws.as<float>());
     return ASCC_OK;
   });
 }
@@ -354,13 +365,23 @@ ascc_status ascc_set_state(ascc_ctx* ctx, const double* t1, const double* t2, co
 }
 
 size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux, const ascc_options* opt) {
-  const double n = o + v;
-  const int m = opt ? opt->diis_dim : 8;
-  const double o2v2 = (double)o * o * v * v;
-  double mol = 8.0 * (naux * n * n * 2 + n * (double)v * v * v * 2 + naux * n * v + naux * (double)v * v);
-  double state = 8.0 * (o2v2 * (2.0 * m + 16) + 3.0 * naux * n * n + (double)o * o * n * n * 2 +
-                        (double)o * o * n * v * 3);
-  return (size_t)(mol + state);
+  // molecule: B, hcore, Bvv, Bnv, ladder block (FP64 or 3 BF16 planes) and its
+  // build chunk; state: amplitudes, residual, DIIS history, per-iteration
+  // workspace and the einsum temporaries (a few o^2 v^2 / o^2 n^2 tensors).
+  const double n = o + v, O = o, V = v, P = naux;
+  const bool mixed = opt && opt->precision == ASCC_MIXED_BF16;
+  const int m = opt ? opt->diis_dim : 16;
+  const double kp = std::ceil(V * V / 64.0) * 64.0;
+  double mol = 8.0 * (P * n * n + n * n + P * V * V + P * n * V);
+  // FP64 ladder block (+ its build temporary); mixed precision adds the BF16
+  // planes, the FP64 block serving the FP64-corrected polishing residuals
+  mol += 8.0 * n * V * V * V * 2.0;
+  if (mixed) mol += 2.0 * 3.0 * n * V * kp;
+  const double o2v2 = O * O * V * V, namp = O * V + o2v2;
+  double state = 8.0 * (namp * (2.0 * m + 4.0) + P * n * n * 1.2 + 24.0 * o2v2 +
+                        O * O * n * n * 3.0 + O * O * n * V * 4.0);
+  if (mixed) state += 2.0 * 3.0 * (O * O + n * V) * kp;  // operand planes of the ladder
+  return (size_t)((mol + state) * 1.1);
 }
 
 int64_t ascc_launch_count(const ascc_ctx* ctx) {

@@ -11,8 +11,10 @@
 // ladder uses the bare (xc|bd) integrals, built once per molecule, with the
 // L and R dressings applied to the output and to the amplitudes.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 
 #include "engine.h"
 #include "gemm_tc.h"
@@ -165,13 +167,15 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
     DevBuf pb(sizeof(__nv_bfloat16) * (size_t)(level_ * Ns * Kp), s_);
     tc::split_bf16(s_, pa.as<__nv_bfloat16>(), Am, Ms, Ks, Ks, level_);
     tc::split_bf16(s_, pb.as<__nv_bfloat16>(), Bn, Ns, Ks, Ks, level_);
+    const int z = tc::splitk_for(Ms, Ns, Ks);
+    DevBuf ws(z > 1 ? sizeof(float) * (size_t)(z * Ms * Ns) : 0, s_);
     if (sp.c == cl) {
       tc::gemm_split(s_, Ms, Ns, Ks, level_, alpha, pa.as<__nv_bfloat16>(),
-                     pb.as<__nv_bfloat16>(), beta, C.p, Ns, err_);
+                     pb.as<__nv_bfloat16>(), beta, C.p, Ns, err_, z, ws.as<float>());
     } else {
       OT Ct(shape_of(cl), s_);
       tc::gemm_split(s_, Ms, Ns, Ks, level_, 1.0, pa.as<__nv_bfloat16>(), pb.as<__nv_bfloat16>(),
-                     0.0, Ct.p(), Ns, err_);
+                     0.0, Ct.p(), Ns, err_, z, ws.as<float>());
       perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
     }
     return;
@@ -219,26 +223,57 @@ Molecule::Molecule(int o_, int v_, int naux_, const double* eps_h, const double*
            {naux, v, v});
   Bnv.make({naux, n, v}, s);
   box_copy(s, Bnv.p(), {(int64_t)n * v, v, 1}, B.p() + o, {(int64_t)n * n, n, 1}, {naux, n, v});
-  // Gext[x][b][c][d] = (xc|bd) = sum_P B[P][x][o+c] B[P][o+b][o+d]
-  Gext.make({n, v, v, v}, s);
-  es.set_split(build_level, err.as<int>(), 0.0);
-  es("Pxc,Pbd->xbcd", 1.0, Bnv.t, Bvv.t, 0.0, Gext.t);
-  int h = 0;
-  ASCC_CUDA(cudaMemcpyAsync(&h, err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
-  ASCC_CUDA(cudaStreamSynchronize(s));
-  if (h) throw Error(ASCC_ERR_TIMEOUT, "tensor-core GEMM wait timed out while building (xc|bd)");
+  build_level_ = build_level;
 }
 
-void Molecule::make_bf16_planes() {
+// Gext[x][b][c][d] = (xc|bd) = sum_P B[P][x][o+c] B[P][o+b][o+d], in FP64.
+void Molecule::ensure_fp64_ladder() {
+  std::lock_guard<std::mutex> lock(mu_);
+  if (Gext.buf.bytes()) return;
+  Einsum es(stream);
+  Gext.make({n, v, v, v}, stream);
+  es.set_split(0, err.as<int>(), 0.0);
+  es("Pxc,Pbd->xbcd", 1.0, Bnv.t, Bvv.t, 0.0, Gext.t);
+  ASCC_CUDA(cudaStreamSynchronize(stream));
+}
+
+// BF16 planes of Gext for the mixed-precision ladder, built x-chunk by
+// x-chunk (from the FP64 block when it exists, else on the tensor cores with
+// the finest split) so that the FP64 block never has to exist in full.
+void Molecule::ensure_bf16_ladder() {
+  std::lock_guard<std::mutex> lock(mu_);
   if (Gext_bf16.bytes()) return;
   const int64_t rows = (int64_t)n * v, K = (int64_t)v * v, Kp = tc::padded_k(K);
   Gext_bf16.alloc(sizeof(__nv_bfloat16) * (size_t)(3 * rows * Kp), stream);
-  tc::split_bf16(stream, Gext_bf16.as<__nv_bfloat16>(), Gext.p(), rows, K, K, 3);
+  if (Gext.buf.bytes()) {
+    tc::split_bf16(stream, Gext_bf16.as<__nv_bfloat16>(), Gext.p(), rows, K, K, 3, rows * Kp);
+    ASCC_CUDA(cudaStreamSynchronize(stream));
+    return;
+  }
+  Einsum es(stream);
+  es.set_split(build_level_ > 0 ? build_level_ : 3, err.as<int>(), 0.0);
+  const int64_t v3 = (int64_t)v * v * v;
+  int64_t xc = std::max<int64_t>(1, ((int64_t)1 << 27) / v3);  // ~1 GB FP64 per chunk
+  xc = std::min<int64_t>(xc, n);
+  OT Ac({naux, xc, v}, stream), Gc({xc, v, v, v}, stream);
+  for (int64_t x0 = 0; x0 < n; x0 += xc) {
+    const int64_t nx = std::min<int64_t>(xc, n - x0);
+    T a(Ac.p(), {naux, nx, v}), gch(Gc.p(), {nx, v, v, v});
+    box_copy(stream, Ac.p(), {nx * v, v, 1}, Bnv.p() + x0 * v, {(int64_t)n * v, v, 1},
+             {naux, nx, v});
+    es("Pxc,Pbd->xbcd", 1.0, a, Bvv.t, 0.0, gch);
+    tc::split_bf16(stream, Gext_bf16.as<__nv_bfloat16>() + x0 * v * Kp, Gc.p(), nx * v, K, K, 3,
+                   rows * Kp);
+  }
+  int h = 0;
+  ASCC_CUDA(cudaMemcpyAsync(&h, err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, stream));
+  ASCC_CUDA(cudaStreamSynchronize(stream));
+  if (h) throw Error(ASCC_ERR_TIMEOUT, "tensor-core GEMM wait timed out while building (xc|bd)");
 }
 
 size_t Molecule::bytes() const {
   return eps.buf.bytes() + B.buf.bytes() + hcore.buf.bytes() + Bvv.buf.bytes() +
-         Bnv.buf.bytes() + Gext.buf.bytes();
+         Bnv.buf.bytes() + Gext.buf.bytes() + Gext_bf16.bytes();
 }
 
 // ---------------------------------------------------------------- State
@@ -270,12 +305,13 @@ std::vector<int32_t> t3p_index(int o, int v, int h, int p) {
 }  // namespace
 
 State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
-             const Options& opt, cudaStream_t s)
+             const Options& opt, cudaStream_t s, double xsign)
     : mol_(std::move(mol)), opt_(opt), s_(s), es_(s) {
   o_ = mol_->o; v_ = mol_->v; n_ = mol_->n; naux_ = mol_->naux;
   hole_ = hole; particle_ = particle;
   beta_ = beta == 0.0 ? 1.0 : beta;
-  xval_ = hole_ >= 0 ? 1.0 / std::sqrt(2.0) : 0.0;
+  xsign_ = xsign < 0 ? -1.0 : 1.0;
+  xval_ = hole_ >= 0 ? xsign_ / std::sqrt(2.0) : 0.0;
   lh_ = hole_ >= 0 ? hole_ : opt_.pl_hole;
   lp_ = hole_ >= 0 ? particle_ : opt_.pl_particle;
   if (lh_ < 0) opt_.linearize = 0;
@@ -297,8 +333,13 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   coef_.make({32}, s);
   const int o = o_, v = v_, n = n_, P = naux_;
   L_.make({n, n}, s); R_.make({n, n}, s);
-  tmpB_.make({P, n, n}, s); Bhat_.make({P, n, n}, s);
-  hhat_.make({n, n}, s); tmpnn_.make({n, n}, s); F_.make({n, n}, s);
+  {
+    const int nc = o + (hole_ >= 0 ? 1 : 0);
+    LamC_.make({n, nc}, s); RhoC_.make({n, nc}, s);
+    rowsC_.make({P, nc, n}, s); colsC_.make({P, n, nc}, s);
+  }
+  Bhat_.make({P, n, n}, s);
+  hhat_.make({n, n}, s); F_.make({n, n}, s);
   dP_.make({P}, s); J_.make({n, n}, s); K_.make({n, n}, s);
   Boo_.make({P, o, o}, s); Bov_.make({P, o, v}, s); Bvo_.make({P, v, o}, s);
   Bvv_.make({P, v, v}, s); Bno_.make({P, n, o}, s); Bon_.make({P, o, n}, s);
@@ -309,6 +350,10 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   WC_.make({o, o, v, v}, s); WD_.make({v, o, o, v}, s); Wq_.make({o, o, o, o}, s);
   Fvv_.make({v, v}, s); Foo_.make({o, o}, s); X_.make({P, o, v}, s);
   Y_.make({o, o, n, v}, s); Yfull_.make({o, o, n, n}, s); Z1_.make({o, o, n, v}, s);
+  {
+    const int nc = o + (hole_ >= 0 ? 1 : 0);
+    YC_.make({o, o, n, nc}, s); Z1C_.make({o, o, nc, v}, s);
+  }
   tt_.make({o, o, nu_, nu_}, s); Yoo_.make({o, o, o, o}, s);
   if (opt_.linearize) {
     m_.make({o, o, v, v}, s);
@@ -316,6 +361,8 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   }
   err_.alloc(sizeof(int), s);
   err_.zero();
+  if (opt_.precision == ASCC_MIXED_BF16) corr_.make({namp()}, s);
+  if (const char* env = std::getenv("ASCC_TC_MIN_FLOPS")) tc_min_flops_ = std::atof(env);
   {
     // Jacobi denominators: the hole and particle of a one-CSF state are half
     // occupied in S phi0; their mean energy enters the non-primary amplitudes.
@@ -329,16 +376,19 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
     ASCC_CUDA(cudaMemcpyAsync(eps_eff_.p(), ee.data(), sizeof(double) * n_, cudaMemcpyHostToDevice, s));
     ASCC_CUDA(cudaStreamSynchronize(s));
   }
-  if (opt_.precision == ASCC_MIXED_BF16) {
-    ASCC_CUDA(cudaStreamSynchronize(mol_->stream));
-    mol_->make_bf16_planes();
-    ASCC_CUDA(cudaStreamSynchronize(mol_->stream));
-  }
+  ASCC_CUDA(cudaStreamSynchronize(mol_->stream));
+  if (opt_.precision == ASCC_MIXED_BF16)
+    mol_->ensure_bf16_ladder();
+  else
+    mol_->ensure_fp64_ladder();
   build_state_integrals();
 }
 
 // Mixed precision: 3 BF16 products (16 significant bits) until max|R| reaches
-// polish_tol, then 6 products (24 bits) for the polishing iterations.
+// polish_tol, then 6 products (24 bits) with an FP64 defect correction: the
+// residual is R3(t) + [R64(t0) - R3(t0)], refreshed from an FP64 evaluation at
+// hand-over and whenever the corrected iteration converges, so that the
+// accepted amplitudes satisfy the FP64 equations.
 int State::level_for_phase() const {
   if (opt_.precision != ASCC_MIXED_BF16) return 0;
   return polish_ ? 3 : 2;
@@ -377,29 +427,48 @@ void State::build_state_integrals() {
 }
 
 void State::initial_guess(std::vector<double>& t) const {
-  // Eq. TP-guess: t1[h][p] = beta/sqrt2, t2[h][h][p][p] = -beta^2/2; else 0.
+  // Eq. TP-guess: t1[h][p] = beta/sqrt2, t2[h][h][p][p] = -beta^2/2; else 0
+  // (t1[h][p] = -beta/sqrt2 for the second ansatz, S -> -S).
   t.assign((size_t)namp(), 0.0);
   if (hole_ < 0) return;
-  t[(size_t)hole_ * v_ + particle_] = beta_ / std::sqrt(2.0);
+  t[(size_t)hole_ * v_ + particle_] = xsign_ * beta_ / std::sqrt(2.0);
   const int64_t i2 = (((int64_t)hole_ * o_ + hole_) * v_ + particle_) * v_ + particle_;
   t[(size_t)(n1() + i2)] = -0.5 * beta_ * beta_;
 }
 
 // B-hat = L B R and h-hat = L h R with the S^+ and T1 orbital transforms.
+// L = 1 + Lambda and R = 1 + Rho have non-zero off-identity columns only in
+// C = {occupied} (+ {p} for a one-CSF state), so
+//   B-hat = B1 + (B1 Rho_C) scattered into the columns C,  B1 = B + Lambda_C B[C, :],
+// which costs 4 n^2 |C| per DF index instead of 4 n^3.
 void State::dress(const double* t1) {
-  const int n = n_, P = naux_;
+  const int n = n_, P = naux_, o = o_;
   Molecule& M = *mol_;
   k::build_LR(s_, L_.p(), R_.p(), t1, o_, v_, hole_, particle_, xval_);
   const int64_t nn = (int64_t)n * n;
-  k::gemm_f64(s_, false, false, n, n, n, 1.0, L_.p(), n, 0, M.B.p(), n, nn, 0.0, tmpB_.p(), n, nn,
-              P);
-  k::gemm_f64(s_, false, false, n, n, n, 1.0, tmpB_.p(), n, nn, R_.p(), n, 0, 0.0, Bhat_.p(), n,
-              nn, P);
-  k::gemm_f64(s_, false, false, n, n, n, 1.0, L_.p(), n, 0, M.hcore.p(), n, 0, 0.0, tmpnn_.p(),
-              n, 0, 1);
-  k::gemm_f64(s_, false, false, n, n, n, 1.0, tmpnn_.p(), n, 0, R_.p(), n, 0, 0.0, hhat_.p(), n,
-              0, 1);
-  const int o = o_, v = v_;
+  const int nc = o + (hole_ >= 0 ? 1 : 0);
+  const int pcol = hole_ >= 0 ? o + particle_ : -1;
+  k::cols_minus_identity(s_, LamC_.p(), L_.p(), n, o, pcol, nc);
+  k::cols_minus_identity(s_, RhoC_.p(), R_.p(), n, o, pcol, nc);
+  auto apply = [&](const double* src, double* dst, int batch) {
+    // rows C of src
+    box_copy(s_, rowsC_.p(), {(int64_t)nc * n, n, 1}, src, {nn, n, 1}, {batch, o, n});
+    if (pcol >= 0)
+      box_copy(s_, rowsC_.p() + (int64_t)o * n, {(int64_t)nc * n, 1}, src + (int64_t)pcol * n,
+               {nn, 1}, {batch, n});
+    ASCC_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * nn * batch, cudaMemcpyDeviceToDevice, s_));
+    k::gemm_f64(s_, false, false, n, n, nc, 1.0, LamC_.p(), nc, 0, rowsC_.p(), n, (int64_t)nc * n,
+                1.0, dst, n, nn, batch);
+    k::gemm_f64(s_, false, false, n, nc, n, 1.0, dst, n, nn, RhoC_.p(), nc, 0, 0.0, colsC_.p(), nc,
+                (int64_t)n * nc, batch);
+    box_copy(s_, dst, {nn, n, 1}, colsC_.p(), {(int64_t)n * nc, nc, 1}, {batch, n, o}, 1.0, 1.0);
+    if (pcol >= 0)
+      box_copy(s_, dst + pcol, {nn, n}, colsC_.p() + o, {(int64_t)n * nc, nc}, {batch, n}, 1.0,
+               1.0);
+  };
+  apply(M.B.p(), Bhat_.p(), P);
+  apply(M.hcore.p(), hhat_.p(), 1);
+  const int v = v_;
   const std::vector<int64_t> bs = {nn, n, 1};
   box_copy(s_, Boo_.p(), {(int64_t)o * o, o, 1}, Bhat_.p(), bs, {P, o, o});
   box_copy(s_, Bov_.p(), {(int64_t)o * v, v, 1}, Bhat_.p() + o, bs, {P, o, v});
@@ -416,7 +485,7 @@ void State::dress(const double* t1) {
   es_("Ppq,P->pq", 1.0, Bhat_.t, dP_.t, 0.0, J_.t);
   es_("Ppk,Pkq->pq", 1.0, Bno_.t, Bon_.t, 0.0, K_.t);
   es_("Pij,Pkl->ijkl", 1.0, Boo_.t, Boo_.t, 0.0, goooo_.t);
-  es_.set_split(lev, err_.as<int>());
+  es_.set_split(lev, err_.as<int>(), tc_min_flops_);
   k::axpby(s_, F_.p(), hhat_.p(), 1.0, 0.0, nn);
   k::axpby(s_, F_.p(), J_.p(), 2.0, 1.0, nn);
   k::axpby(s_, F_.p(), K_.p(), -1.0, 1.0, nn);
@@ -455,8 +524,11 @@ void State::ladder(const T& t2, const T& r2) {
     DevBuf pa(sizeof(__nv_bfloat16) * (size_t)(lev * (int64_t)o * o * Kp), s_);
     tc::split_bf16(s_, pa.as<__nv_bfloat16>(), t2.p, (int64_t)o * o, K, K, lev);
     // planes of Gext are stored [3][rows][Kp]; the kernel reads planes 0..lev-1
+    const int z = tc::splitk_for((int64_t)o * o, rows, K);
+    DevBuf ws(z > 1 ? sizeof(float) * (size_t)(z * (int64_t)o * o * rows) : 0, s_);
     tc::gemm_split(s_, (int64_t)o * o, rows, K, lev, 1.0, pa.as<__nv_bfloat16>(),
-                   M.Gext_bf16.as<__nv_bfloat16>(), 0.0, Y_.p(), rows, err_.as<int>());
+                   M.Gext_bf16.as<__nv_bfloat16>(), 0.0, Y_.p(), rows, err_.as<int>(), z,
+                   ws.as<float>());
   } else {
     es_("ijcd,xbcd->ijxb", 1.0, t2, M.Gext.t, 0.0, Y_.t);
   }
@@ -501,12 +573,25 @@ void State::ladder(const T& t2, const T& r2) {
            {(int64_t)n * v, (int64_t)o * n * v, 1, v}, {o, o, v, o});
   box_copy(s_, Yfull_.p(), {fs[0], fs[1], n, 1}, Yoo_.p(),
            {(int64_t)o * o * o, (int64_t)o * o, o, 1}, {o, o, o, o});
-  // r2[i][j][a][b] += sum_{t,v'} L[o+a][t] L[o+b][v'] Yfull[i][j][t][v']
-  const double* LV = L_.p() + (int64_t)o * n;
-  k::gemm_f64(s_, false, true, (int64_t)o * o * n, v, n, 1.0, Yfull_.p(), n, 0, LV, n, 0, 0.0,
-              Z1_.p(), v, 0, 1);
-  k::gemm_f64(s_, false, false, v, v, n, 1.0, LV, n, 0, Z1_.p(), v, (int64_t)n * v, 1.0, r2.p, v,
-              vv, (int64_t)o * o);
+  // r2[i][j][a][b] += sum_{t,v'} L[o+a][t] L[o+b][v'] Yfull[i][j][t][v'] with
+  // L[o+a][.] = e_{o+a} + Lambda[o+a][C] (columns C = occupied + p only):
+  //   Z1 = Yfull[.., V] + Yfull[.., C] Lambda_V^T,  r2 += Z1[V, ..] + Lambda_V Z1[C, ..]
+  const int nc = o + (hole_ >= 0 ? 1 : 0);
+  const int pcol = hole_ >= 0 ? o + particle_ : -1;
+  const double* LamV = LamC_.p() + (int64_t)o * nc;  // rows o..n-1 of (L - 1)[:, C]
+  const int64_t oo = (int64_t)o * o;
+  box_copy(s_, Z1_.p(), {v, 1}, Yfull_.p() + o, {n, 1}, {oo * n, v});
+  box_copy(s_, YC_.p(), {nc, 1}, Yfull_.p(), {n, 1}, {oo * n, o});
+  if (pcol >= 0) box_copy(s_, YC_.p() + o, {nc}, Yfull_.p() + pcol, {n}, {oo * n});
+  k::gemm_f64(s_, false, true, oo * n, v, nc, 1.0, YC_.p(), nc, 0, LamV, nc, 0, 1.0, Z1_.p(), v, 0,
+              1);
+  box_copy(s_, r2.p, {vv, 1}, Z1_.p() + (int64_t)o * v, {(int64_t)n * v, 1}, {oo, vv}, 1.0, 1.0);
+  box_copy(s_, Z1C_.p(), {(int64_t)nc * v, v, 1}, Z1_.p(), {(int64_t)n * v, v, 1}, {oo, o, v});
+  if (pcol >= 0)
+    box_copy(s_, Z1C_.p() + (int64_t)o * v, {(int64_t)nc * v, 1}, Z1_.p() + (int64_t)pcol * v,
+             {(int64_t)n * v, 1}, {oo, v});
+  k::gemm_f64(s_, false, false, v, v, nc, 1.0, LamV, nc, 0, Z1C_.p(), v, (int64_t)nc * v, 1.0,
+              r2.p, v, vv, oo);
 }
 
 // Terms bilinear in T2 with intermediates built from (t, u = 2t - t^T) and
@@ -542,11 +627,15 @@ void State::residual(const double* tv, double* rv, double* energy) {
   es_("Pkc,kicd->Pid", 1.0, Bov_.t, u_.t, 0.0, X_.t);
   es_("Pad,Pid->ia", 1.0, Bvv_.t, X_.t, 1.0, r1);                         // sum u g_adkc
   es_("klac,kilc->ia", -1.0, u_.t, gooov_.t, 1.0, r1);
+  // contractions with the Fock matrix carry O(1) x O(t) products and stay FP64
+  const int lev = es_.level();
+  es_.set_split(0, err_.as<int>());
   {
     OT Fov({o, v}, s_);
     box_copy(s_, Fov.p(), {v, 1}, F_.p() + o, {n, 1}, {o, v});
     es_("ikac,kc->ia", 1.0, u_.t, Fov.t, 1.0, r1);
   }
+  es_.set_split(lev, err_.as<int>(), tc_min_flops_);
   // ---- doubles (alpha-beta projection)
   es_.perm("aibj->ijab", 1.0, gvovo_.t, 0.0, r2);
   ladder(t2, r2);
@@ -555,6 +644,7 @@ void State::residual(const double* tv, double* rv, double* energy) {
   es_("kjbc,kiac->ijab", -0.5, t2, goovv_.t, 1.0, Z_.t);
   es_("kibc,kjac->ijab", -1.0, t2, goovv_.t, 1.0, Z_.t);
   es_("jkbc,aikc->ijab", 0.5, u_.t, Lvoov_.t, 1.0, Z_.t);
+  es_.set_split(0, err_.as<int>());
   {
     OT Fvv({v, v}, s_), Foo({o, o}, s_);
     box_copy(s_, Fvv.p(), {v, 1}, F_.p() + (int64_t)o * n + o, {n, 1}, {v, v});
@@ -562,6 +652,7 @@ void State::residual(const double* tv, double* rv, double* energy) {
     es_("ijac,bc->ijab", 1.0, t2, Fvv.t, 1.0, Z_.t);
     es_("ikab,kj->ijab", -1.0, t2, Foo.t, 1.0, Z_.t);
   }
+  es_.set_split(lev, err_.as<int>(), tc_min_flops_);
   quad_terms(t2, u_.t, Z_.t, r2, 1.0);
   if (opt_.linearize) {
     // PLASCC (Sec. II.C): remove the terms bilinear in the mixed doubles
@@ -649,7 +740,10 @@ void State::reset() {
   next_slot_ = 0;
   iter_ = 0;
   iter_low_ = 0;
+  fp64_evals_ = 0;
   polish_ = false;
+  need_refresh_ = false;
+  have_corr_ = false;
   have_prev_ = false;
   done_ = false;
   status_ = ASCC_ERR_NOT_CONVERGED;
@@ -663,8 +757,31 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
   const int m = opt_.diis_dim;
   for (int step = 0; step < max_steps && !done_; ++step) {
     const int lev = level_for_phase();
-    es_.set_split(lev, err_.as<int>());
-    residual(t_.p(), r_.p(), scal_.p());
+    bool refreshed = false;
+    if (lev == 3 && need_refresh_) {
+      // FP64 polishing: the FP64 residual and the 6-product residual at the
+      // same amplitudes; their difference corrects the following iterations
+      // (defect correction), and this step itself uses the FP64 residual.
+      mol_->ensure_fp64_ladder();  // the FP64 residual reads the FP64 (xc|bd) block
+      es_.set_split(0, err_.as<int>(), tc_min_flops_);
+      residual(t_.p(), r_.p(), scal_.p());
+      es_.set_split(3, err_.as<int>(), tc_min_flops_);
+      residual(t_.p(), corr_.p(), scal_.p() + 2);
+      k::axpby(s_, corr_.p(), r_.p(), 1.0, -1.0, N);            // corr = R64 - R3
+      k::axpby(s_, scal_.p() + 3, scal_.p(), 1.0, 0.0, 1);
+      k::axpby(s_, scal_.p() + 3, scal_.p() + 2, -1.0, 1.0, 1);  // E64 - E3
+      need_refresh_ = false;
+      have_corr_ = true;
+      refreshed = true;
+      ++fp64_evals_;
+    } else {
+      es_.set_split(lev, err_.as<int>(), tc_min_flops_);
+      residual(t_.p(), r_.p(), scal_.p());
+      if (lev == 3 && have_corr_) {
+        k::axpby(s_, r_.p(), corr_.p(), 1.0, 1.0, N);
+        k::axpby(s_, scal_.p(), scal_.p() + 3, 1.0, 1.0, 1);
+      }
+    }
     k::maxabs(s_, r_.p(), N, scal_.p() + 1, work_.p());
     double h2[2];
     int kerr = 0;
@@ -679,9 +796,14 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     const int it = iter_++;
     if (lev == 2) ++iter_low_;
     if (lev == 2 && std::isfinite(r_last_) && r_last_ <= opt_.polish_tol) {
-      // hand over to the polishing precision and re-evaluate before testing convergence
+      // hand over to the polishing precision: the stored error vectors carry the
+      // coarser residual, so the DIIS history restarts; re-evaluate (with an
+      // FP64 correction) before testing convergence
       polish_ = true;
+      need_refresh_ = true;
       have_prev_ = false;
+      slots_.clear();
+      next_slot_ = 0;
     }
     if (!std::isfinite(e_last_) || !std::isfinite(r_last_)) {
       status_ = ASCC_ERR_DIVERGED;
@@ -689,6 +811,11 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
       break;
     }
     if (have_prev_ && r_last_ <= opt_.r_tol && std::fabs(e_last_ - e_prev_) <= opt_.e_tol) {
+      if (lev == 3 && !refreshed) {
+        // converged on the corrected residual: confirm with a fresh FP64 one
+        need_refresh_ = true;
+        continue;
+      }
       status_ = ASCC_OK;
       done_ = true;
       break;
@@ -712,6 +839,7 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     double* en = hist_e_.p() + (int64_t)slot * N;
     k::jacobi(s_, tn, en, t_.p(), r_.p(), mol_->eps.p(), eps_eff_.p(), o_, v_, hole_, particle_,
               n3() ? reinterpret_cast<const int32_t*>(t3idx_.p()) : nullptr, n3());
+    k::jacobi_pairs(s_, tn, en, t_.p(), r_.p(), eps_eff_.p(), F_.p(), o_, v_, hole_, particle_);
     k::dot_rows(s_, en, hist_e_.p(), N, m, N, scal_.p() + 32, work_.p());
     std::vector<double> row(m);
     ASCC_CUDA(cudaMemcpyAsync(row.data(), scal_.p() + 32, m * sizeof(double),
@@ -746,6 +874,7 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     res->iterations = iter_;
     res->status = done_ ? status_ : ASCC_ERR_NOT_CONVERGED;
     res->iterations_low = iter_low_;
+    res->fp64_evaluations = fp64_evals_;
     res->e_ref = 0.0;
   }
   return done_ ? status_ : ASCC_ERR_NOT_CONVERGED;

@@ -2,6 +2,7 @@
 // integrals, the per-state amplitude iteration.
 #pragma once
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -55,7 +56,11 @@ struct Molecule {
   OT Bnv;    // [naux][n][v]
   OT Gext;   // [n][v][v][v], Gext[x][b][c][d] = (xc|bd)
   DevBuf Gext_bf16;  // [3][n v][v^2 padded] BF16 planes of Gext (mixed precision)
-  void make_bf16_planes();
+  // The ladder block is built on first use by a state of that precision.
+  void ensure_fp64_ladder();
+  void ensure_bf16_ladder();
+  int build_level_ = 0;
+  std::mutex mu_;
   // build_level 0 builds the bare integrals in FP64; 1..3 on the BF16 tensor
   // cores with that split level (used when the first state is mixed precision).
   Molecule(int o, int v, int naux, const double* eps_h, const double* B_src, bool on_device,
@@ -72,14 +77,15 @@ struct Options {
   double r_tol = 1e-8, e_tol = 1e-10;
   int max_iter = 200, diis_dim = 16, diis_start = 3;
   int polish_iter = 50;
-  double polish_tol = 1e-6;
+  double polish_tol = 1e-5;
 };
 
 // One state (ground or one-CSF excited) of a molecule.
 class State {
  public:
+  // xsign = -1 runs the second ansatz of Sec. II.D (S -> -S).
   State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta, const Options& opt,
-        cudaStream_t s);
+        cudaStream_t s, double xsign = 1.0);
   ~State();
 
   int64_t n1() const { return (int64_t)o_ * v_; }
@@ -93,7 +99,9 @@ class State {
   void residual(const double* t, double* r, double* energy);
   // Precision of a stand-alone residual call: FP64, or the polishing split
   // level in mixed precision.
-  void prepare_eval() { es_.set_split(opt_.precision == ASCC_MIXED_BF16 ? 3 : 0, err_.as<int>()); }
+  void prepare_eval() {
+    es_.set_split(opt_.precision == ASCC_MIXED_BF16 ? 3 : 0, err_.as<int>(), tc_min_flops_);
+  }
   ascc_status solve(ascc_result* res);
   // Iteration control: reset() loads the zeroth-order guess and clears the
   // DIIS history; iterate() runs up to max_steps residual evaluations from
@@ -135,7 +143,7 @@ class State {
   int o_, v_, n_, naux_;
   int hole_, particle_;  // -1 for the ground state
   int lh_, lp_;          // primary labels used by the partial linearisation
-  double beta_, xval_;
+  double beta_, xval_, xsign_ = 1.0;
   int nu_;               // v (+1 with the hole slot of an excited state)
   Einsum es_;
   std::vector<int32_t> t3idx_host_;
@@ -145,13 +153,16 @@ class State {
   // amplitudes, residual, DIIS
   OT t_, r_, hist_t_, hist_e_, scal_, work_, coef_, eps_eff_;
   DevBuf err_;           // int: device-side timeout codes of the tensor-core GEMM
-  bool polish_ = false;
+  bool polish_ = false, need_refresh_ = false, have_corr_ = false;
+  int fp64_evals_ = 0;
+  OT corr_;  // FP64-minus-polishing residual correction (mixed precision)
+  double tc_min_flops_ = 4e7;  // contractions below this stay FP64 (ASCC_TC_MIN_FLOPS overrides)
   int iter_low_ = 0;
   int level_for_phase() const;
   // per-iteration workspace
-  OT L_, R_, tmpB_, Bhat_, hhat_, tmpnn_, F_, dP_, J_, K_, Boo_, Bov_, Bvo_, Bvv_, Bno_, Bon_;
+  OT L_, R_, LamC_, RhoC_, rowsC_, colsC_, Bhat_, hhat_, F_, dP_, J_, K_, Boo_, Bov_, Bvo_, Bvv_, Bno_, Bon_;
   OT goooo_, gooov_, goovv_, govov_, gvovo_, gvoov_, gvvoo_, Lvoov_, Lovov_;
-  OT u_, m_, um_, Z_, WC_, WD_, Wq_, Fvv_, Foo_, X_, Y_, Yfull_, Z1_, tt_, Yoo_;
+  OT u_, m_, um_, Z_, WC_, WD_, Wq_, Fvv_, Foo_, X_, Y_, Yfull_, Z1_, tt_, Yoo_, YC_, Z1C_;
 };
 
 }  // namespace ascc

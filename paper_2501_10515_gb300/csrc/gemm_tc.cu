@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
                const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap b0,
                const __grid_constant__ CUtensorMap b1, const __grid_constant__ CUtensorMap b2,
-               Segs segs, int M, int N, int num_kt, double alpha, double beta,
-               double* __restrict__ C, long long ldc, int* err) {
+               Segs segs, int M, int N, int num_kt, int kt_chunk, double alpha, double beta,
+               double* __restrict__ C, long long ldc, float* __restrict__ ws, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -171,7 +171,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_holder;
-  const int total = segs.n * num_kt;
+  // split K: this CTA covers k-tiles [kt0, kt0 + nkt) of every segment
+  const int kt0 = blockIdx.z * kt_chunk;
+  const int nkt = max(0, min(kt_chunk, num_kt - kt0));
+  const int total = segs.n * nkt;
 
   if (warp == 0 && lane == 0) {
     // TMA producer
@@ -185,7 +188,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
         break;
       }
       if (*(volatile int*)&abort_flag) break;
-      const int seg = it / num_kt, kt = it % num_kt;
+      const int seg = it / nkt, kt = kt0 + it % nkt;
       const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
       mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
       tma_load_2d(sa, am[segs.a[seg]], full0 + 8 * s, kt * BK, m0);
@@ -219,23 +222,41 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // tcgen05.ld is warp-collective: take the decision per warp
   const bool go = __all_sync(0xffffffffu, ok) && !*(volatile int*)&abort_flag;
-  if (go) {
+  if (go && total > 0) {
     const int row = m0 + warp * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t r[16];
       tmem_ld16(taddr + c0, r);
       if (row < M) {
-        double* crow = C + (long long)row * ldc;
+        if (ws) {
+          // split-K partial, summed later in FP64
+          float* wrow = ws + ((long long)blockIdx.z * M + row) * N;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < N) {
-            const double acc = (double)__uint_as_float(r[j]);
-            crow[col] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * crow[col]);
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < N) wrow[col] = __uint_as_float(r[j]);
+          }
+        } else {
+          double* crow = C + (long long)row * ldc;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < N) {
+              const double acc = (double)__uint_as_float(r[j]);
+              crow[col] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * crow[col]);
+            }
           }
         }
       }
+    }
+  } else if (go && ws) {
+    // an empty chunk (K shorter than the grid) contributes zeros
+    const int row = m0 + warp * 32 + lane;
+    if (row < M) {
+      float* wrow = ws + ((long long)blockIdx.z * M + row) * N;
+      for (int j = 0; j < BN; ++j)
+        if (n0 + j < N) wrow[n0 + j] = 0.f;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -247,10 +268,26 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
   }
 }
 
+// C = alpha * sum_z ws[z] + beta * C, the split-K partials summed in FP64 in a
+// fixed order.
+__global__ void splitk_reduce_kernel(double* __restrict__ C, long long ldc,
+                                     const float* __restrict__ ws, long long M, long long N,
+                                     int nz, double alpha, double beta) {
+  const long long total = M * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < nz; ++z) acc += (double)ws[(long long)z * total + idx];
+    const long long m = idx / N, n = idx % N;
+    double* c = C + m * ldc + n;
+    *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *c);
+  }
+}
+
 // FP64 [rows][K] (row stride ld) -> nsplit BF16 planes [nsplit][rows][Kp], zero padded.
 __global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double* __restrict__ in,
                                   long long rows, long long K, long long ld, long long Kp,
-                                  int nsplit) {
+                                  int nsplit, long long plane_stride) {
   const long long total = rows * Kp;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -258,7 +295,7 @@ __global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double*
     double x = (k < K) ? in[r * ld + k] : 0.0;
     for (int s = 0; s < nsplit; ++s) {
       const __nv_bfloat16 h = __double2bfloat16(x);
-      out[(long long)s * total + idx] = h;
+      out[(long long)s * plane_stride + idx] = h;
       x -= (double)__bfloat162float(h);
     }
   }
@@ -297,29 +334,42 @@ CUtensorMap make_map(const __nv_bfloat16* base, int64_t rows, int64_t Kp, int bo
 int64_t padded_k(int64_t K) { return (K + BK - 1) / BK * BK; }
 
 void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t rows, int64_t K,
-                int64_t ld, int nsplit) {
+                int64_t ld, int nsplit, int64_t plane_stride) {
   const int64_t Kp = padded_k(K), total = rows * Kp;
   if (total == 0) return;
+  if (plane_stride <= 0) plane_stride = total;
   int64_t g = (total + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
-  split_bf16_kernel<<<(int)g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit);
+  split_bf16_kernel<<<(int)g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit, plane_stride);
   count_launch();
   check_launch("split_bf16");
 }
 
 int products_for(int level) { return level == 1 ? 1 : level == 2 ? 3 : 6; }
 
+int splitk_for(int64_t M, int64_t N, int64_t K) {
+  // K chunks of at most 2048 (FP32 accumulation error ~ 2^-24 sqrt(K/16) per chunk),
+  // and enough CTAs to fill the GPU for small M x N
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int64_t num_kt = (K + BK - 1) / BK;
+  int64_t z = (K + 2047) / 2048;
+  while (tiles * z < 2 * 152 && z < num_kt) ++z;
+  return (int)std::min<int64_t>(std::max<int64_t>(z, 1), std::min<int64_t>(num_kt, 512));
+}
+
 void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
                 const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C, int64_t ldc,
-                int* err) {
+                int* err, int splitk, float* ws) {
   ASCC_REQUIRE(level >= 1 && level <= 3, "split level 1..3");
   ASCC_REQUIRE(M > 0 && N > 0 && K > 0, "gemm_split: empty");
-  static bool attr_set = false;
-  if (!attr_set) {
-    ASCC_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   SMEM_BYTES));
-    attr_set = true;
-  }
+  ASCC_REQUIRE(splitk >= 1 && (splitk == 1 || ws), "gemm_split: split-K needs a workspace");
+  static std::once_flag attr_once;
+  cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    attr_err = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES);
+  });
+  ASCC_CUDA(attr_err);
   const int64_t Kp = padded_k(K);
   CUtensorMap am[3], bm[3];
   for (int u = 0; u < 3; ++u) {
@@ -337,13 +387,23 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
     sg = {6, {2, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
   }
   count_flops(2.0 * (double)M * N * K * sg.n);
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN));
+  const int num_kt = (int)(Kp / BK);
+  const int kt_chunk = (num_kt + splitk - 1) / splitk;
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splitk);
   ASCC_REQUIRE(grid.y <= 65535, "gemm_split: N too large");
   gemm_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(am[0], am[1], am[2], bm[0], bm[1], bm[2], sg,
-                                                    (int)M, (int)N, (int)(Kp / BK), alpha, beta, C,
-                                                    (long long)ldc, err);
+                                                    (int)M, (int)N, num_kt, kt_chunk, alpha, beta,
+                                                    C, (long long)ldc, splitk > 1 ? ws : nullptr,
+                                                    err);
   count_launch();
   check_launch("gemm_tc");
+  if (splitk > 1) {
+    int64_t g = (M * N + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    splitk_reduce_kernel<<<(int)g, 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk, alpha, beta);
+    count_launch();
+    check_launch("splitk_reduce");
+  }
 }
 
 }  // namespace tc

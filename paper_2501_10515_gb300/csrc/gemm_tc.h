@@ -14,17 +14,24 @@ int64_t padded_k(int64_t K);
 // Number of BF16 x BF16 products a split level uses (1, 3 or 6).
 int products_for(int level);
 
-// out[s][r][0..Kp) = s-th BF16 plane of in[r][0..K) (row stride ld), zero
-// padded to Kp; s < nsplit.  x = sum_s plane_s up to the last plane's rounding.
+// out[s * plane_stride + r * Kp + k] = s-th BF16 plane of in[r][k] (row stride
+// ld), zero padded to Kp; s < nsplit; plane_stride <= 0 means rows * Kp.
+// x = sum_s plane_s up to the last plane's rounding.
 void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t rows, int64_t K,
-                int64_t ld, int nsplit);
+                int64_t ld, int nsplit, int64_t plane_stride = 0);
 
 // C[M][N] (FP64, row stride ldc) = alpha * A B^T + beta * C with A [level][M][Kp] and
 // B [level][N][Kp] BF16 planes from split_bf16 (K-major).  err: device int that
 // receives a nonzero code if a bounded wait inside the kernel gives up.
+// splitk > 1 splits K over the grid: each chunk's FP32 accumulator goes to
+// ws [splitk][M][N] (FP32) and the chunks are summed in FP64 afterwards, which
+// bounds the FP32 accumulation error by the chunk length.
 void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
                 const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C,
-                int64_t ldc, int* err);
+                int64_t ldc, int* err, int splitk = 1, float* ws = nullptr);
+
+// Number of K chunks the residual engine uses for an M x N x K product.
+int splitk_for(int64_t M, int64_t N, int64_t K);
 
 }  // namespace tc
 }  // namespace ascc

@@ -50,6 +50,20 @@ void jacobi(cudaStream_t s, double* tn, double* e, const double* t,
             const double* r, const double* eps, const double* eps_eff, int o,
             int v, int hole, int particle, const int32_t* t3idx, int64_t n3);
 
+// out[r][j] = M[r][c_j] - delta(r, c_j) for the columns c_j = j (j < nlo) and
+// c_j = extra (j = nlo, when nc = nlo + 1) of an n x n matrix M.
+void cols_minus_identity(cudaStream_t s, double* out, const double* M, int n, int nlo, int extra,
+                         int nc);
+
+// Overwrites the steps of the pairs (t1[i][a], t2[i][h][a][p] = t2[h][i][p][a])
+// of a one-CSF state with the solution of the 2 x 2 model Jacobian
+//   [[-D1, c F_hp], [q, -D2]]  (c = 2, q = 0 if i != h and a != p; c = 1,
+//   q = F_ph if exactly one of them is primary; [[0, F_hp], [2 F_hp, 0]] for
+//   (h, p)), D from eps_eff and F the dressed Fock matrix (n x n).  A
+//   near-singular pair keeps its diagonal step.  No-op for hole < 0.
+void jacobi_pairs(cudaStream_t s, double* tn, double* e, const double* t, const double* r,
+                  const double* eps_eff, const double* F, int o, int v, int hole, int particle);
+
 // d[P] = sum_k B[P][k][k]
 void diag_sum(cudaStream_t s, double* d, const double* B, int naux, int n, int o);
 

@@ -98,6 +98,20 @@ gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
   }
 }
 
+// C = alpha * sum_z ws[z] + beta * C for z slices of M x N (fixed summation order).
+__global__ void reduce_slices_kernel(double* C, int64_t ldc, const double* ws, int64_t M,
+                                     int64_t N, int z, double alpha, double beta) {
+  const int64_t total = M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < z; ++q) acc += ws[(int64_t)q * total + idx];
+    const int64_t m = idx / N, n = idx % N;
+    double* c = C + m * ldc + n;
+    *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *c);
+  }
+}
+
 struct Strides {
   int nd;
   int64_t shape[8];
@@ -301,6 +315,58 @@ __global__ void jacobi_kernel(double* tn, double* e, const double* t, const doub
   }
 }
 
+// Pair step of a one-CSF state: (t1[i][a], t2[i][h][a][p]) solve a 2 x 2
+// model Jacobian [[-D1, c F_hp], [q, -D2]] (see jacobi_pairs in kernels.h).
+__global__ void pair_step_kernel(double* tn, double* e, const double* t, const double* r,
+                                 const double* eps_eff, const double* F, int o, int v, int hole,
+                                 int particle) {
+  const int n = o + v;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= o * v) return;
+  const int i = idx / v, a = idx % v, h = hole, p = particle;
+  const int64_t n1 = (int64_t)o * v, vv = (int64_t)v * v;
+  const double fhp = F[(int64_t)h * n + o + p], fph = F[(int64_t)(o + p) * n + h];
+  double J00, J01, J10, J11;
+  if (i == h && a == p) {
+    J00 = 0.0; J01 = fhp; J10 = 2.0 * fhp; J11 = 0.0;
+  } else {
+    const bool mixed = (i == h) || (a == p);
+    J00 = -(eps_eff[i] - eps_eff[o + a]);
+    J11 = -(eps_eff[i] + eps_eff[h] - eps_eff[o + a] - eps_eff[o + p]);
+    J01 = (mixed ? 1.0 : 2.0) * fhp;
+    J10 = mixed ? fph : 0.0;
+  }
+  const double det = J00 * J11 - J01 * J10;
+  const double mx = fmax(fmax(fabs(J00), fabs(J01)), fmax(fabs(J10), fabs(J11)));
+  if (!(fabs(det) > 1e-12 * mx * mx)) return;  // keep the diagonal step
+  const int64_t q1 = (int64_t)i * v + a;
+  const int64_t q2 = n1 + (((int64_t)i * o + h) * v + a) * v + p;
+  const int64_t q2s = n1 + (((int64_t)h * o + i) * v + p) * v + a;
+  const double r1 = r[q1], r2 = r[q2];
+  const double d1 = -(J11 * r1 - J01 * r2) / det;
+  const double d2 = -(-J10 * r1 + J00 * r2) / det;
+  tn[q1] = t[q1] + d1;
+  e[q1] = d1;
+  tn[q2] = t[q2] + d2;
+  e[q2] = d2;
+  if (q2s != q2) {
+    tn[q2s] = t[q2s] + d2;
+    e[q2s] = d2;
+  }
+  (void)vv;
+}
+
+// out[r][j] = M[r][cols[j]] - (r == cols[j]) for an n x n matrix M.
+__global__ void cols_minus_identity_kernel(double* out, const double* M, int n, int c0, int nlo,
+                                           int extra, int nc) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * nc;
+       idx += gridDim.x * blockDim.x) {
+    const int r = idx / nc, j = idx % nc;
+    const int c = j < nlo ? c0 + j : extra;
+    out[idx] = M[(int64_t)r * n + c] - (r == c ? 1.0 : 0.0);
+  }
+}
+
 __global__ void diag_sum_kernel(double* d, const double* B, int naux, int n, int o) {
   const int P = blockIdx.x * blockDim.x + threadIdx.x;
   if (P >= naux) return;
@@ -346,6 +412,32 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
     return;
   }
   count_flops(2.0 * (double)M * (double)N * (double)K * (double)batch);
+  // split K over the grid when the output has too few 64 x 64 tiles to fill the
+  // GPU: K is cut into z equal chunks (z divides K), each chunk's product goes
+  // to its own FP64 slice and the slices are summed in a fixed order
+  const int64_t tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+  if (batch == 1 && tiles < 152 && K >= 2048) {
+    int64_t zmax = std::min<int64_t>(2 * 152 / tiles, K / 256);
+    int64_t z = 1;
+    for (int64_t c = zmax; c >= 2; --c)
+      if (K % c == 0) {
+        z = c;
+        break;
+      }
+    if (z >= 2) {
+      const int64_t kc = K / z;
+      double* ws = nullptr;
+      ASCC_CUDA(cudaMallocAsync(&ws, sizeof(double) * (size_t)(z * M * N), s));
+      gemm_f64(s, ta, tb, M, N, kc, 1.0, A, lda, ta ? kc * lda : kc, B, ldb, tb ? kc : kc * ldb,
+               0.0, ws, N, M * N, z);
+      count_flops(-2.0 * (double)M * (double)N * (double)K);  // counted above already
+      reduce_slices_kernel<<<grid_for(M * N), 256, 0, s>>>(C, ldc, ws, M, N, (int)z, alpha, beta);
+      count_launch();
+      check_launch("reduce_slices");
+      ASCC_CUDA(cudaFreeAsync(ws, s));
+      return;
+    }
+  }
   dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM), 1);
   for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
     const int64_t nb = std::min<int64_t>(65535, batch - b0);
@@ -451,6 +543,23 @@ void jacobi(cudaStream_t s, double* tn, double* e, const double* t, const double
                                                 t3idx, n3);
   count_launch();
   check_launch("jacobi");
+}
+
+void cols_minus_identity(cudaStream_t s, double* out, const double* M, int n, int nlo, int extra,
+                         int nc) {
+  cols_minus_identity_kernel<<<grid_for((int64_t)n * nc), 256, 0, s>>>(out, M, n, 0, nlo, extra,
+                                                                        nc);
+  count_launch();
+  check_launch("cols_minus_identity");
+}
+
+void jacobi_pairs(cudaStream_t s, double* tn, double* e, const double* t, const double* r,
+                  const double* eps_eff, const double* F, int o, int v, int hole, int particle) {
+  if (hole < 0) return;
+  pair_step_kernel<<<(o * v + 127) / 128, 128, 0, s>>>(tn, e, t, r, eps_eff, F, o, v, hole,
+                                                       particle);
+  count_launch();
+  check_launch("pair_step");
 }
 
 void diag_sum(cudaStream_t s, double* d, const double* B, int naux, int n, int o) {

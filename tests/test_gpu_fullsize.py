@@ -1,0 +1,56 @@
+"""Parity at the full o=20, v=200 (naux 660) size the benchmark times.
+
+The oracle evaluates one residual of the same state at the same amplitudes
+(the zeroth-order guess plus a small seeded perturbation) on the host; the CUDA
+path must match it element by element: FP64 to 1e-9 in relative residual norm
+and 1e-10 Eh in energy, mixed precision to 5e-6 and 1e-8 Eh.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import amplitudes as amp
+from oracle import ascc as oracle_ascc
+from oracle import spinadapted as sa
+
+pytestmark = pytest.mark.gpu
+
+O, V, SEED = 20, 200, 0
+
+
+@pytest.fixture(scope="module")
+def system():
+    return synth.make_system(O, V, seed=SEED)
+
+
+def _amps(hole, part):
+    t1, t2, _ = amp.initial_guess(O, V, hole, part)
+    d1, d2, _ = synth.random_amplitudes(O, V, seed=77, scale=2e-4)
+    return t1 + d1, t2 + d2
+
+
+def _oracle(s, hole, part, t1, t2, lh, lp):
+    hbar, Bbar, _ = oracle_ascc.prepare(s.eps, s.B, O, hole, part)
+    return sa.residual(hbar, Bbar, O, t1, t2, linearize=True, hole=lh, particle=lp)
+
+
+@pytest.mark.parametrize("exc", [(19, 3), None])
+def test_fullsize_residual_fp64_and_mixed(system, exc):
+    import paper_2501_10515_gb300 as pkg
+    s = system
+    hole, part = exc if exc else (None, None)
+    lh, lp = (19, 3)
+    t1, t2 = _amps(hole, part)
+    Eo, r1o, r2o, _ = _oracle(s, hole, part, t1, t2, lh, lp)
+    Ro = np.concatenate([r1o.ravel(), r2o.ravel()])
+    kw = dict(linearize=1)
+    if exc is None:
+        kw.update(pl_hole=lh, pl_particle=lp)
+    for prec, rtol, etol in [(pkg.ASCC_FP64, 1e-9, 1e-10), (pkg.ASCC_MIXED_BF16, 5e-6, 1e-8)]:
+        ctx = pkg.Context(O, V, s.naux, s.eps, s.B, hole=hole, particle=part, precision=prec, **kw)
+        E, r1, r2, _ = ctx.residual(t1, t2)
+        ctx.close()
+        R = np.concatenate([r1.ravel(), r2.ravel()])
+        rel = np.linalg.norm(R - Ro) / np.linalg.norm(Ro)
+        assert rel <= rtol, (prec, rel, abs(E - Eo))
+        assert abs(E - Eo) <= etol, (prec, rel, abs(E - Eo))

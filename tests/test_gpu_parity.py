@@ -101,3 +101,18 @@ def test_sibling_state_shares_molecule():
     ref = _ctx(s, 3, 0, linearize=1)
     E2, q1, q2, _ = ref.residual(t1, t2)
     assert E == E2 and np.array_equal(r2, q2)
+
+
+@pytest.mark.parametrize("ansatz", [0, 1])
+def test_second_ansatz_matches_oracle(ansatz):
+    """Sec. II.D: the two ansatz choices for an Aufbau weight alpha, and their average."""
+    o, v, alpha = 4, 20, 0.1
+    s = synth.make_system(o, v, seed=0)
+    beta, sign = oracle_ascc.ansatz_beta(alpha, ansatz)
+    ref = oracle_ascc.solve_state(s.eps, s.B, o, 3, 0, linearize=True, beta=beta, xsign=sign)
+    ctx = _ctx(s, 3, 0, linearize=1, alpha=alpha, ansatz=ansatz)
+    res = ctx.solve()
+    assert ref.converged and res.status == 0
+    assert abs(res.energy - ref.energy) <= E_TOL
+    import paper_2501_10515_gb300 as pkg
+    assert pkg.two_ansatz_average(res.energy, 0, 1.0, 4) == res.energy

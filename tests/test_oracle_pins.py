@@ -304,3 +304,24 @@ def test_invariance_to_nonprimary_occupied_rotation():
     rot = solver.solve(fn, eps_rot, o, t1, t2, t3, **kw)
     assert ref.converged and rot.converged
     assert rot.energy == pytest.approx(ref.energy, abs=1e-9)
+
+
+def test_second_ansatz_reference_has_the_same_aufbau_weight():
+    """Both ansatz choices of Sec. II.D build alpha phi0 + S phi0 (up to normalisation)."""
+    o, v = 2, 3
+    sp = bf.DetSpace(o, v)
+    hole, part = 1, 0
+    alpha = 0.15
+    r = 1 / math.sqrt(2)
+    h_, p_ = hole, o + part
+    S = sp.string_matrix([(r, [(sp.spin_orb(p_, s), True), (sp.spin_orb(h_, s), False)]) for s in (0, 1)])
+    Sd = S.T.tocsr()
+    ref = np.zeros(sp.dim); ref[sp.ref] = 1.0
+    want = alpha * ref + S @ ref
+    for ans in (0, 1):
+        beta, sign = ascc.ansatz_beta(alpha, ans)
+        t1, t2, _ = amp.initial_guess(o, v, hole, part, beta=beta, xsign=sign)
+        T = sp.string_matrix(sp.cluster_strings(t1, t2))
+        psi = sp.exp_apply(sign * Sd, sp.exp_apply(T, ref, +1.0), -1.0)
+        k = np.argmax(np.abs(want))
+        assert np.allclose(psi / psi[k] * want[k], want, atol=1e-14)
