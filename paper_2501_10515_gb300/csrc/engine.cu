@@ -63,6 +63,12 @@ void box_copy(cudaStream_t s, double* out, std::vector<int64_t> ostride, const d
                   alpha, beta);
 }
 
+void* Einsum::scratch(int which, size_t bytes) const {
+  DevBuf& b = scratch_[which];
+  if (b.bytes() < bytes) b.alloc(bytes + bytes / 8, s_);
+  return b.as<void>();
+}
+
 void Einsum::perm(const char* spec, double alpha, const T& A, double beta, const T& C) const {
   Spec sp = parse(spec, false);
   ASCC_REQUIRE((int)sp.a.size() == A.nd() && (int)sp.c.size() == C.nd(), "perm: rank");
@@ -163,19 +169,17 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
       Bn = Bn_t.p();
     }
     const int64_t Kp = tc::padded_k(Ks);
-    DevBuf pa(sizeof(__nv_bfloat16) * (size_t)(level_ * Ms * Kp), s_);
-    DevBuf pb(sizeof(__nv_bfloat16) * (size_t)(level_ * Ns * Kp), s_);
-    tc::split_bf16(s_, pa.as<__nv_bfloat16>(), Am, Ms, Ks, Ks, level_);
-    tc::split_bf16(s_, pb.as<__nv_bfloat16>(), Bn, Ns, Ks, Ks, level_);
+    auto* pa = static_cast<__nv_bfloat16*>(scratch(0, sizeof(__nv_bfloat16) * (size_t)(level_ * Ms * Kp)));
+    auto* pb = static_cast<__nv_bfloat16*>(scratch(1, sizeof(__nv_bfloat16) * (size_t)(level_ * Ns * Kp)));
+    tc::split_bf16(s_, pa, Am, Ms, Ks, Ks, level_);
+    tc::split_bf16(s_, pb, Bn, Ns, Ks, Ks, level_);
     const int z = tc::splitk_for(Ms, Ns, Ks);
-    DevBuf ws(z > 1 ? sizeof(float) * (size_t)(z * Ms * Ns) : 0, s_);
+    float* ws = z > 1 ? static_cast<float*>(scratch(2, sizeof(float) * (size_t)(z * Ms * Ns))) : nullptr;
     if (sp.c == cl) {
-      tc::gemm_split(s_, Ms, Ns, Ks, level_, alpha, pa.as<__nv_bfloat16>(),
-                     pb.as<__nv_bfloat16>(), beta, C.p, Ns, err_, z, ws.as<float>());
+      tc::gemm_split(s_, Ms, Ns, Ks, level_, alpha, pa, pb, beta, C.p, Ns, err_, z, ws);
     } else {
       OT Ct(shape_of(cl), s_);
-      tc::gemm_split(s_, Ms, Ns, Ks, level_, 1.0, pa.as<__nv_bfloat16>(), pb.as<__nv_bfloat16>(),
-                     0.0, Ct.p(), Ns, err_, z, ws.as<float>());
+      tc::gemm_split(s_, Ms, Ns, Ks, level_, 1.0, pa, pb, 0.0, Ct.p(), Ns, err_, z, ws);
       perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
     }
     return;
@@ -521,14 +525,16 @@ void State::ladder(const T& t2, const T& r2) {
   if (es_.level() > 0) {
     const int lev = es_.level();
     const int64_t K = vv, Kp = tc::padded_k(K), rows = (int64_t)n * v;
-    DevBuf pa(sizeof(__nv_bfloat16) * (size_t)(lev * (int64_t)o * o * Kp), s_);
-    tc::split_bf16(s_, pa.as<__nv_bfloat16>(), t2.p, (int64_t)o * o, K, K, lev);
+    auto* pa = static_cast<__nv_bfloat16*>(
+        es_.scratch(0, sizeof(__nv_bfloat16) * (size_t)(lev * (int64_t)o * o * Kp)));
+    tc::split_bf16(s_, pa, t2.p, (int64_t)o * o, K, K, lev);
     // planes of Gext are stored [3][rows][Kp]; the kernel reads planes 0..lev-1
     const int z = tc::splitk_for((int64_t)o * o, rows, K);
-    DevBuf ws(z > 1 ? sizeof(float) * (size_t)(z * (int64_t)o * o * rows) : 0, s_);
-    tc::gemm_split(s_, (int64_t)o * o, rows, K, lev, 1.0, pa.as<__nv_bfloat16>(),
-                   M.Gext_bf16.as<__nv_bfloat16>(), 0.0, Y_.p(), rows, err_.as<int>(), z,
-                   ws.as<float>());
+    float* ws = z > 1 ? static_cast<float*>(
+                            es_.scratch(2, sizeof(float) * (size_t)(z * (int64_t)o * o * rows)))
+                      : nullptr;
+    tc::gemm_split(s_, (int64_t)o * o, rows, K, lev, 1.0, pa, M.Gext_bf16.as<__nv_bfloat16>(), 0.0,
+                   Y_.p(), rows, err_.as<int>(), z, ws);
   } else {
     es_("ijcd,xbcd->ijxb", 1.0, t2, M.Gext.t, 0.0, Y_.t);
   }

@@ -31,12 +31,16 @@ class Einsum {
     min_flops_ = min_flops;
   }
   int level() const { return level_; }
+  // Scratch of the tensor-core path, grown on demand and reused by every call
+  // on this stream (calls on one stream never overlap).
+  void* scratch(int which, size_t bytes) const;
 
  private:
   cudaStream_t s_;
   int level_ = 0;
   int* err_ = nullptr;
   double min_flops_ = 4e7;
+  mutable DevBuf scratch_[3];
 };
 
 // Copies a strided box of `in` into `out` (both with explicit strides).
