@@ -38,6 +38,8 @@ WORKLOADS = {
                name="ascc-fp64 o=20 v=200 naux=660 excitation 19->3 (PLASCC)"),
     "c1": dict(o=4, v=20, seed=0, hole=3, particle=0,
                name="ascc-fp64 o=4 v=20 naux=72 excitation 3->0 (PLASCC)"),
+    "c3": dict(o=30, v=300, seed=0, hole=29, particle=0,
+               name="ascc-mixed o=30 v=300 naux=990 excitation 29->0 (PLASCC)"),
 }
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -186,6 +188,16 @@ def run_reference(args, wl):
     return 0
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The timed region of a step is the slowest rank's (replicas share no data)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def golden_energy(name):
     path = os.path.join(ROOT, "tests", "golden", "reference_energies.txt")
     if not os.path.exists(path):
@@ -255,13 +267,41 @@ def run_server_workload(args, kind):
     return 0
 
 
+def run_gemm(args):
+    """The split-BF16 tensor-core GEMM alone on the ladder's shape class (M = o^2 = 400,
+    N = (o+v) v = 44000) with K = 4096, inputs larger than L2."""
+    import torch
+    import paper_2501_10515_gb300 as pkg
+    M, N, K, lev = 400, 44000, 4096, args.level
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn(M, K, device="cuda", dtype=torch.float64, generator=g)
+    B = torch.randn(N, K, device="cuda", dtype=torch.float64, generator=g)
+    C = torch.zeros(M, N, device="cuda", dtype=torch.float64)
+    for _ in range(args.warmup):
+        pkg.gemm_split_bf16(A, B, C, lev)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pkg.gemm_split_bf16(A, B, C, lev)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    products = {1: 1, 2: 3, 3: 6}[lev]
+    tf = 2.0 * M * N * K * products / (ms / 1e3) / 1e12
+    print(json.dumps({"kernel": "split-BF16 tcgen05 GEMM incl. operand split and K reduction",
+                      "M": M, "N": N, "K": K, "level": lev, "products": products,
+                      "ms": ms, "tflops": tf, "frac_of_bf16_burst": tf / 1977.2}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["batch", "serve", "gemm"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--step", default="solve", choices=["solve", "iteration"])
     ap.add_argument("--e2e-steps", type=int, default=1)
@@ -271,10 +311,13 @@ def main():
     ap.add_argument("--rate", type=float, default=1.0)
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=180.0)
+    ap.add_argument("--level", type=int, default=2)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload in ("batch", "serve"):
         return run_server_workload(args, args.workload)
+    if args.workload == "gemm":
+        return run_gemm(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -328,11 +371,7 @@ def main():
     ctx.set_profiling(False)
     p1 = ctx.profile()
     per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    ms = sum(per)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(per), dist, "cuda")
     units = world * args.steps
     flops = p1.gemm_flops - p0.gemm_flops
     tflops = world * flops / (ms / 1e3) / 1e12
@@ -356,13 +395,14 @@ def main():
     eps_p, B_p = pin(s.eps), pin(s.B)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    e2e_energy = None
     for _ in range(args.e2e_steps):
         c2 = pkg.Context(o, v, s.naux, eps_p, B_p, hole=wl["hole"], particle=wl["particle"],
                          linearize=1, precision=prec)
         r2 = c2.solve()
         e2e_energy = r2.energy
         c2.close()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
 
     # the plain FP64 path on the same state: a few iterations, for the comparison
     fp64 = None
@@ -396,7 +436,7 @@ def main():
                             if args.step == "solve" else
                             "one solve iteration (residual + convergence test + Jacobi + DIIS)")},
         "clocks": clocks,
-        "e2e": {"value": (1.0 / e2e_s) if args.step == "solve" else None,
+        "e2e": {"value": (1.0 / e2e_s) if (args.step == "solve" and args.e2e_steps) else None,
                 "unit": "solves/s",
                 "h2d_bytes_per_step": int(eps_p.nbytes + B_p.nbytes), "d2h_bytes_per_step": 56},
         "gpu_launches": int(p1.launches - p0.launches),

@@ -1,0 +1,69 @@
+"""Multi-process host logic of the bench's replica mode, on CPU with gloo.
+
+The hot path does not shard (one solve per GPU, no exchange step), so N GPUs
+run N independent replicas and the only collective is the max-over-ranks of
+the timed region.  These tests run that reduction with world_size 2 on the
+gloo backend, plus the reference arm's rule that only rank 0 works.
+"""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r reports a step time of 10 (r + 1) ms: every rank must see the slowest
+        ms = bench.max_over_ranks(10.0 * (rank + 1), dist, "cpu")
+        q.put((rank, ms))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    assert got == {0: 20.0, 1: 20.0}
+
+
+def test_max_over_ranks_single_process_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5) == 12.5
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+
+    class A:
+        steps, warmup = 1, 3
+
+    assert bench.run_reference(A(), bench.WORKLOADS["c1"]) == 0
+    assert capsys.readouterr().out == ""
