@@ -136,6 +136,9 @@ ascc_status ascc_t3p_indices(const ascc_ctx* ctx, int32_t* idx);
  * context's options say so) at caller-given amplitudes.
  *   t1, t2, t3p  inputs; r1, r2, r3p, energy outputs (any may be NULL
  *   except t1, t2; t3p may be NULL when ascc_t3p_size is 0).
+ *   t2 [o][o][v][v] must have the pair symmetry of closed-shell spin-adapted
+ *   doubles, t2[i][j][a][b] = t2[j][i][b][a]: the particle-particle ladder
+ *   is evaluated for the pairs i <= j only and the rest follows from it.
  * ascc_residual takes host buffers; ascc_residual_device takes device
  * buffers and does not synchronise the stream. */
 ascc_status ascc_residual(ascc_ctx* ctx, const double* t1, const double* t2,

@@ -237,7 +237,18 @@ void Molecule::ensure_fp64_ladder() {
   Einsum es(stream);
   Gext.make({n, v, v, v}, stream);
   es.set_split(0, err.as<int>(), 0.0);
-  es("Pxc,Pbd->xbcd", 1.0, Bnv.t, Bvv.t, 0.0, Gext.t);
+  // x-chunks keep the GEMM's permutation temporary at ~1 GB
+  const int64_t v3 = (int64_t)v * v * v;
+  int64_t xc = std::max<int64_t>(1, ((int64_t)1 << 27) / v3);
+  xc = std::min<int64_t>(xc, n);
+  OT Ac({naux, xc, v}, stream);
+  for (int64_t x0 = 0; x0 < n; x0 += xc) {
+    const int64_t nx = std::min<int64_t>(xc, n - x0);
+    T a(Ac.p(), {naux, nx, v}), gch(Gext.p() + x0 * v3, {nx, v, v, v});
+    box_copy(stream, Ac.p(), {nx * v, v, 1}, Bnv.p() + x0 * v, {(int64_t)n * v, v, 1},
+             {naux, nx, v});
+    es("Pxc,Pbd->xbcd", 1.0, a, Bvv.t, 0.0, gch);
+  }
   ASCC_CUDA(cudaStreamSynchronize(stream));
 }
 
@@ -353,7 +364,10 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   u_.make({o, o, v, v}, s); Z_.make({o, o, v, v}, s);
   WC_.make({o, o, v, v}, s); WD_.make({v, o, o, v}, s); Wq_.make({o, o, o, o}, s);
   Fvv_.make({v, v}, s); Foo_.make({o, o}, s); X_.make({P, o, v}, s);
-  Y_.make({o, o, n, v}, s); Yfull_.make({o, o, n, n}, s); Z1_.make({o, o, n, v}, s);
+  Y_.make({o, o, n, v}, s);
+  tpair_.make({(int64_t)o * (o + 1) / 2, (int64_t)v * v}, s);
+  Yvv_.make({(int64_t)o * (o + 1) / 2, (int64_t)v * v}, s);
+  Yov_.make({(int64_t)o * o, (int64_t)o * v}, s); Yfull_.make({o, o, n, n}, s); Z1_.make({o, o, n, v}, s);
   {
     const int nc = o + (hole_ >= 0 ? 1 : 0);
     YC_.make({o, o, n, nc}, s); Z1C_.make({o, o, nc, v}, s);
@@ -522,27 +536,48 @@ void State::ladder(const T& t2, const T& r2) {
     ASCC_CUDA(cudaEventCreate(&ev1));
     ASCC_CUDA(cudaEventRecord(ev0, s_));
   }
+  // (xc|bd) = (bd|xc) and t_ji^dc = t_ij^cd give Y_ji^{ab} = Y_ij^{ba} for the
+  // virtual rows x = o+a: those come from the o(o+1)/2 pairs i <= j only; the
+  // occupied rows x = k need every pair.
+  const int64_t npair = (int64_t)o * (o + 1) / 2, ovr = (int64_t)o * v, vvr = vv;
+  k::gather_pairs(s_, tpair_.p(), t2.p, o, vv);
   if (es_.level() > 0) {
     const int lev = es_.level();
     const int64_t K = vv, Kp = tc::padded_k(K), rows = (int64_t)n * v;
+    // planes of Gext are stored [3][rows][Kp]; the kernel reads planes 0..lev-1
+    const __nv_bfloat16* G = M.Gext_bf16.as<__nv_bfloat16>();
     auto* pa = static_cast<__nv_bfloat16*>(
         es_.scratch(0, sizeof(__nv_bfloat16) * (size_t)(lev * (int64_t)o * o * Kp)));
+    // occupied rows: all pairs
     tc::split_bf16(s_, pa, t2.p, (int64_t)o * o, K, K, lev);
-    // planes of Gext are stored [3][rows][Kp]; the kernel reads planes 0..lev-1
-    const int z = tc::splitk_for((int64_t)o * o, rows, K);
+    int z = tc::splitk_for((int64_t)o * o, ovr, K);
     float* ws = z > 1 ? static_cast<float*>(
-                            es_.scratch(2, sizeof(float) * (size_t)(z * (int64_t)o * o * rows)))
+                            es_.scratch(2, sizeof(float) * (size_t)(z * (int64_t)o * o * ovr)))
                       : nullptr;
-    tc::gemm_split(s_, (int64_t)o * o, rows, K, lev, 1.0, pa, M.Gext_bf16.as<__nv_bfloat16>(), 0.0,
-                   Y_.p(), rows, err_.as<int>(), z, ws);
+    tc::gemm_split(s_, (int64_t)o * o, ovr, K, lev, 1.0, pa, G, 0.0, Yov_.p(), ovr, err_.as<int>(),
+                   z, ws, rows * Kp);
+    // virtual rows: pairs i <= j
+    tc::split_bf16(s_, pa, tpair_.p(), npair, K, K, lev);
+    z = tc::splitk_for(npair, vvr, K);
+    ws = z > 1 ? static_cast<float*>(es_.scratch(2, sizeof(float) * (size_t)(z * npair * vvr)))
+               : nullptr;
+    tc::gemm_split(s_, npair, vvr, K, lev, 1.0, pa, G + ovr * Kp, 0.0, Yvv_.p(), vvr,
+                   err_.as<int>(), z, ws, rows * Kp);
   } else {
-    es_("ijcd,xbcd->ijxb", 1.0, t2, M.Gext.t, 0.0, Y_.t);
+    const double* G = M.Gext.p();
+    k::gemm_f64(s_, false, true, (int64_t)o * o, ovr, vv, 1.0, t2.p, vv, 0, G, vv, 0, 0.0,
+                Yov_.p(), ovr, 0, 1);
+    k::gemm_f64(s_, false, true, npair, vvr, vv, 1.0, tpair_.p(), vv, 0, G + ovr * vv, vv,
+                0, 0.0, Yvv_.p(), vvr, 0, 1);
   }
+  // Y[i][j][k][b] = Yov[ij][k b];  Y[i][j][o+a][b] from the pair products
+  box_copy(s_, Y_.p(), {(int64_t)n * v, 1}, Yov_.p(), {ovr, 1}, {(int64_t)o * o, ovr});
+  k::scatter_pairs(s_, Y_.p(), Yvv_.p(), o, v, n);
   if (profile_) {
     ASCC_CUDA(cudaEventRecord(ev1, s_));
     events_.push_back({ev0, ev1});
     ladder_launches_ += 1;
-    ladder_flops_ += 2.0 * o * o * (double)vv * n * v *
+    ladder_flops_ += 2.0 * (double)vv * ((double)o * o * o * v + (double)npair * vv) *
                      (es_.level() > 0 ? tc::products_for(es_.level()) : 1);
   }
   // R-dressed amplitudes tt[i][j][u][w], u, w over the virtuals (+ hole slot)

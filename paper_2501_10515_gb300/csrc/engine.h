@@ -167,6 +167,7 @@ class State {
   OT L_, R_, LamC_, RhoC_, rowsC_, colsC_, Bhat_, hhat_, F_, dP_, J_, K_, Boo_, Bov_, Bvo_, Bvv_, Bno_, Bon_;
   OT goooo_, gooov_, goovv_, govov_, gvovo_, gvoov_, gvvoo_, Lvoov_, Lovov_;
   OT u_, m_, um_, Z_, WC_, WD_, Wq_, Fvv_, Foo_, X_, Y_, Yfull_, Z1_, tt_, Yoo_, YC_, Z1C_;
+  OT tpair_, Yvv_, Yov_;  // pair-symmetric ladder operands
 };
 
 }  // namespace ascc

@@ -359,7 +359,7 @@ int splitk_for(int64_t M, int64_t N, int64_t K) {
 
 void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
                 const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C, int64_t ldc,
-                int* err, int splitk, float* ws) {
+                int* err, int splitk, float* ws, int64_t b_plane_stride) {
   ASCC_REQUIRE(level >= 1 && level <= 3, "split level 1..3");
   ASCC_REQUIRE(M > 0 && N > 0 && K > 0, "gemm_split: empty");
   ASCC_REQUIRE(splitk >= 1 && (splitk == 1 || ws), "gemm_split: split-K needs a workspace");
@@ -375,7 +375,7 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   for (int u = 0; u < 3; ++u) {
     const int uu = u < level ? u : 0;
     am[u] = make_map(A + (int64_t)uu * M * Kp, M, Kp, BM);
-    bm[u] = make_map(B + (int64_t)uu * N * Kp, N, Kp, BN);
+    bm[u] = make_map(B + (int64_t)uu * (b_plane_stride > 0 ? b_plane_stride : N * Kp), N, Kp, BN);
   }
   // products with the small planes first (accumulated before the large ones)
   Segs sg;

@@ -26,9 +26,12 @@ void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t ro
 // splitk > 1 splits K over the grid: each chunk's FP32 accumulator goes to
 // ws [splitk][M][N] (FP32) and the chunks are summed in FP64 afterwards, which
 // bounds the FP32 accumulation error by the chunk length.
+// b_plane_stride: elements between B's planes (<= 0: N * Kp, i.e. packed planes),
+// so that a row block of a larger plane set can serve as B.
 void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
                 const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C,
-                int64_t ldc, int* err, int splitk = 1, float* ws = nullptr);
+                int64_t ldc, int* err, int splitk = 1, float* ws = nullptr,
+                int64_t b_plane_stride = 0);
 
 // Number of K chunks the residual engine uses for an M x N x K product.
 int splitk_for(int64_t M, int64_t N, int64_t K);

@@ -64,6 +64,14 @@ void cols_minus_identity(cudaStream_t s, double* out, const double* M, int n, in
 void jacobi_pairs(cudaStream_t s, double* tn, double* e, const double* t, const double* r,
                   const double* eps_eff, const double* F, int o, int v, int hole, int particle);
 
+// Pair-symmetric ladder operands (t_ji^dc = t_ij^cd, (ac|bd) = (bd|ac) give
+// Y_ji^{ba} = Y_ij^{ab}): gather_pairs packs the rows t[i][j][:] (vv values)
+// of the pairs i <= j, row p = i o - i (i - 1) / 2 + (j - i); scatter_pairs
+// writes Y[i][j][o+a][b] (Y [o][o][n][v]) from the pair products
+// Yvv[p][a][b], transposing a and b for i > j.
+void gather_pairs(cudaStream_t s, double* tpair, const double* t, int o, int64_t vv);
+void scatter_pairs(cudaStream_t s, double* Y, const double* Yvv, int o, int v, int n);
+
 // d[P] = sum_k B[P][k][k]
 void diag_sum(cudaStream_t s, double* d, const double* B, int naux, int n, int o);
 

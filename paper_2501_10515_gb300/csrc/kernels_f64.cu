@@ -281,6 +281,42 @@ __global__ void mixed_mask_kernel(double* m, const double* t, int o, int v, int 
   }
 }
 
+__device__ __forceinline__ int64_t pair_row(int i, int j, int o) {
+  return (int64_t)i * o - (int64_t)i * (i - 1) / 2 + (j - i);
+}
+
+__global__ void gather_pairs_kernel(double* tpair, const double* t, int o, int64_t vv) {
+  const int64_t npair = (int64_t)o * (o + 1) / 2, total = npair * vv;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = idx / vv, c = idx % vv;
+    // invert p = i o - i (i - 1) / 2 + (j - i) by walking i (o is small)
+    int i = 0;
+    int64_t base = 0;
+    while (base + (o - i) <= p) {
+      base += o - i;
+      ++i;
+    }
+    const int j = i + (int)(p - base);
+    tpair[idx] = t[((int64_t)i * o + j) * vv + c];
+  }
+}
+
+__global__ void scatter_pairs_kernel(double* Y, const double* Yvv, int o, int v, int n) {
+  const int64_t vv = (int64_t)v * v, total = (int64_t)o * o * vv;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx;
+    const int b = (int)(r % v); r /= v;
+    const int a = (int)(r % v); r /= v;
+    const int j = (int)(r % o);
+    const int i = (int)(r / o);
+    const double y = (i <= j) ? Yvv[pair_row(i, j, o) * vv + (int64_t)a * v + b]
+                              : Yvv[pair_row(j, i, o) * vv + (int64_t)b * v + a];
+    Y[(((int64_t)i * o + j) * n + o + a) * v + b] = y;
+  }
+}
+
 // Denominators: bare eps for the primary amplitudes (every index h or p) of a
 // one-CSF state and for the ground state; eps_eff (h and p at their mean) for
 // all other amplitudes of a one-CSF state.
@@ -527,6 +563,22 @@ void tilde(cudaStream_t s, double* u, const double* t, int o, int v) {
   tilde_kernel<<<grid_for((int64_t)o * o * v * v), 256, 0, s>>>(u, t, o, v);
   count_launch();
   check_launch("tilde");
+}
+
+void gather_pairs(cudaStream_t s, double* tpair, const double* t, int o, int64_t vv) {
+  const int64_t total = (int64_t)o * (o + 1) / 2 * vv;
+  if (!total) return;
+  gather_pairs_kernel<<<grid_for(total), 256, 0, s>>>(tpair, t, o, vv);
+  count_launch();
+  check_launch("gather_pairs");
+}
+
+void scatter_pairs(cudaStream_t s, double* Y, const double* Yvv, int o, int v, int n) {
+  const int64_t total = (int64_t)o * o * v * v;
+  if (!total) return;
+  scatter_pairs_kernel<<<grid_for(total), 256, 0, s>>>(Y, Yvv, o, v, n);
+  count_launch();
+  check_launch("scatter_pairs");
 }
 
 void mixed_mask(cudaStream_t s, double* m, const double* t, int o, int v, int hole, int particle) {
