@@ -188,6 +188,14 @@ def run_reference(args, wl):
     return 0
 
 
+DTYPES = {"fp64": "f64", "mixed": "bf16x3-split/f64",
+          "fp64tc": "f64 via bf16 digit-plane tensor-core products"}
+
+
+def precision_code(pkg, name):
+    return {"fp64": pkg.ASCC_FP64, "mixed": pkg.ASCC_MIXED_BF16, "fp64tc": pkg.ASCC_FP64_TC}[name]
+
+
 def max_over_ranks(ms, dist=None, device="cpu"):
     """The timed region of a step is the slowest rank's (replicas share no data)."""
     if dist is None:
@@ -214,7 +222,7 @@ def run_server_workload(args, kind):
     import synth
     import paper_2501_10515_gb300 as pkg
     torch.cuda.set_device(0)
-    prec = pkg.ASCC_MIXED_BF16 if args.precision == "mixed" else pkg.ASCC_FP64
+    prec = precision_code(pkg, args.precision)
     if kind == "batch":
         reqs = []
         for w in synth.batch_workload(args.requests or 64):
@@ -254,7 +262,7 @@ def run_server_workload(args, kind):
         "metric": METRIC, "value": ok / wall, "unit": "solves/s", "n_gpus": 1,
         "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * wall / max(1, len(reqs)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x3-split/f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "dtype": DTYPES[args.precision], "data": "synthetic",
         "config": {"workload": ("batched launch of 64 independent molecules, o in [4,16], v in "
                                 "[40,160], 1-3 excitations each plus the ground state"
                                 if kind == "batch" else SERVE_NOTE),
@@ -268,30 +276,36 @@ def run_server_workload(args, kind):
 
 
 def run_gemm(args):
-    """The split-BF16 tensor-core GEMM alone on the ladder's shape class (M = o^2 = 400,
-    N = (o+v) v = 44000) with K = 4096, inputs larger than L2."""
+    """One tensor-core GEMM alone, by default on the ladder's shape class (M = o^2 = 400,
+    N = (o+v) v = 44000) with K = 4096, inputs larger than L2.  --level 1..3: split-BF16
+    products; --level 4: FP64-class digit-plane products."""
     import torch
     import paper_2501_10515_gb300 as pkg
-    M, N, K, lev = 400, 44000, 4096, args.level
+    M, N, K = (int(x) for x in args.gemm_shape.split(","))
+    lev = args.level
     g = torch.Generator(device="cuda").manual_seed(1)
     A = torch.randn(M, K, device="cuda", dtype=torch.float64, generator=g)
     B = torch.randn(N, K, device="cuda", dtype=torch.float64, generator=g)
     C = torch.zeros(M, N, device="cuda", dtype=torch.float64)
+    call = ((lambda: pkg.gemm_fp64_tc(A, B, C)) if lev == 4 else
+            (lambda: pkg.gemm_split_bf16(A, B, C, lev)))
     for _ in range(args.warmup):
-        pkg.gemm_split_bf16(A, B, C, lev)
+        call()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        pkg.gemm_split_bf16(A, B, C, lev)
+        call()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    products = {1: 1, 2: 3, 3: 6}[lev]
-    tf = 2.0 * M * N * K * products / (ms / 1e3) / 1e12
-    print(json.dumps({"kernel": "split-BF16 tcgen05 GEMM incl. operand split and K reduction",
-                      "M": M, "N": N, "K": K, "level": lev, "products": products,
-                      "ms": ms, "tflops": tf, "frac_of_bf16_burst": tf / 1977.2}), flush=True)
+    products = {1: 1, 2: 3, 3: 6, 4: 21}[lev]
+    tf = 2.0 * M * N * K / (ms / 1e3) / 1e12
+    print(json.dumps({"kernel": ("digit-plane tcgen05 GEMM" if lev == 4 else "split-BF16 tcgen05 GEMM")
+                      + " incl. operand split and K reduction",
+                      "M": M, "N": N, "K": K, "level": lev, "products": products, "ms": ms,
+                      "tflops_fp64_equivalent": tf, "mma_tflops": tf * products,
+                      "mma_frac_of_bf16_burst": tf * products / 1977.2}), flush=True)
     return 0
 
 
@@ -302,7 +316,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["batch", "serve", "gemm"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "fp64tc"])
     ap.add_argument("--step", default="solve", choices=["solve", "iteration"])
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-iterations", type=int, default=2)
@@ -312,6 +326,7 @@ def main():
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=180.0)
     ap.add_argument("--level", type=int, default=2)
+    ap.add_argument("--gemm-shape", default="400,44000,4096")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload in ("batch", "serve"):
@@ -335,8 +350,8 @@ def main():
     o, v = wl["o"], wl["v"]
     s = synth.make_system(o, v, seed=wl["seed"])
     stream = torch.cuda.current_stream()
-    mixed = args.precision == "mixed"
-    prec = pkg.ASCC_MIXED_BF16 if mixed else pkg.ASCC_FP64
+    mixed = args.precision != "fp64"  # tensor-core contractions
+    prec = precision_code(pkg, args.precision)
     ctx = pkg.Context(o, v, s.naux, s.eps, s.B, hole=wl["hole"], particle=wl["particle"],
                       linearize=1, stream=stream.cuda_stream, precision=prec)
 
@@ -378,7 +393,9 @@ def main():
     nlad = max(1, p1.ladder_launches - p0.ladder_launches)
     lad_ms = (p1.ladder_ms - p0.ladder_ms) / nlad
     lad_fl = (p1.ladder_flops - p0.ladder_flops) / nlad
+    lad_mma = (p1.ladder_mma_flops - p0.ladder_mma_flops) / nlad
     achieved = lad_fl / (lad_ms / 1e3) / 1e12
+    mma_rate = lad_mma / (lad_ms / 1e3) / 1e12
     if mixed:
         peak, bound, unit_note = 1977.2, "tensor", "BF16 dense burst, measured (MEASURED_PEAKS.json)"
     else:
@@ -427,7 +444,7 @@ def main():
         "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x3-split/f64" if mixed else "f64", "data": "synthetic",
+        "dtype": DTYPES[args.precision], "data": "synthetic",
         "config": {"workload": wl["name"], "o": o, "v": v, "naux": s.naux,
                    "excitation": [wl["hole"], wl["particle"]], "method": "PLASCC",
                    "precision": args.precision, "parallelism": f"replicas{world}",
@@ -442,9 +459,14 @@ def main():
         "gpu_launches": int(p1.launches - p0.launches),
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": ("gemm_tc_kernel" if mixed else "gemm_f64_kernel") +
-                               " (dense particle-particle ladder launch)",
-                     "peak_source": unit_note},
+                     "kernel": {"fp64": "gemm_f64_kernel", "mixed": "gemm_tc_kernel",
+                                "fp64tc": "gemm_oz_kernel"}[args.precision] +
+                               " (particle-particle ladder: its operand splits and GEMMs)",
+                     "peak_source": unit_note,
+                     "achieved_note": "algorithmic flops of the ladder (one product per "
+                                      "multiply-add) over its CUDA-event time",
+                     "mma_tflops": mma_rate,
+                     "mma_frac": mma_rate / peak},
         "residual_tflops": tflops,
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "iterations": iters, "iterations_low_precision": last.iterations_low,

@@ -56,7 +56,16 @@ typedef enum {
   ASCC_ERR_TIMEOUT = 6         /* a bounded device wait gave up                 */
 } ascc_status;
 
-enum { ASCC_FP64 = 0, ASCC_MIXED_BF16 = 1 };
+/* Precision of the residual contractions.
+ *   ASCC_FP64        every contraction in FP64 (DFMA).
+ *   ASCC_MIXED_BF16  large contractions on the BF16 tensor cores, 3 then 6
+ *                    split products, with defect correction from FP64-class
+ *                    evaluations (ASCC_FP64_TC contractions); the accepted
+ *                    amplitudes satisfy the FP64 equations to r_tol.
+ *   ASCC_FP64_TC     every large contraction as exact BF16 digit-plane
+ *                    products on the tensor cores (ascc_gemm_fp64_tc, error
+ *                    1e-12 to 5e-12 of |A||B|); iterations follow the FP64 path. */
+enum { ASCC_FP64 = 0, ASCC_MIXED_BF16 = 1, ASCC_FP64_TC = 2 };
 
 typedef struct {
   int32_t n_csf;     /* 0 = ground state (S = 0); 1 = one-CSF excited state     */
@@ -72,7 +81,7 @@ typedef struct {
 } ascc_excitation;
 
 typedef struct {
-  int32_t precision;   /* ASCC_FP64 or ASCC_MIXED_BF16                          */
+  int32_t precision;   /* ASCC_FP64, ASCC_MIXED_BF16 or ASCC_FP64_TC            */
   int32_t linearize;   /* 0 = ASCC, 1 = PLASCC (Sec. II.C)                      */
   int32_t triples;     /* 1 = include T3' for n_csf = 1 (Sec. II.B.1)           */
   int32_t pl_hole;     /* primary pair used to split a ground-state solve for   */
@@ -94,7 +103,8 @@ typedef struct {
   int32_t iterations; /* residual evaluations performed                        */
   int32_t status;     /* ascc_status of the solve                              */
   int32_t iterations_low;   /* of which in low precision (mixed precision)     */
-  int32_t fp64_evaluations; /* FP64 residuals of the polishing phase (mixed)   */
+  int32_t fp64_evaluations; /* FP64-class residuals of the polishing phase
+                               (mixed precision)                               */
 } ascc_result;
 
 /* Fills *opt with defaults: FP64, PLASCC, triples off, r_tol 1e-8, e_tol 1e-10,
@@ -171,13 +181,18 @@ ascc_status ascc_iterate(ascc_ctx* ctx, int32_t max_steps, ascc_result* res);
 /* Profiling of the dense particle-particle ladder contraction: when enabled,
  * each launch is bracketed by CUDA events on the context's stream.
  * ascc_get_profile reports the summed event time (ms), the number of
- * launches and their algorithmic flops (2 o^2 v^2 (o+v) v each). */
+ * launches and their flops: 2 v^2 (o^3 v + o(o+1)/2 v^2) each (the dense
+ * 2 o^2 v^2 (o+v) v with the pair symmetry of t2 used for the virtual rows),
+ * and the same times the plane products the tensor cores execute. */
 typedef struct {
   double ladder_ms;
   double ladder_flops;
   int64_t ladder_launches;
   int64_t launches;   /* kernel launches of this library since the context was made */
-  double gemm_flops;  /* flops (2 m n k) of all contractions since the context was made */
+  double gemm_flops;  /* flops (2 m n k) of all contractions since the context was made,
+                         one product each whatever the precision                   */
+  double ladder_mma_flops; /* ladder_flops times the BF16 plane products per step
+                              (equal to ladder_flops on the FP64 path)             */
 } ascc_profile;
 ascc_status ascc_set_profiling(ascc_ctx* ctx, int32_t enable);
 ascc_status ascc_get_profile(ascc_ctx* ctx, ascc_profile* out);
@@ -196,6 +211,25 @@ ascc_status ascc_get_profile(ascc_ctx* ctx, ascc_profile* out);
 ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level,
                                  double alpha, const double* A, const double* B,
                                  double beta, double* C, void* stream);
+
+/* FP64-class GEMM on the BF16 tensor cores (the contraction device behind
+ * ASCC_FP64_TC and the polishing evaluations of ASCC_MIXED_BF16):
+ *   C = alpha * A B^T + beta * C,
+ * A [M][K], B [N][K], C [M][N]: row-major FP64 device buffers.  Each row is
+ * scaled by a power of two and rounded to a 42-bit integer held as six
+ * 7-bit BF16 digit planes (error-free splitting of Ozaki, Ogita and Oishi);
+ * the 21 leading plane products run as tcgen05 BF16 MMAs whose grouped FP32
+ * sums are exact over chunks of 1024 K values and are folded into 64-bit
+ * integers.  Error: 1e-12 to 5e-12 of |A||B| elementwise for rows of even
+ * magnitude (each row is a 42-bit fixed-point number relative to its largest
+ * entry, and the plane products with s + t >= 6 are left out); a row or
+ * column holding a NaN or an infinity gives NaN.  Results do not depend on
+ * the K split.  stream: cudaStream_t or NULL; the call does not synchronise
+ * (it allocates its operand planes and workspace stream-ordered).  Returns
+ * ASCC_ERR_TIMEOUT if a bounded wait of an earlier call gave up. */
+ascc_status ascc_gemm_fp64_tc(int64_t M, int64_t N, int64_t K, double alpha,
+                              const double* A, const double* B, double beta,
+                              double* C, void* stream);
 
 /* The same product as ascc_gemm_split_bf16, for callers that cannot
  * allocate device memory when they need it: work recorded inside a CUDA

@@ -13,6 +13,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ascc.h")
 
 ASCC_FP64 = 0
 ASCC_MIXED_BF16 = 1
+ASCC_FP64_TC = 2
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "not converged", 5: "diverged", 6: "device wait timed out"}
@@ -40,7 +41,7 @@ class Result(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("ladder_ms", C.c_double), ("ladder_flops", C.c_double),
                 ("ladder_launches", C.c_int64), ("launches", C.c_int64),
-                ("gemm_flops", C.c_double)]
+                ("gemm_flops", C.c_double), ("ladder_mma_flops", C.c_double)]
 
 
 class ServeResult(C.Structure):
@@ -86,6 +87,8 @@ def load():
         "ascc_get_profile": (C.c_int, [vp, P(Profile)]),
         "ascc_gemm_split_bf16": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_double,
                                            vp, vp, C.c_double, vp, vp]),
+        "ascc_gemm_fp64_tc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, vp, vp,
+                                        C.c_double, vp, vp]),
         "ascc_gemm_split_bf16_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                                    C.c_double, vp, vp, C.c_double, vp, vp]),
         "ascc_server_create": (C.c_int, [P(vp), C.c_size_t, C.c_int32, P(Options)]),
@@ -129,6 +132,16 @@ def gemm_split_bf16(A, B, out, level, alpha=1.0, beta=0.0, stream=None):
     assert tuple(out.shape) == (M, N) and B.shape[1] == K
     _check(load().ascc_gemm_split_bf16(M, N, K, level, alpha, C_void(A), C_void(B), beta,
                                        C_void(out), C.c_void_p(stream) if stream else None))
+
+
+def gemm_fp64_tc(A, B, out, alpha=1.0, beta=0.0, stream=None):
+    """out = alpha A B^T + beta out on device FP64 tensors (exact digit-plane
+    products on the tensor cores, see ascc_gemm_fp64_tc)."""
+    M, K = A.shape
+    N = B.shape[0]
+    assert tuple(out.shape) == (M, N) and B.shape[1] == K
+    _check(load().ascc_gemm_fp64_tc(M, N, K, alpha, C_void(A), C_void(B), beta, C_void(out),
+                                    C.c_void_p(stream) if stream else None))
 
 
 def gemm_split_bf16_noalloc(A, B, out, level, alpha=1.0, beta=0.0, stream=None):

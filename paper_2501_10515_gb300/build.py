@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libascc.so")
 OBJ = os.path.join(HERE, "_build")
-SOURCES = ["kernels_f64.cu", "gemm_tc.cu", "engine.cu", "api.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["kernels_f64.cu", "gemm_tc.cu", "gemm_oz.cu", "engine.cu", "api.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

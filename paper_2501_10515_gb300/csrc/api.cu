@@ -5,6 +5,7 @@
 #include <memory>
 
 #include "engine.h"
+#include "gemm_oz.h"
 #include "gemm_tc.h"
 #include "kernels.h"
 
@@ -293,7 +294,8 @@ ascc_status ascc_set_profiling(ascc_ctx* ctx, int32_t enable) {
 ascc_status ascc_get_profile(ascc_ctx* ctx, ascc_profile* out) {
   return guard([&]() -> ascc_status {
     ASCC_REQUIRE(ctx && ctx->state && out, "null argument");
-    ctx->state->profile(&out->ladder_ms, &out->ladder_launches, &out->ladder_flops);
+    ctx->state->profile(&out->ladder_ms, &out->ladder_launches, &out->ladder_flops,
+                        &out->ladder_mma_flops);
     out->launches = launch_total() - ctx->launches0;
     out->gemm_flops = flop_total() - ctx->flops0;
     return ASCC_OK;
@@ -327,6 +329,36 @@ ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level,
     DevBuf ws(z > 1 ? sizeof(float) * (size_t)(z * M * N) : 0, s);
     tc::gemm_split(s, M, N, K, level, alpha, pa.as<__nv_bfloat16>(), pb.as<__nv_bfloat16>(), beta,
                    C, N, err, z, ws.as<float>());
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_gemm_fp64_tc(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                              const double* B, double beta, double* C, void* stream) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(A && B && C && M > 0 && N > 0 && K > 0, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    static int* err = nullptr;
+    if (!err) {
+      ASCC_CUDA(cudaMalloc(&err, sizeof(int)));
+      ASCC_CUDA(cudaMemset(err, 0, sizeof(int)));
+    }
+    int h = 0;
+    ASCC_CUDA(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+      cudaMemset(err, 0, sizeof(int));
+      throw Error(ASCC_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
+    }
+    const int64_t Kq = oz::padded_k(K);
+    DevBuf pa(sizeof(__nv_bfloat16) * (size_t)(oz::NSLICE * M * Kq), s);
+    DevBuf pb(sizeof(__nv_bfloat16) * (size_t)(oz::NSLICE * N * Kq), s);
+    DevBuf ea(sizeof(int32_t) * (size_t)M, s), eb(sizeof(int32_t) * (size_t)N, s);
+    DevBuf ws(oz::ws_bytes(M, N), s);
+    oz::split(s, pa.as<__nv_bfloat16>(), ea.as<int32_t>(), A, M, K, K);
+    oz::split(s, pb.as<__nv_bfloat16>(), eb.as<int32_t>(), B, N, K, K);
+    oz::gemm(s, M, N, K, alpha, pa.as<__nv_bfloat16>(), ea.as<int32_t>(), 0,
+             pb.as<__nv_bfloat16>(), eb.as<int32_t>(), 0, beta, C, N, ws.as<long long>(), err,
+             oz::splitk_for(M, N, K));
     return ASCC_OK;
   });
 }
@@ -369,18 +401,23 @@ size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux, const ascc_optio
   // build chunk; state: amplitudes, residual, DIIS history, per-iteration
   // workspace and the einsum temporaries (a few o^2 v^2 / o^2 n^2 tensors).
   const double n = o + v, O = o, V = v, P = naux;
-  const bool mixed = opt && opt->precision == ASCC_MIXED_BF16;
+  const int prec = opt ? opt->precision : ASCC_FP64;
+  const bool mixed = prec == ASCC_MIXED_BF16, digits = prec != ASCC_FP64;
   const int m = opt ? opt->diis_dim : 16;
-  const double kp = std::ceil(V * V / 64.0) * 64.0;
+  const double kp = std::ceil(V * V / 64.0) * 64.0, kq = std::ceil(V * V / 32.0) * 32.0;
   double mol = 8.0 * (P * n * n + n * n + P * V * V + P * n * V);
-  // FP64 ladder block (+ its build temporary); mixed precision adds the BF16
-  // planes, the FP64 block serving the FP64-corrected polishing residuals
-  mol += 8.0 * n * V * V * V * 2.0;
+  // ladder blocks: FP64 (+ its build temporary), or the BF16 split planes
+  // (mixed) and the six digit planes (mixed, FP64_TC) with ~2 GB of build chunks
+  if (!digits) mol += 8.0 * n * V * V * V * 2.0;
   if (mixed) mol += 2.0 * 3.0 * n * V * kp;
+  if (digits) mol += 2.0 * 6.0 * n * V * kq + 4.0 * n * V + 2.2e9;
   const double o2v2 = O * O * V * V, namp = O * V + o2v2;
   double state = 8.0 * (namp * (2.0 * m + 4.0) + P * n * n * 1.2 + 24.0 * o2v2 +
                         O * O * n * n * 3.0 + O * O * n * V * 4.0);
   if (mixed) state += 2.0 * 3.0 * (O * O + n * V) * kp;  // operand planes of the ladder
+  // digit planes of the ladder's t operand, the integer workspace, and the
+  // planes of the largest generic contraction (o v x o v x o v)
+  if (digits) state += 2.0 * 6.0 * O * O * kq + 8.0 * o2v2 + 2.0 * 6.0 * 2.0 * o2v2 + 8.0 * o2v2;
   return (size_t)((mol + state) * 1.1);
 }
 

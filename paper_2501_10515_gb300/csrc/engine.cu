@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "engine.h"
+#include "gemm_oz.h"
 #include "gemm_tc.h"
 #include "kernels.h"
 
@@ -168,6 +169,28 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
       perm((sp.b + "->" + Nl + Kl).c_str(), 1.0, B, 0.0, Bn_t.t);
       Bn = Bn_t.p();
     }
+    if (level_ == 4) {
+      // exact digit-plane products (FP64-class)
+      const int64_t Kq = oz::padded_k(Ks);
+      auto* pa = static_cast<__nv_bfloat16*>(
+          scratch(0, sizeof(__nv_bfloat16) * (size_t)(oz::NSLICE * Ms * Kq)));
+      auto* pb = static_cast<__nv_bfloat16*>(
+          scratch(1, sizeof(__nv_bfloat16) * (size_t)(oz::NSLICE * Ns * Kq)));
+      auto* ea = static_cast<int32_t*>(scratch(3, sizeof(int32_t) * (size_t)Ms));
+      auto* eb = static_cast<int32_t*>(scratch(4, sizeof(int32_t) * (size_t)Ns));
+      oz::split(s_, pa, ea, Am, Ms, Ks, Ks);
+      oz::split(s_, pb, eb, Bn, Ns, Ks, Ks);
+      auto* ws = static_cast<long long*>(scratch(2, oz::ws_bytes(Ms, Ns)));
+      const int z = oz::splitk_for(Ms, Ns, Ks);
+      if (sp.c == cl) {
+        oz::gemm(s_, Ms, Ns, Ks, alpha, pa, ea, 0, pb, eb, 0, beta, C.p, Ns, ws, err_, z);
+      } else {
+        OT Ct(shape_of(cl), s_);
+        oz::gemm(s_, Ms, Ns, Ks, 1.0, pa, ea, 0, pb, eb, 0, 0.0, Ct.p(), Ns, ws, err_, z);
+        perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
+      }
+      return;
+    }
     const int64_t Kp = tc::padded_k(Ks);
     auto* pa = static_cast<__nv_bfloat16*>(scratch(0, sizeof(__nv_bfloat16) * (size_t)(level_ * Ms * Kp)));
     auto* pb = static_cast<__nv_bfloat16*>(scratch(1, sizeof(__nv_bfloat16) * (size_t)(level_ * Ns * Kp)));
@@ -286,9 +309,46 @@ void Molecule::ensure_bf16_ladder() {
   if (h) throw Error(ASCC_ERR_TIMEOUT, "tensor-core GEMM wait timed out while building (xc|bd)");
 }
 
+// Digit planes of Gext for FP64-class tensor-core ladders, built x-chunk by
+// x-chunk with FP64-class contractions (or split from the FP64 block when it
+// exists).
+void Molecule::ensure_oz_ladder() {
+  std::lock_guard<std::mutex> lock(mu_);
+  if (Gext_oz.bytes()) return;
+  const int64_t rows = (int64_t)n * v, K = (int64_t)v * v, Kq = oz::padded_k(K);
+  Gext_oz.alloc(sizeof(__nv_bfloat16) * (size_t)(oz::NSLICE * rows * Kq), stream);
+  Gext_oz_exp.alloc(sizeof(int32_t) * (size_t)rows, stream);
+  auto* planes = Gext_oz.as<__nv_bfloat16>();
+  auto* exps = Gext_oz_exp.as<int32_t>();
+  if (Gext.buf.bytes()) {
+    oz::split(stream, planes, exps, Gext.p(), rows, K, K, rows * Kq);
+    ASCC_CUDA(cudaStreamSynchronize(stream));
+    return;
+  }
+  Einsum es(stream);
+  es.set_split(4, err.as<int>(), 0.0);
+  const int64_t v3 = (int64_t)v * v * v;
+  int64_t xc = std::max<int64_t>(1, ((int64_t)1 << 27) / v3);  // ~1 GB FP64 per chunk
+  xc = std::min<int64_t>(xc, n);
+  OT Ac({naux, xc, v}, stream), Gc({xc, v, v, v}, stream);
+  for (int64_t x0 = 0; x0 < n; x0 += xc) {
+    const int64_t nx = std::min<int64_t>(xc, n - x0);
+    T a(Ac.p(), {naux, nx, v}), gch(Gc.p(), {nx, v, v, v});
+    box_copy(stream, Ac.p(), {nx * v, v, 1}, Bnv.p() + x0 * v, {(int64_t)n * v, v, 1},
+             {naux, nx, v});
+    es("Pxc,Pbd->xbcd", 1.0, a, Bvv.t, 0.0, gch);
+    oz::split(stream, planes + x0 * v * Kq, exps + x0 * v, Gc.p(), nx * v, K, K, rows * Kq);
+  }
+  int h = 0;
+  ASCC_CUDA(cudaMemcpyAsync(&h, err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, stream));
+  ASCC_CUDA(cudaStreamSynchronize(stream));
+  if (h) throw Error(ASCC_ERR_TIMEOUT, "tensor-core GEMM wait timed out while building (xc|bd)");
+}
+
 size_t Molecule::bytes() const {
   return eps.buf.bytes() + B.buf.bytes() + hcore.buf.bytes() + Bvv.buf.bytes() +
-         Bnv.buf.bytes() + Gext.buf.bytes() + Gext_bf16.bytes();
+         Bnv.buf.bytes() + Gext.buf.bytes() + Gext_bf16.bytes() + Gext_oz.bytes() +
+         Gext_oz_exp.bytes();
 }
 
 // ---------------------------------------------------------------- State
@@ -330,8 +390,9 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   lh_ = hole_ >= 0 ? hole_ : opt_.pl_hole;
   lp_ = hole_ >= 0 ? particle_ : opt_.pl_particle;
   if (lh_ < 0) opt_.linearize = 0;
-  ASCC_REQUIRE(opt_.precision == ASCC_FP64 || opt_.precision == ASCC_MIXED_BF16,
-               "precision must be ASCC_FP64 or ASCC_MIXED_BF16");
+  ASCC_REQUIRE(opt_.precision == ASCC_FP64 || opt_.precision == ASCC_MIXED_BF16 ||
+                   opt_.precision == ASCC_FP64_TC,
+               "precision must be ASCC_FP64, ASCC_MIXED_BF16 or ASCC_FP64_TC");
   ASCC_REQUIRE(opt_.diis_dim >= 1 && opt_.diis_dim <= 32, "diis_dim in 1..32");
   if (opt_.triples && hole_ >= 0) {
     t3idx_host_ = t3p_index(o_, v_, hole_, particle_);
@@ -395,10 +456,14 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
     ASCC_CUDA(cudaStreamSynchronize(s));
   }
   ASCC_CUDA(cudaStreamSynchronize(mol_->stream));
-  if (opt_.precision == ASCC_MIXED_BF16)
+  if (opt_.precision == ASCC_MIXED_BF16) {
     mol_->ensure_bf16_ladder();
-  else
+    mol_->ensure_oz_ladder();  // FP64-class polishing evaluations
+  } else if (opt_.precision == ASCC_FP64_TC) {
+    mol_->ensure_oz_ladder();
+  } else {
     mol_->ensure_fp64_ladder();
+  }
   build_state_integrals();
 }
 
@@ -408,6 +473,7 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
 // hand-over and whenever the corrected iteration converges, so that the
 // accepted amplitudes satisfy the FP64 equations.
 int State::level_for_phase() const {
+  if (opt_.precision == ASCC_FP64_TC) return 4;
   if (opt_.precision != ASCC_MIXED_BF16) return 0;
   return polish_ ? 3 : 2;
 }
@@ -541,7 +607,24 @@ void State::ladder(const T& t2, const T& r2) {
   // occupied rows x = k need every pair.
   const int64_t npair = (int64_t)o * (o + 1) / 2, ovr = (int64_t)o * v, vvr = vv;
   k::gather_pairs(s_, tpair_.p(), t2.p, o, vv);
-  if (es_.level() > 0) {
+  if (es_.level() == 4) {
+    const int64_t K = vv, Kq = oz::padded_k(K), rows = (int64_t)n * v;
+    const __nv_bfloat16* G = M.Gext_oz.as<__nv_bfloat16>();
+    const int32_t* eG = M.Gext_oz_exp.as<int32_t>();
+    auto* pa = static_cast<__nv_bfloat16*>(
+        es_.scratch(0, sizeof(__nv_bfloat16) * (size_t)(oz::NSLICE * (int64_t)o * o * Kq)));
+    auto* ea = static_cast<int32_t*>(es_.scratch(3, sizeof(int32_t) * (size_t)o * o));
+    // occupied rows: all pairs
+    oz::split(s_, pa, ea, t2.p, (int64_t)o * o, K, K);
+    auto* ws = static_cast<long long*>(es_.scratch(2, oz::ws_bytes((int64_t)o * o, ovr)));
+    oz::gemm(s_, (int64_t)o * o, ovr, K, 1.0, pa, ea, 0, G, eG, rows * Kq, 0.0, Yov_.p(), ovr, ws,
+             err_.as<int>(), oz::splitk_for((int64_t)o * o, ovr, K));
+    // virtual rows: pairs i <= j
+    oz::split(s_, pa, ea, tpair_.p(), npair, K, K);
+    ws = static_cast<long long*>(es_.scratch(2, oz::ws_bytes(npair, vvr)));
+    oz::gemm(s_, npair, vvr, K, 1.0, pa, ea, 0, G + ovr * Kq, eG + ovr, rows * Kq, 0.0, Yvv_.p(),
+             vvr, ws, err_.as<int>(), oz::splitk_for(npair, vvr, K));
+  } else if (es_.level() > 0) {
     const int lev = es_.level();
     const int64_t K = vv, Kp = tc::padded_k(K), rows = (int64_t)n * v;
     // planes of Gext are stored [3][rows][Kp]; the kernel reads planes 0..lev-1
@@ -577,8 +660,11 @@ void State::ladder(const T& t2, const T& r2) {
     ASCC_CUDA(cudaEventRecord(ev1, s_));
     events_.push_back({ev0, ev1});
     ladder_launches_ += 1;
-    ladder_flops_ += 2.0 * (double)vv * ((double)o * o * o * v + (double)npair * vv) *
-                     (es_.level() > 0 ? tc::products_for(es_.level()) : 1);
+    const double fl = 2.0 * (double)vv * ((double)o * o * o * v + (double)npair * vv);
+    ladder_flops_ += fl;
+    ladder_mma_flops_ += fl * (es_.level() == 4   ? oz::products()
+                               : es_.level() > 0 ? tc::products_for(es_.level())
+                                                 : 1);
   }
   // R-dressed amplitudes tt[i][j][u][w], u, w over the virtuals (+ hole slot)
   const int64_t s4[4] = {(int64_t)o * vv, vv, v, 1};
@@ -803,8 +889,8 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
       // FP64 polishing: the FP64 residual and the 6-product residual at the
       // same amplitudes; their difference corrects the following iterations
       // (defect correction), and this step itself uses the FP64 residual.
-      mol_->ensure_fp64_ladder();  // the FP64 residual reads the FP64 (xc|bd) block
-      es_.set_split(0, err_.as<int>(), tc_min_flops_);
+      // FP64-class residual: exact digit-plane products on the tensor cores
+      es_.set_split(4, err_.as<int>(), tc_min_flops_);
       residual(t_.p(), r_.p(), scal_.p());
       es_.set_split(3, err_.as<int>(), tc_min_flops_);
       residual(t_.p(), corr_.p(), scal_.p() + 2);
@@ -926,7 +1012,8 @@ ascc_status State::solve(ascc_result* res) {
   return iterate(opt_.max_iter + 1, res);
 }
 
-void State::profile(double* ladder_ms, int64_t* ladder_launches, double* ladder_flops) {
+void State::profile(double* ladder_ms, int64_t* ladder_launches, double* ladder_flops,
+                    double* ladder_mma_flops) {
   for (auto& ev : events_) {
     ASCC_CUDA(cudaEventSynchronize(ev.second));
     float ms = 0.f;
@@ -939,6 +1026,7 @@ void State::profile(double* ladder_ms, int64_t* ladder_launches, double* ladder_
   if (ladder_ms) *ladder_ms = ladder_ms_;
   if (ladder_launches) *ladder_launches = ladder_launches_;
   if (ladder_flops) *ladder_flops = ladder_flops_;
+  if (ladder_mma_flops) *ladder_mma_flops = ladder_mma_flops_;
 }
 
 }  // namespace ascc

@@ -24,7 +24,8 @@ class Einsum {
   void perm(const char* spec, double alpha, const T& A, double beta, const T& C) const;
   // level 0: FP64 DFMA GEMM.  level 1..3: unbatched contractions of at least
   // min_flops run on the BF16 tensor cores with operands split into `level`
-  // BF16 planes (1, 3 or 6 products); err receives kernel timeout codes.
+  // BF16 planes (1, 3 or 6 products); level 4: the same contractions as exact
+  // digit-plane products (FP64-class); err receives kernel timeout codes.
   void set_split(int level, int* err, double min_flops = 4e7) {
     level_ = level;
     err_ = err;
@@ -40,7 +41,7 @@ class Einsum {
   int level_ = 0;
   int* err_ = nullptr;
   double min_flops_ = 4e7;
-  mutable DevBuf scratch_[3];
+  mutable DevBuf scratch_[5];
 };
 
 // Copies a strided box of `in` into `out` (both with explicit strides).
@@ -60,9 +61,12 @@ struct Molecule {
   OT Bnv;    // [naux][n][v]
   OT Gext;   // [n][v][v][v], Gext[x][b][c][d] = (xc|bd)
   DevBuf Gext_bf16;  // [3][n v][v^2 padded] BF16 planes of Gext (mixed precision)
+  DevBuf Gext_oz;    // [6][n v][v^2 padded to 32] BF16 digit planes of Gext
+  DevBuf Gext_oz_exp;  // int32 [n v] row exponents of Gext_oz
   // The ladder block is built on first use by a state of that precision.
   void ensure_fp64_ladder();
   void ensure_bf16_ladder();
+  void ensure_oz_ladder();
   int build_level_ = 0;
   std::mutex mu_;
   // build_level 0 builds the bare integrals in FP64; 1..3 on the BF16 tensor
@@ -104,7 +108,8 @@ class State {
   // Precision of a stand-alone residual call: FP64, or the polishing split
   // level in mixed precision.
   void prepare_eval() {
-    es_.set_split(opt_.precision == ASCC_MIXED_BF16 ? 3 : 0, err_.as<int>(), tc_min_flops_);
+    es_.set_split(opt_.precision == ASCC_MIXED_BF16 ? 3 : opt_.precision == ASCC_FP64_TC ? 4 : 0,
+                  err_.as<int>(), tc_min_flops_);
   }
   ascc_status solve(ascc_result* res);
   // Iteration control: reset() loads the zeroth-order guess and clears the
@@ -114,7 +119,8 @@ class State {
   ascc_status iterate(int max_steps, ascc_result* res);
   // Profiling of the dense ladder GEMM (CUDA events on the state's stream).
   void set_profiling(bool on) { profile_ = on; }
-  void profile(double* ladder_ms, int64_t* ladder_launches, double* ladder_flops);
+  void profile(double* ladder_ms, int64_t* ladder_launches, double* ladder_flops,
+               double* ladder_mma_flops = nullptr);
   void initial_guess(std::vector<double>& t) const;
 
   double* amplitudes() { return t_.p(); }
@@ -141,7 +147,7 @@ class State {
   // profiling
   bool profile_ = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events_;
-  double ladder_ms_ = 0.0, ladder_flops_ = 0.0;
+  double ladder_ms_ = 0.0, ladder_flops_ = 0.0, ladder_mma_flops_ = 0.0;
   int64_t ladder_launches_ = 0;
   cudaStream_t s_;
   int o_, v_, n_, naux_;

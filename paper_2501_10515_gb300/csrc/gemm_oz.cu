@@ -1,0 +1,393 @@
+// FP64-class tensor-core GEMM from exact BF16 digit-plane products
+// (tcgen05 + TMA + TMEM, sm_103a).  The number format is described in
+// gemm_oz.h.
+//
+// One CTA computes a 128 x 96 tile of C over its K range with 8 warps:
+// warp 0 issues TMA loads of all 6 digit planes of A and B for a 32-wide K
+// tile (84 KB per stage, 2 stages, 64-byte swizzle), warp 1 issues the 21
+// plane products per K tile (tcgen05.mma M=128 N=96 K=16) into five TMEM
+// accumulators of 96 columns, and warps 4..7 fold the accumulators into the
+// 64-bit integer tile in global memory after every 1024 K values.  Every wait
+// is bounded by a 2-second %globaltimer budget; on expiry the kernel records
+// an error code, waits (bounded) for its own copies and MMAs in flight, frees
+// its TMEM and returns.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <mutex>
+
+#include "gemm_oz.h"
+#include "tc_ptx.cuh"
+
+namespace ascc {
+namespace oz {
+namespace {
+
+using namespace tc::ptx;
+
+constexpr int BM = 128, BN = 96, BK = 32, STAGES = 2, NTHREADS = 256;
+constexpr int KCT = 32;                          // K tiles per exact chunk (1024 K values)
+constexpr int A_TILE = BM * BK * 2;              // one plane of A, 8 KB
+constexpr int B_TILE = BN * BK * 2;              // one plane of B, 6 KB
+constexpr int A_BYTES = NSLICE * A_TILE;         // 48 KB
+constexpr int STAGE_BYTES = A_BYTES + NSLICE * B_TILE;  // 84 KB
+// accumulators: exact groups s + t = 0, 1, 2, 3 and the tail 4..5 (weights
+// 2^-28 and 2^-35), whose FP32 sums the tensor core truncates
+constexpr int NACC = 5;
+constexpr int TMEM_COLS = 512;                   // NACC * BN = 480 rounded to a power of two
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int L = NSLICE * BETA;                 // 42 bits per scaled value
+constexpr int UNIT = 4 * BETA;                   // fold unit 2^-28
+static_assert(NACC * BN <= TMEM_COLS, "TMEM holds 512 columns");
+static_assert(A_TILE % 512 == 0 && B_TILE % 512 == 0, "64-byte swizzle atoms are 512 bytes");
+// |digit| <= 64, so a group of g + 1 <= 4 products sums to at most 1024 * 4 * 4096 = 2^24 per
+// chunk: every partial sum is an integer multiple of 2^(-7 g) that FP32 holds exactly
+static_assert((long long)KCT * BK * 4 * 64 * 64 <= (1ll << 24), "group chunk sums must stay exact");
+
+// One element of the chunk fold: groups 0..3 are exact integers (times
+// 2^(-7 g)); the tail is rounded once to the 2^-28 unit.
+__device__ __forceinline__ long long fold_value(uint32_t a0, uint32_t a1, uint32_t a2,
+                                                uint32_t a3, uint32_t a4) {
+  const long long i0 = __float2int_rn(__uint_as_float(a0));
+  const long long i1 = __float2int_rn(__uint_as_float(a1) * 128.f);
+  const long long i2 = __float2int_rn(__uint_as_float(a2) * 16384.f);
+  const long long i3 = __float2int_rn(__uint_as_float(a3) * 2097152.f);
+  const long long it = __float2ll_rn(__uint_as_float(a4) * 268435456.f);
+  return i0 * (1ll << 28) + i1 * (1ll << 21) + i2 * (1ll << 14) + i3 * (1ll << 7) + it;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+               int M, int N, int num_kt, int kt_chunk, unsigned long long* __restrict__ ws,
+               int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 3);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                 acc_full = smem_u32(bars + 2 * STAGES), acc_empty = smem_u32(bars + 2 * STAGES + 1),
+                 drained = smem_u32(bars + 2 * STAGES + 2);
+  __shared__ int abort_flag;
+  __shared__ int mma_consumed;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mma_consumed = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 128);
+    mbar_init(drained, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+  const int kt0 = blockIdx.z * kt_chunk;
+  const int nkt = max(0, min(kt_chunk, num_kt - kt0));
+  const int nchunks = (nkt + KCT - 1) / KCT;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer: all planes of A and B for one K tile per stage
+    int issued = 0;
+    for (int it = 0; it < nkt; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err, 11)) {
+        abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      const int kx = (kt0 + it) * BK;
+      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+      tma_load_3d(sa, &amap, full0 + 8 * s, kx, m0, 0);
+      tma_load_3d(sa + A_BYTES, &bmap, full0 + 8 * s, kx, n0, 0);
+      issued = it + 1;
+    }
+    if (*(volatile int*)&abort_flag) {
+      // let the copies still in flight land before the CTA exits
+      const int first = max(*(volatile int*)&mma_consumed, issued - STAGES);
+      for (int j = first; j < issued; ++j)
+        mbar_wait(full0 + 8 * (j % STAGES), (uint32_t)((j / STAGES) & 1), err, 11);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: 21 plane products per K tile, accumulator by s + t
+    constexpr uint32_t idesc = tc::ptx::idesc_bf16(BM, BN);
+    for (int it = 0; it < nkt; ++it) {
+      const int kc = it % KCT, chunk = it / KCT;
+      if (kc == 0 && chunk > 0) {
+        // the fold of the previous chunk must have drained the accumulators
+        if (!mbar_wait(acc_empty, (uint32_t)((chunk - 1) & 1), err, 12)) {
+          abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      if (!mbar_wait(full0 + 8 * s, ph, err, 13)) {
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+      uint32_t seen = 0;
+#pragma unroll
+      for (int u = 0; u < NSLICE; ++u) {
+#pragma unroll
+        for (int w = 0; u + w < NSLICE; ++w) {
+          const int acc = min(u + w, NACC - 1);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ad = sw64_desc(sa + u * A_TILE + kk * 32);
+            const uint64_t bd = sw64_desc(sb + w * B_TILE + kk * 32);
+            const uint32_t en = (kc == 0 && kk == 0 && !((seen >> acc) & 1u)) ? 0u : 1u;
+            mma_bf16(tmem + (uint32_t)(acc * BN), ad, bd, idesc, en);
+          }
+          seen |= 1u << acc;
+        }
+      }
+      mma_commit(empty0 + 8 * s);
+      *(volatile int*)&mma_consumed = it + 1;
+      if (kc == KCT - 1 || it == nkt - 1) mma_commit(acc_full);
+    }
+    // every MMA of this CTA has completed before TMEM is released
+    mma_commit(drained);
+    mbar_wait(drained, 0, err, 15);
+  } else if (warp >= 4) {
+    // fold: TMEM lanes [32 q, 32 q + 32) hold rows m0 + 32 q + lane
+    const int q = warp - 4;
+    const int row = m0 + q * 32 + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+    for (int chunk = 0; chunk < nchunks; ++chunk) {
+      const bool ok = mbar_wait(acc_full, (uint32_t)(chunk & 1), err, 14);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!__all_sync(0xffffffffu, ok) || *(volatile int*)&abort_flag) {
+        abort_flag = 1;
+        break;
+      }
+      unsigned long long* wrow = ws + (long long)row * N;
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r0[16], r1[16], r2[16], r3[16], r4[16];
+        tmem_ld16_nowait(taddr + 0 * BN + c0, r0);
+        tmem_ld16_nowait(taddr + 1 * BN + c0, r1);
+        tmem_ld16_nowait(taddr + 2 * BN + c0, r2);
+        tmem_ld16_nowait(taddr + 3 * BN + c0, r3);
+        tmem_ld16_nowait(taddr + 4 * BN + c0, r4);
+        tmem_wait_ld();
+        if (row < M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < N)
+              atomicAdd(wrow + col,
+                        (unsigned long long)fold_value(r0[j], r1[j], r2[j], r3[j], r4[j]));
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acc_empty);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// C = alpha * 2^(e_i + f_j - 42) * ws + beta * C; NaN where a row or column
+// held a non-finite value.
+__global__ void oz_finish_kernel(double* __restrict__ C, long long ldc,
+                                 const long long* __restrict__ ws, const int32_t* __restrict__ ea,
+                                 const int32_t* __restrict__ eb, long long M, long long N,
+                                 double alpha, double beta) {
+  const long long total = M * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long m = idx / N, n = idx % N;
+    const int32_t a = ea[m], b = eb[n];
+    double val;
+    if (a == kNonFinite || b == kNonFinite)
+      val = __longlong_as_double(0x7ff8000000000000ll);
+    else
+      val = ldexp((double)ws[idx], a + b - (2 * BETA + UNIT));
+    double* c = C + m * ldc + n;
+    *c = (beta == 0.0) ? alpha * val : fma(alpha, val, beta * *c);
+  }
+}
+
+// One block per row: row exponent from max |x|, then the balanced digits.
+__global__ void oz_split_kernel(__nv_bfloat16* __restrict__ out, int32_t* __restrict__ exps,
+                                const double* __restrict__ in, long long rows, long long K,
+                                long long ld, long long Kp, long long plane_stride) {
+  __shared__ double red_max[32];
+  __shared__ int red_bad[32];
+  __shared__ int row_e;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double* x = in + r * ld;
+    double mx = 0.0;
+    int bad = 0;
+    for (long long k = threadIdx.x; k < K; k += blockDim.x) {
+      const double a = fabs(x[k]);
+      if (!(a <= 1.7976931348623157e308)) bad = 1;  // NaN or infinity
+      else mx = fmax(mx, a);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red_max[threadIdx.x >> 5] = mx;
+      red_bad[threadIdx.x >> 5] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      int b = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        m = fmax(m, red_max[w]);
+        b |= red_bad[w];
+      }
+      int e = 0;
+      if (b) {
+        e = kNonFinite;
+      } else if (m > 0.0) {
+        int E;
+        frexp(m, &E);  // m = f 2^E, f in [1/2, 1)
+        e = E + 1;     // max |x| < 2^(e - 1)
+      }
+      row_e = e;
+      exps[r] = e;
+    }
+    __syncthreads();
+    const int e = row_e;
+    for (long long k = threadIdx.x; k < Kp; k += blockDim.x) {
+      long long q = 0;
+      if (e != kNonFinite && k < K) q = llrint(ldexp(x[k], L - e));  // |q| <= 2^41
+      // balanced base-2^7 digits from the least significant end
+      __nv_bfloat16 dig[NSLICE];
+#pragma unroll
+      for (int s = NSLICE - 1; s >= 1; --s) {
+        const long long d = ((q + 64) & 127) - 64;
+        q = (q - d) >> BETA;
+        dig[s] = __float2bfloat16_rn(ldexpf((float)d, -BETA * s));
+      }
+      dig[0] = __float2bfloat16_rn((float)q);
+#pragma unroll
+      for (int s = 0; s < NSLICE; ++s) out[(long long)s * plane_stride + r * Kp + k] = dig[s];
+    }
+    __syncthreads();
+  }
+}
+
+CUtensorMap make_map3(const __nv_bfloat16* base, int64_t rows, int64_t Kp, int64_t plane_stride,
+                      int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)NSLICE};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(plane_stride * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)NSLICE};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = tc::encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides,
+                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(ASCC_ERR_CUDA, "cuTensorMapEncodeTiled (digit planes) failed");
+  return m;
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)std::max<int64_t>(g, 1);
+}
+
+}  // namespace
+
+int64_t padded_k(int64_t K) { return (K + BK - 1) / BK * BK; }
+
+void split(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const double* in, int64_t rows,
+           int64_t K, int64_t ld, int64_t plane_stride) {
+  if (rows <= 0) return;
+  const int64_t Kp = padded_k(K);
+  if (plane_stride <= 0) plane_stride = rows * Kp;
+  const int g = (int)std::min<int64_t>(rows, 152 * 8);
+  oz_split_kernel<<<g, 256, 0, s>>>(planes, exps, in, rows, K, ld, Kp, plane_stride);
+  count_launch();
+  check_launch("oz_split");
+}
+
+int splitk_for(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int64_t num_kt = (K + BK - 1) / BK;
+  // each slice keeps at least two exact chunks; among those, the split whose
+  // CTA count fills the last wave best (one CTA per SM), the smaller on ties
+  const int64_t zmax = std::max<int64_t>(1, std::min<int64_t>(64, num_kt / (2 * KCT)));
+  int best = 1;
+  double best_eff = 0.0;
+  for (int64_t z = 1; z <= zmax; ++z) {
+    const int64_t ctas = tiles * z;
+    const int64_t waves = (ctas + 151) / 152;
+    const double eff = (double)ctas / (double)(waves * 152);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = (int)z;
+    }
+  }
+  return best;
+}
+
+void gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const __nv_bfloat16* A,
+          const int32_t* ea, int64_t a_plane_stride, const __nv_bfloat16* B, const int32_t* eb,
+          int64_t b_plane_stride, double beta, double* C, int64_t ldc, long long* ws, int* err,
+          int splitk) {
+  ASCC_REQUIRE(M > 0 && N > 0 && K > 0, "oz::gemm: empty");
+  ASCC_REQUIRE(splitk >= 1 && ws, "oz::gemm: needs a workspace");
+  static std::once_flag attr_once;
+  cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    attr_err = cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES);
+  });
+  ASCC_CUDA(attr_err);
+  const int64_t Kp = padded_k(K);
+  if (a_plane_stride <= 0) a_plane_stride = M * Kp;
+  if (b_plane_stride <= 0) b_plane_stride = N * Kp;
+  const CUtensorMap am = make_map3(A, M, Kp, a_plane_stride, BM);
+  const CUtensorMap bm = make_map3(B, N, Kp, b_plane_stride, BN);
+  count_flops(2.0 * (double)M * N * K);
+  const int num_kt = (int)(Kp / BK);
+  // slices of whole exact chunks
+  int kt_chunk = (num_kt + splitk - 1) / splitk;
+  kt_chunk = (kt_chunk + KCT - 1) / KCT * KCT;
+  const int z = (num_kt + kt_chunk - 1) / kt_chunk;
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)z);
+  ASCC_REQUIRE(grid.y <= 65535, "oz::gemm: N too large");
+  ASCC_CUDA(cudaMemsetAsync(ws, 0, ws_bytes(M, N), s));
+  gemm_oz_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(am, bm, (int)M, (int)N, num_kt, kt_chunk,
+                                                    reinterpret_cast<unsigned long long*>(ws), err);
+  count_launch();
+  check_launch("gemm_oz");
+  oz_finish_kernel<<<grid_for(M * N), 256, 0, s>>>(C, (long long)ldc, ws, ea, eb, M, N, alpha,
+                                                   beta);
+  count_launch();
+  check_launch("oz_finish");
+}
+
+}  // namespace oz
+}  // namespace ascc
