@@ -2,12 +2,15 @@
 // (tcgen05 + TMA + TMEM, sm_103a).  The number format is described in
 // gemm_oz.h.
 //
-// One CTA computes a 128 x 96 tile of C over its K range with 8 warps:
+// One CTA computes a 128 x 96 tile of C over its K range with 12 warps:
 // warp 0 issues TMA loads of all 6 digit planes of A and B for a 32-wide K
 // tile (84 KB per stage, 2 stages, 64-byte swizzle), warp 1 issues the 21
 // plane products per K tile (tcgen05.mma M=128 N=96 K=16) into five TMEM
-// accumulators of 96 columns, and warps 4..7 fold the accumulators into the
-// 64-bit integer tile in global memory after every 1024 K values.  Every wait
+// accumulators of 96 columns, and warps 4..11 fold the accumulators into
+// 64-bit integer sums held in registers (one row and 48 columns per thread)
+// after every 1024 K values.  At the end the CTA writes C itself (alpha,
+// beta, row and column scales) or, when K is split over several CTAs, adds
+// its integer sums into a workspace that a second kernel converts.  Every wait
 // is bounded by a 2-second %globaltimer budget; on expiry the kernel records
 // an error code, waits (bounded) for its own copies and MMAs in flight, frees
 // its TMEM and returns.
@@ -25,7 +28,9 @@ namespace {
 
 using namespace tc::ptx;
 
-constexpr int BM = 128, BN = 96, BK = 32, STAGES = 2, NTHREADS = 256;
+constexpr int BM = 128, BN = 96, BK = 32, STAGES = 2, NTHREADS = 384;
+constexpr int NFOLD = 8;                         // fold warps: 4 lane quarters x 2 column halves
+constexpr int HALF = BN / 2;                     // columns per fold thread
 constexpr int KCT = 32;                          // K tiles per exact chunk (1024 K values)
 constexpr int A_TILE = BM * BK * 2;              // one plane of A, 8 KB
 constexpr int B_TILE = BN * BK * 2;              // one plane of B, 6 KB
@@ -44,22 +49,25 @@ static_assert(A_TILE % 512 == 0 && B_TILE % 512 == 0, "64-byte swizzle atoms are
 // chunk: every partial sum is an integer multiple of 2^(-7 g) that FP32 holds exactly
 static_assert((long long)KCT * BK * 4 * 64 * 64 <= (1ll << 24), "group chunk sums must stay exact");
 
-// One element of the chunk fold: groups 0..3 are exact integers (times
-// 2^(-7 g)); the tail is rounded once to the 2^-28 unit.
-__device__ __forceinline__ long long fold_value(uint32_t a0, uint32_t a1, uint32_t a2,
-                                                uint32_t a3, uint32_t a4) {
+// One element of the chunk fold, in units of 2^-28: groups 0..3 are exact
+// integers (times 2^(-7 g)); the tail is rounded once to the unit.
+__device__ __forceinline__ long long fold_high(uint32_t a0, uint32_t a1, uint32_t a2) {
   const long long i0 = __float2int_rn(__uint_as_float(a0));
   const long long i1 = __float2int_rn(__uint_as_float(a1) * 128.f);
   const long long i2 = __float2int_rn(__uint_as_float(a2) * 16384.f);
+  return i0 * (1ll << 28) + i1 * (1ll << 21) + i2 * (1ll << 14);
+}
+__device__ __forceinline__ long long fold_low(uint32_t a3, uint32_t a4) {
   const long long i3 = __float2int_rn(__uint_as_float(a3) * 2097152.f);
   const long long it = __float2ll_rn(__uint_as_float(a4) * 268435456.f);
-  return i0 * (1ll << 28) + i1 * (1ll << 21) + i2 * (1ll << 14) + i3 * (1ll << 7) + it;
+  return i3 * (1ll << 7) + it;
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                int M, int N, int num_kt, int kt_chunk, unsigned long long* __restrict__ ws,
-               int* err) {
+               const int32_t* __restrict__ ea, const int32_t* __restrict__ eb, double alpha,
+               double beta, double* __restrict__ C, long long ldc, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -80,7 +88,7 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 128);
+    mbar_init(acc_empty, NFOLD * 32);
     mbar_init(drained, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -168,38 +176,66 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     mma_commit(drained);
     mbar_wait(drained, 0, err, 15);
   } else if (warp >= 4) {
-    // fold: TMEM lanes [32 q, 32 q + 32) hold rows m0 + 32 q + lane
-    const int q = warp - 4;
+    // fold: TMEM lanes [32 q, 32 q + 32) hold rows m0 + 32 q + lane; this
+    // warp takes the columns [c_lo, c_lo + HALF) of them
+    const int q = (warp - 4) & 3, c_lo = ((warp - 4) >> 2) * HALF;
     const int row = m0 + q * 32 + lane;
-    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c_lo;
+    long long acc[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) acc[j] = 0;
+    bool ok_all = true;
     for (int chunk = 0; chunk < nchunks; ++chunk) {
       const bool ok = mbar_wait(acc_full, (uint32_t)(chunk & 1), err, 14);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!__all_sync(0xffffffffu, ok) || *(volatile int*)&abort_flag) {
         abort_flag = 1;
+        ok_all = false;
         break;
       }
-      unsigned long long* wrow = ws + (long long)row * N;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t r0[16], r1[16], r2[16], r3[16], r4[16];
-        tmem_ld16_nowait(taddr + 0 * BN + c0, r0);
-        tmem_ld16_nowait(taddr + 1 * BN + c0, r1);
-        tmem_ld16_nowait(taddr + 2 * BN + c0, r2);
-        tmem_ld16_nowait(taddr + 3 * BN + c0, r3);
-        tmem_ld16_nowait(taddr + 4 * BN + c0, r4);
-        tmem_wait_ld();
-        if (row < M) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = n0 + c0 + j;
-            if (col < N)
-              atomicAdd(wrow + col,
-                        (unsigned long long)fold_value(r0[j], r1[j], r2[j], r3[j], r4[j]));
-          }
-        }
+      for (int cb = 0; cb < HALF / 8; ++cb) {
+        // two passes (groups 0..2, then 3 and the tail) keep few values live
+        uint32_t r0[8], r1[8], r2[8];
+        tmem_ld8_nowait(taddr + 0 * BN + cb * 8, r0);
+        tmem_ld8_nowait(taddr + 1 * BN + cb * 8, r1);
+        tmem_ld8_nowait(taddr + 2 * BN + cb * 8, r2);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[cb * 8 + j] += fold_high(r0[j], r1[j], r2[j]);
+        tmem_ld8_nowait(taddr + 3 * BN + cb * 8, r0);
+        tmem_ld8_nowait(taddr + 4 * BN + cb * 8, r1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[cb * 8 + j] += fold_low(r0[j], r1[j]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(acc_empty);
+    }
+    if (ok_all && row < M && nchunks > 0) {
+      if (gridDim.z == 1) {
+        // whole K in this CTA: scale, alpha, beta and store
+        const int32_t a = ea[row];
+        double* crow = C + (long long)row * ldc;
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) {
+          const int col = n0 + c_lo + j;
+          if (col < N) {
+            const int32_t b = eb[col];
+            const double val = (a == kNonFinite || b == kNonFinite)
+                                   ? __longlong_as_double(0x7ff8000000000000ll)
+                                   : ldexp((double)acc[j], a + b - (2 * BETA + UNIT));
+            crow[col] = (beta == 0.0) ? alpha * val : fma(alpha, val, beta * crow[col]);
+          }
+        }
+      } else {
+        unsigned long long* wrow = ws + (long long)row * N;
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) {
+          const int col = n0 + c_lo + j;
+          if (col < N) atomicAdd(wrow + col, (unsigned long long)acc[j]);
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -357,7 +393,7 @@ void gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const _
           int64_t b_plane_stride, double beta, double* C, int64_t ldc, long long* ws, int* err,
           int splitk) {
   ASCC_REQUIRE(M > 0 && N > 0 && K > 0, "oz::gemm: empty");
-  ASCC_REQUIRE(splitk >= 1 && ws, "oz::gemm: needs a workspace");
+  ASCC_REQUIRE(splitk >= 1 && (splitk == 1 || ws), "oz::gemm: split K needs a workspace");
   static std::once_flag attr_once;
   cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [&] {
@@ -378,15 +414,18 @@ void gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const _
   const int z = (num_kt + kt_chunk - 1) / kt_chunk;
   dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)z);
   ASCC_REQUIRE(grid.y <= 65535, "oz::gemm: N too large");
-  ASCC_CUDA(cudaMemsetAsync(ws, 0, ws_bytes(M, N), s));
+  if (z > 1) ASCC_CUDA(cudaMemsetAsync(ws, 0, ws_bytes(M, N), s));
   gemm_oz_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(am, bm, (int)M, (int)N, num_kt, kt_chunk,
-                                                    reinterpret_cast<unsigned long long*>(ws), err);
+                                                    reinterpret_cast<unsigned long long*>(ws), ea,
+                                                    eb, alpha, beta, C, (long long)ldc, err);
   count_launch();
   check_launch("gemm_oz");
-  oz_finish_kernel<<<grid_for(M * N), 256, 0, s>>>(C, (long long)ldc, ws, ea, eb, M, N, alpha,
-                                                   beta);
-  count_launch();
-  check_launch("oz_finish");
+  if (z > 1) {
+    oz_finish_kernel<<<grid_for(M * N), 256, 0, s>>>(C, (long long)ldc, ws, ea, eb, M, N, alpha,
+                                                     beta);
+    count_launch();
+    check_launch("oz_finish");
+  }
 }
 
 }  // namespace oz
