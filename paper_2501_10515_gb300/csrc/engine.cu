@@ -561,10 +561,11 @@ void State::dress(const double* t1) {
   box_copy(s_, Bno_.p(), {(int64_t)n * o, o, 1}, Bhat_.p(), bs, {P, n, o});
   box_copy(s_, Bon_.p(), {(int64_t)o * n, n, 1}, Bhat_.p(), bs, {P, o, n});
   // Fock matrix of H-hat: F = h + 2 J - K.  F enters R1 and R2 with O(1)
-  // weight, so it (and the oooo block of the reference energy) stays FP64 in
-  // every precision mode.
+  // weight, so it (and the oooo block of the reference energy) is built in
+  // FP64, or with the FP64-class digit-plane products when the state uses
+  // the tensor cores.
   const int lev = es_.level();
-  es_.set_split(0, err_.as<int>());
+  es_.set_split(lev ? 4 : 0, err_.as<int>(), tc_min_flops_);
   k::diag_sum(s_, dP_.p(), Bhat_.p(), P, n, o);
   es_("Ppq,P->pq", 1.0, Bhat_.t, dP_.t, 0.0, J_.t);
   es_("Ppk,Pkq->pq", 1.0, Bno_.t, Bon_.t, 0.0, K_.t);
@@ -754,9 +755,10 @@ void State::residual(const double* tv, double* rv, double* energy) {
   es_("Pkc,kicd->Pid", 1.0, Bov_.t, u_.t, 0.0, X_.t);
   es_("Pad,Pid->ia", 1.0, Bvv_.t, X_.t, 1.0, r1);                         // sum u g_adkc
   es_("klac,kilc->ia", -1.0, u_.t, gooov_.t, 1.0, r1);
-  // contractions with the Fock matrix carry O(1) x O(t) products and stay FP64
+  // contractions with the Fock matrix carry O(1) x O(t) products: FP64, or
+  // the FP64-class digit-plane products on the tensor-core paths
   const int lev = es_.level();
-  es_.set_split(0, err_.as<int>());
+  es_.set_split(lev ? 4 : 0, err_.as<int>(), tc_min_flops_);
   {
     OT Fov({o, v}, s_);
     box_copy(s_, Fov.p(), {v, 1}, F_.p() + o, {n, 1}, {o, v});
@@ -771,7 +773,7 @@ void State::residual(const double* tv, double* rv, double* energy) {
   es_("kjbc,kiac->ijab", -0.5, t2, goovv_.t, 1.0, Z_.t);
   es_("kibc,kjac->ijab", -1.0, t2, goovv_.t, 1.0, Z_.t);
   es_("jkbc,aikc->ijab", 0.5, u_.t, Lvoov_.t, 1.0, Z_.t);
-  es_.set_split(0, err_.as<int>());
+  es_.set_split(lev ? 4 : 0, err_.as<int>(), tc_min_flops_);
   {
     OT Fvv({v, v}, s_), Foo({o, o}, s_);
     box_copy(s_, Fvv.p(), {v, 1}, F_.p() + (int64_t)o * n + o, {n, 1}, {v, v});
