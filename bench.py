@@ -448,7 +448,10 @@ def main():
         "config": {"workload": wl["name"], "o": o, "v": v, "naux": s.naux,
                    "excitation": [wl["hole"], wl["particle"]], "method": "PLASCC",
                    "precision": args.precision, "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2: the (xc|bd) block (10.6 GB BF16 / 14 GB FP64) is streamed every iteration",
+                   "l2": ("inputs larger than L2: the (xc|bd) block (%.1f GB as 3 BF16 planes, "
+                          "%.1f GB as 6 digit planes, %.1f GB FP64) is streamed every iteration"
+                          % (6.0 * (o + v) * v ** 3 / 1e9, 12.0 * (o + v) * v ** 3 / 1e9,
+                             8.0 * (o + v) * v ** 3 / 1e9)),
                    "step": ("one complete solve from the zeroth-order guess to max|R| <= 1e-8, |dE| <= 1e-10"
                             if args.step == "solve" else
                             "one solve iteration (residual + convergence test + Jacobi + DIIS)")},

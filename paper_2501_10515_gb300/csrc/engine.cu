@@ -541,10 +541,22 @@ void State::dress(const double* t1) {
       box_copy(s_, rowsC_.p() + (int64_t)o * n, {(int64_t)nc * n, 1}, src + (int64_t)pcol * n,
                {nn, 1}, {batch, n});
     ASCC_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * nn * batch, cudaMemcpyDeviceToDevice, s_));
-    k::gemm_f64(s_, false, false, n, n, nc, 1.0, LamC_.p(), nc, 0, rowsC_.p(), n, (int64_t)nc * n,
-                1.0, dst, n, nn, batch);
-    k::gemm_f64(s_, false, false, n, nc, n, 1.0, dst, n, nn, RhoC_.p(), nc, 0, 0.0, colsC_.p(), nc,
-                (int64_t)n * nc, batch);
+    if (es_.level() > 0 && batch > 1) {
+      // tensor-core states: both K = |C| products as single FP64-class
+      // digit-plane GEMMs over all DF indices (FP64 DFMA is the scarce unit)
+      const int lev = es_.level();
+      es_.set_split(4, err_.as<int>(), tc_min_flops_);
+      T lam(LamC_.p(), {n, nc}), rho(RhoC_.p(), {n, nc});
+      T rows(rowsC_.p(), {batch, nc, n}), cols(colsC_.p(), {batch, n, nc}), d(dst, {batch, n, n});
+      es_("pk,Pkq->Ppq", 1.0, lam, rows, 1.0, d);
+      es_("Ppq,qj->Ppj", 1.0, d, rho, 0.0, cols);
+      es_.set_split(lev, err_.as<int>(), tc_min_flops_);
+    } else {
+      k::gemm_f64(s_, false, false, n, n, nc, 1.0, LamC_.p(), nc, 0, rowsC_.p(), n,
+                  (int64_t)nc * n, 1.0, dst, n, nn, batch);
+      k::gemm_f64(s_, false, false, n, nc, n, 1.0, dst, n, nn, RhoC_.p(), nc, 0, 0.0, colsC_.p(),
+                  nc, (int64_t)n * nc, batch);
+    }
     box_copy(s_, dst, {nn, n, 1}, colsC_.p(), {(int64_t)n * nc, nc, 1}, {batch, n, o}, 1.0, 1.0);
     if (pcol >= 0)
       box_copy(s_, dst + pcol, {nn, n}, colsC_.p() + o, {(int64_t)n * nc, nc}, {batch, n}, 1.0,

@@ -268,65 +268,93 @@ __global__ void oz_finish_kernel(double* __restrict__ C, long long ldc,
   }
 }
 
-// One block per row: row exponent from max |x|, then the balanced digits.
+// |x| as the integer bit pattern of a double (monotone in |x|; NaN and the
+// infinities sort above every finite value).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// rint(x 2^sh) for |x 2^sh| < 2^41 from the bits of x: integer arithmetic
+// only (round half away from zero), no FP64 instruction.
+__device__ __forceinline__ long long scaled_int(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  unsigned long long m = b & 0xfffffffffffffull;
+  int e2 = -1074;  // x = m 2^e2
+  if (ef != 0) {
+    m |= 1ull << 52;
+    e2 = ef - 1075;
+  }
+  const int s = e2 + sh;
+  long long q;
+  if (s >= 0) {
+    q = (long long)(m << s);  // no overflow: |q| < 2^41
+  } else if (s > -64) {
+    const int r = -s;
+    q = (long long)((m >> r) + ((m >> (r - 1)) & 1ull));
+  } else {
+    q = 0;
+  }
+  return (b >> 63) ? -q : q;
+}
+
+// One block per row (a warp per row when rows are short): row exponent from
+// max |x|, then the balanced digits, in integer arithmetic.
 __global__ void oz_split_kernel(__nv_bfloat16* __restrict__ out, int32_t* __restrict__ exps,
                                 const double* __restrict__ in, long long rows, long long K,
                                 long long ld, long long Kp, long long plane_stride) {
-  __shared__ double red_max[32];
-  __shared__ int red_bad[32];
-  __shared__ int row_e;
-  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
-    const double* x = in + r * ld;
-    double mx = 0.0;
-    int bad = 0;
-    for (long long k = threadIdx.x; k < K; k += blockDim.x) {
-      const double a = fabs(x[k]);
-      if (!(a <= 1.7976931348623157e308)) bad = 1;  // NaN or infinity
-      else mx = fmax(mx, a);
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-      bad |= __shfl_xor_sync(0xffffffffu, bad, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red_max[threadIdx.x >> 5] = mx;
-      red_bad[threadIdx.x >> 5] = bad;
+  // groups of `width` threads share a row
+  const int width = (Kp <= 256) ? 32 : (int)blockDim.x;
+  const int groups = blockDim.x / width, g = threadIdx.x / width, t = threadIdx.x % width;
+  __shared__ unsigned long long red[32];
+  __shared__ int row_e[8];
+  for (long long r0 = (long long)blockIdx.x * groups; r0 < rows; r0 += (long long)gridDim.x * groups) {
+    const long long r = r0 + g;
+    const bool live = r < rows;
+    const double* x = in + (live ? r : 0) * ld;
+    unsigned long long mx = 0;
+    if (live)
+      for (long long k = t; k < K; k += width) mx = max(mx, abs_bits(x[k]));
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (width == 32) {
+      if (t == 0) red[g] = mx;
+    } else if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = mx;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double m = 0.0;
-      int b = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        m = fmax(m, red_max[w]);
-        b |= red_bad[w];
-      }
+    if (t == 0 && live) {
+      unsigned long long m = red[g];
+      if (width != 32)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
       int e = 0;
-      if (b) {
+      if (m >= 0x7ff0000000000000ull) {
         e = kNonFinite;
-      } else if (m > 0.0) {
+      } else if (m != 0) {
         int E;
-        frexp(m, &E);  // m = f 2^E, f in [1/2, 1)
-        e = E + 1;     // max |x| < 2^(e - 1)
+        frexp(__longlong_as_double((long long)m), &E);  // max |x| = f 2^E, f in [1/2, 1)
+        e = E + 1;                                      // max |x| < 2^(e - 1)
       }
-      row_e = e;
+      row_e[g] = e;
       exps[r] = e;
     }
     __syncthreads();
-    const int e = row_e;
-    for (long long k = threadIdx.x; k < Kp; k += blockDim.x) {
-      long long q = 0;
-      if (e != kNonFinite && k < K) q = llrint(ldexp(x[k], L - e));  // |q| <= 2^41
-      // balanced base-2^7 digits from the least significant end
-      __nv_bfloat16 dig[NSLICE];
+    if (live) {
+      const int e = row_e[g];
+      for (long long k = t; k < Kp; k += width) {
+        long long q = 0;
+        if (e != kNonFinite && k < K) q = scaled_int(x[k], L - e);  // |q| <= 2^41
+        // balanced base-2^7 digits from the least significant end
+        __nv_bfloat16 dig[NSLICE];
 #pragma unroll
-      for (int s = NSLICE - 1; s >= 1; --s) {
-        const long long d = ((q + 64) & 127) - 64;
-        q = (q - d) >> BETA;
-        dig[s] = __float2bfloat16_rn(ldexpf((float)d, -BETA * s));
+        for (int s = NSLICE - 1; s >= 1; --s) {
+          const long long d = ((q + 64) & 127) - 64;
+          q = (q - d) >> BETA;
+          dig[s] = __float2bfloat16_rn(ldexpf((float)d, -BETA * s));
+        }
+        dig[0] = __float2bfloat16_rn((float)q);
+#pragma unroll
+        for (int s = 0; s < NSLICE; ++s) out[(long long)s * plane_stride + r * Kp + k] = dig[s];
       }
-      dig[0] = __float2bfloat16_rn((float)q);
-#pragma unroll
-      for (int s = 0; s < NSLICE; ++s) out[(long long)s * plane_stride + r * Kp + k] = dig[s];
     }
     __syncthreads();
   }
@@ -362,7 +390,8 @@ void split(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const double* i
   if (rows <= 0) return;
   const int64_t Kp = padded_k(K);
   if (plane_stride <= 0) plane_stride = rows * Kp;
-  const int g = (int)std::min<int64_t>(rows, 152 * 8);
+  const int per = (Kp <= 256) ? 8 : 1;  // rows per block: a warp each for short rows
+  const int g = (int)std::min<int64_t>((rows + per - 1) / per, 152 * 8);
   oz_split_kernel<<<g, 256, 0, s>>>(planes, exps, in, rows, K, ld, Kp, plane_stride);
   count_launch();
   check_launch("oz_split");

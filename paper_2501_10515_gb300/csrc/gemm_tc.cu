@@ -3,8 +3,9 @@
 //   C (FP64, row-major) = alpha * sum_{(u,w) in segs} A_u B_w^T + beta * C
 //
 // A_u [M][Kp] and B_w [N][Kp] are BF16, K-major (row-major with K
-// contiguous), Kp a multiple of 64.  A FP64 operand x is carried as
-// x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1));
+// contiguous), Kp a multiple of 64.  A FP64 operand x is rounded to FP32
+// (f) and carried as f = x0 + x1 + x2 (x0 = bf16(f), x1 = bf16(f - x0),
+// x2 = bf16(f - x0 - x1), the subtractions exact in FP32);
 // the products x0 y0, x0 y1, x1 y0 (, x0 y2, x1 y1, x2 y0) recover 16 (24)
 // significant bits, each product exact in the FP32 accumulator.
 //
@@ -14,6 +15,7 @@
 // (tcgen05.ld 32x32b) for the FP64 epilogue.  Every wait is bounded by a
 // 2-second %globaltimer budget; on expiry the kernel records an error code,
 // skips the remaining work, frees its TMEM and returns.
+#include <algorithm>
 #include <mutex>
 
 #include "gemm_tc.h"
@@ -170,35 +172,48 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
   }
 }
 
-// C = alpha * sum_z ws[z] + beta * C, the split-K partials summed in FP64 in a
-// fixed order.
+// C = alpha * sum_z ws[z] + beta * C.  The FP32 partials are summed in FP32
+// with a compensation term (Fast2Sum), i.e. to about 2^-48 relative, in a
+// fixed order, and converted to FP64 once: the FP64 units are the scarce
+// ones on this part.
 __global__ void splitk_reduce_kernel(double* __restrict__ C, long long ldc,
                                      const float* __restrict__ ws, long long M, long long N,
                                      int nz, double alpha, double beta) {
   const long long total = M * N;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int z = 0; z < nz; ++z) acc += (double)ws[(long long)z * total + idx];
-    const long long m = idx / N, n = idx % N;
-    double* c = C + m * ldc + n;
-    *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *c);
+  for (long long m = blockIdx.y; m < M; m += gridDim.y) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+      const long long idx = m * N + n;
+      float hi = 0.f, lo = 0.f;
+      for (int z = 0; z < nz; ++z) {
+        const float x = ws[(long long)z * total + idx];
+        const float t = hi + x;
+        lo += (fabsf(hi) >= fabsf(x)) ? (hi - t) + x : (x - t) + hi;
+        hi = t;
+      }
+      const double acc = (double)hi + (double)lo;
+      double* c = C + m * ldc + n;
+      *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *c);
+    }
   }
 }
 
 // FP64 [rows][K] (row stride ld) -> nsplit BF16 planes [nsplit][rows][Kp], zero padded.
+// The value is rounded to FP32 once (24 significant bits, as many as three
+// planes hold) and split with exact FP32 subtractions.
 __global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double* __restrict__ in,
                                   long long rows, long long K, long long ld, long long Kp,
                                   int nsplit, long long plane_stride) {
-  const long long total = rows * Kp;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / Kp, k = idx % Kp;
-    double x = (k < K) ? in[r * ld + k] : 0.0;
-    for (int s = 0; s < nsplit; ++s) {
-      const __nv_bfloat16 h = __double2bfloat16(x);
-      out[(long long)s * plane_stride + idx] = h;
-      x -= (double)__bfloat162float(h);
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double* x = in + r * ld;
+    __nv_bfloat16* o = out + r * Kp;
+    for (long long k = threadIdx.x; k < Kp; k += blockDim.x) {
+      float f = (k < K) ? (float)x[k] : 0.f;
+      for (int s = 0; s < nsplit; ++s) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(f);
+        o[(long long)s * plane_stride + k] = h;
+        f -= __bfloat162float(h);
+      }
     }
   }
 }
@@ -240,9 +255,8 @@ void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t ro
   const int64_t Kp = padded_k(K), total = rows * Kp;
   if (total == 0) return;
   if (plane_stride <= 0) plane_stride = total;
-  int64_t g = (total + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  split_bf16_kernel<<<(int)g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit, plane_stride);
+  const int g = (int)std::min<int64_t>(rows, 152 * 16);
+  split_bf16_kernel<<<g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit, plane_stride);
   count_launch();
   check_launch("split_bf16");
 }
@@ -300,9 +314,10 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   count_launch();
   check_launch("gemm_tc");
   if (splitk > 1) {
-    int64_t g = (M * N + 255) / 256;
-    if (g > 152 * 16) g = 152 * 16;
-    splitk_reduce_kernel<<<(int)g, 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk, alpha, beta);
+    const unsigned gx = (unsigned)std::min<int64_t>((N + 255) / 256, 64);
+    const unsigned gy = (unsigned)std::min<int64_t>(M, 65535);
+    splitk_reduce_kernel<<<dim3(gx, gy), 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk, alpha,
+                                                     beta);
     count_launch();
     check_launch("splitk_reduce");
   }

@@ -16,7 +16,7 @@ int products_for(int level);
 
 // out[s * plane_stride + r * Kp + k] = s-th BF16 plane of in[r][k] (row stride
 // ld), zero padded to Kp; s < nsplit; plane_stride <= 0 means rows * Kp.
-// x = sum_s plane_s up to the last plane's rounding.
+// x = sum_s plane_s up to the FP32 rounding of x and the last plane's rounding.
 void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t rows, int64_t K,
                 int64_t ld, int nsplit, int64_t plane_stride = 0);
 

@@ -1,5 +1,6 @@
 // FP64 kernels of the residual engine: a tiled DFMA GEMM, strided copies,
 // reductions and the elementwise steps of the amplitude update.
+#include <algorithm>
 #include <atomic>
 
 #include "kernels.h"
@@ -132,6 +133,74 @@ __global__ void strided_copy_kernel(double* __restrict__ out, const double* __re
     }
     const double val = alpha * in[ioff];
     out[ooff] = (beta == 0.0) ? val : val + beta * out[ooff];
+  }
+}
+
+// Row-wise copy: the last dimension is walked by the threads (len values per
+// row, `per` rows per block pass), the outer index is decomposed once per row.
+// PLAIN (alpha = 1, beta = 0) moves the bits without FP64 arithmetic.
+template <bool PLAIN>
+__global__ void copy_rows_kernel(double* __restrict__ out, const double* __restrict__ in,
+                                 int64_t rows, int len, int per, Strides st, int64_t is_last,
+                                 int64_t os_last, double alpha, double beta) {
+  const int sub = threadIdx.x / (blockDim.x / per), t = threadIdx.x % (blockDim.x / per);
+  const int width = blockDim.x / per;
+  for (int64_t row = (int64_t)blockIdx.x * per + sub; row < rows; row += (int64_t)gridDim.x * per) {
+    int64_t rem = row, ioff = 0, ooff = 0;
+    for (int d = st.nd - 1; d >= 0; --d) {
+      const int64_t c = rem % st.shape[d];
+      rem /= st.shape[d];
+      ioff += c * st.istride[d];
+      ooff += c * st.ostride[d];
+    }
+    for (int j = t; j < len; j += width) {
+      const double v = in[ioff + j * is_last];
+      double* o = out + ooff + j * os_last;
+      if (PLAIN) *o = v;
+      else *o = (beta == 0.0) ? alpha * v : fma(alpha, v, beta * *o);
+    }
+  }
+}
+
+// Tiled transpose: dimension a is contiguous in the input and the last
+// dimension b in the output; 32 x 32 tiles go through shared memory so that
+// both the loads and the stores are coalesced.  The other dimensions (st)
+// are decomposed once per tile.
+template <bool PLAIN>
+__global__ void copy_transpose_kernel(double* __restrict__ out, const double* __restrict__ in,
+                                      int64_t na, int64_t nb, int64_t outer, Strides st,
+                                      int64_t is_b, int64_t os_a, double alpha, double beta) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int64_t ta_n = (na + 31) / 32, tb_n = (nb + 31) / 32;
+  const int64_t ntiles = outer * ta_n * tb_n;
+  for (int64_t tid = blockIdx.x; tid < ntiles; tid += gridDim.x) {
+    const int64_t tb = tid % tb_n, ta = (tid / tb_n) % ta_n, q = tid / (tb_n * ta_n);
+    int64_t rem = q, ioff = 0, ooff = 0;
+    for (int d = st.nd - 1; d >= 0; --d) {
+      const int64_t c = rem % st.shape[d];
+      rem /= st.shape[d];
+      ioff += c * st.istride[d];
+      ooff += c * st.ostride[d];
+    }
+    const int64_t a0 = ta * 32, b0 = tb * 32;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t a = a0 + tx, b = b0 + ty + 8 * i;
+      if (a < na && b < nb) tile[ty + 8 * i][tx] = in[ioff + a + b * is_b];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t b = b0 + tx, a = a0 + ty + 8 * i;
+      if (a < na && b < nb) {
+        const double v = tile[tx][ty + 8 * i];
+        double* o = out + ooff + a * os_a + b;
+        if (PLAIN) *o = v;
+        else *o = (beta == 0.0) ? alpha * v : fma(alpha, v, beta * *o);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -498,17 +567,82 @@ void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const 
                   const int64_t* in_stride, int nd, const int64_t* shape, double alpha,
                   double beta) {
   ASCC_REQUIRE(nd >= 1 && nd <= 8, "strided_copy: 1..8 dimensions");
-  Strides st;
-  st.nd = nd;
+  // drop unit dimensions
+  int64_t sh[8], is[8], os[8];
+  int m = 0;
   int64_t total = 1;
   for (int d = 0; d < nd; ++d) {
-    st.shape[d] = shape[d];
-    st.istride[d] = in_stride[d];
-    st.ostride[d] = out_stride[d];
     total *= shape[d];
+    if (shape[d] == 1) continue;
+    sh[m] = shape[d];
+    is[m] = in_stride[d];
+    os[m] = out_stride[d];
+    ++m;
   }
   if (total == 0) return;
-  strided_copy_kernel<<<grid_for(total), 256, 0, s>>>(out, in, total, st, alpha, beta);
+  if (m == 0) {
+    sh[0] = 1;
+    is[0] = os[0] = 1;
+    m = 1;
+  }
+  const bool plain = alpha == 1.0 && beta == 0.0;
+  const int last = m - 1;
+  // the input-contiguous dimension, if it is not the last one
+  int a = -1;
+  for (int d = 0; d < last; ++d)
+    if (is[d] == 1) a = d;
+  if (os[last] == 1 && is[last] != 1 && a >= 0 && out != in && sh[last] >= 8 && sh[a] >= 8) {
+    Strides st;
+    st.nd = 0;
+    int64_t outer = 1;
+    for (int d = 0; d < last; ++d) {
+      if (d == a) continue;
+      st.shape[st.nd] = sh[d];
+      st.istride[st.nd] = is[d];
+      st.ostride[st.nd] = os[d];
+      ++st.nd;
+      outer *= sh[d];
+    }
+    const int64_t tiles = outer * ((sh[a] + 31) / 32) * ((sh[last] + 31) / 32);
+    const int g = (int)std::min<int64_t>(tiles, 152 * 16);
+    if (plain)
+      copy_transpose_kernel<true><<<g, dim3(32, 8), 0, s>>>(out, in, sh[a], sh[last], outer, st,
+                                                            is[last], os[a], alpha, beta);
+    else
+      copy_transpose_kernel<false><<<g, dim3(32, 8), 0, s>>>(out, in, sh[a], sh[last], outer, st,
+                                                             is[last], os[a], alpha, beta);
+  } else if (os[last] == 1 || is[last] == 1) {
+    // rows along the last dimension (coalesced on at least one side)
+    Strides st;
+    st.nd = last;
+    int64_t rows = 1;
+    for (int d = 0; d < last; ++d) {
+      st.shape[d] = sh[d];
+      st.istride[d] = is[d];
+      st.ostride[d] = os[d];
+      rows *= sh[d];
+    }
+    const int len = (int)sh[last];
+    int per = 1;
+    while (per < 32 && 256 / (per * 2) >= len) per *= 2;  // several short rows per block
+    const int64_t blocks = (rows + per - 1) / per;
+    const int g = (int)std::min<int64_t>(blocks, 152 * 16);
+    if (plain)
+      copy_rows_kernel<true><<<g, 256, 0, s>>>(out, in, rows, len, per, st, is[last], os[last],
+                                               alpha, beta);
+    else
+      copy_rows_kernel<false><<<g, 256, 0, s>>>(out, in, rows, len, per, st, is[last], os[last],
+                                                alpha, beta);
+  } else {
+    Strides st;
+    st.nd = m;
+    for (int d = 0; d < m; ++d) {
+      st.shape[d] = sh[d];
+      st.istride[d] = is[d];
+      st.ostride[d] = os[d];
+    }
+    strided_copy_kernel<<<grid_for(total), 256, 0, s>>>(out, in, total, st, alpha, beta);
+  }
   count_launch();
   check_launch("strided_copy");
 }
