@@ -31,6 +31,7 @@ using namespace tc::ptx;
 constexpr int BM = 128, BN = 96, BK = 32, STAGES = 2, NTHREADS = 384;
 constexpr int NFOLD = 8;                         // fold warps: 4 lane quarters x 2 column halves
 constexpr int HALF = BN / 2;                     // columns per fold thread
+constexpr int PITCH = BN + 1;                    // int64 epilogue tile pitch (odd)
 constexpr int KCT = 32;                          // K tiles per exact chunk (1024 K values)
 constexpr int A_TILE = BM * BK * 2;              // one plane of A, 8 KB
 constexpr int B_TILE = BN * BK * 2;              // one plane of B, 6 KB
@@ -44,6 +45,8 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barrier
 constexpr int L = NSLICE * BETA;                 // 42 bits per scaled value
 constexpr int UNIT = 4 * BETA;                   // fold unit 2^-28
 static_assert(NACC * BN <= TMEM_COLS, "TMEM holds 512 columns");
+static_assert(BM * PITCH * 8 <= STAGES * STAGE_BYTES, "the epilogue tile reuses the ring");
+static_assert(NTHREADS % BN == 0, "whole rows per store pass");
 static_assert(A_TILE % 512 == 0 && B_TILE % 512 == 0, "64-byte swizzle atoms are 512 bytes");
 // |digit| <= 64, so a group of g + 1 <= 4 products sums to at most 1024 * 4 * 4096 = 2^24 per
 // chunk: every partial sum is an integer multiple of 2^(-7 g) that FP32 holds exactly
@@ -179,7 +182,6 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     // fold: TMEM lanes [32 q, 32 q + 32) hold rows m0 + 32 q + lane; this
     // warp takes the columns [c_lo, c_lo + HALF) of them
     const int q = (warp - 4) & 3, c_lo = ((warp - 4) >> 2) * HALF;
-    const int row = m0 + q * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c_lo;
     long long acc[HALF];
 #pragma unroll
@@ -212,28 +214,34 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(acc_empty);
     }
-    if (ok_all && row < M && nchunks > 0) {
-      if (gridDim.z == 1) {
-        // whole K in this CTA: scale, alpha, beta and store
-        const int32_t a = ea[row];
-        double* crow = C + (long long)row * ldc;
+    // park the integer sums in the idle ring (every MMA and copy has completed)
+    if (ok_all && nchunks > 0) {
+      long long* tile = reinterpret_cast<long long*>(smem);
 #pragma unroll
-        for (int j = 0; j < HALF; ++j) {
-          const int col = n0 + c_lo + j;
-          if (col < N) {
-            const int32_t b = eb[col];
-            const double val = (a == kNonFinite || b == kNonFinite)
-                                   ? __longlong_as_double(0x7ff8000000000000ll)
-                                   : ldexp((double)acc[j], a + b - (2 * BETA + UNIT));
-            crow[col] = (beta == 0.0) ? alpha * val : fma(alpha, val, beta * crow[col]);
-          }
-        }
-      } else {
-        unsigned long long* wrow = ws + (long long)row * N;
-#pragma unroll
-        for (int j = 0; j < HALF; ++j) {
-          const int col = n0 + c_lo + j;
-          if (col < N) atomicAdd(wrow + col, (unsigned long long)acc[j]);
+      for (int j = 0; j < HALF; ++j) tile[(q * 32 + lane) * PITCH + c_lo + j] = acc[j];
+    }
+  }
+  // all warps: coalesced rows of C (scale, alpha, beta) or of the split-K
+  // integer workspace
+  const bool go = __syncthreads_and(!*(volatile int*)&abort_flag) != 0;
+  if (go && nchunks > 0) {
+    const long long* tile = reinterpret_cast<const long long*>(smem);
+    const int rows = min(BM, M - m0);
+    constexpr int RPP = NTHREADS / BN;  // rows per pass
+    const int c = threadIdx.x % BN, col = n0 + c;
+    if (col < N) {
+      const int32_t b = eb[col];
+      for (int rr = threadIdx.x / BN; rr < rows; rr += RPP) {
+        const long long v = tile[rr * PITCH + c], row = m0 + rr;
+        if (gridDim.z == 1) {
+          const int32_t a = ea[row];
+          const double val = (a == kNonFinite || b == kNonFinite)
+                                 ? __longlong_as_double(0x7ff8000000000000ll)
+                                 : ldexp((double)v, a + b - (2 * BETA + UNIT));
+          double* cp = C + row * ldc + col;
+          *cp = (beta == 0.0) ? alpha * val : fma(alpha, val, beta * *cp);
+        } else {
+          atomicAdd(ws + row * N + col, (unsigned long long)v);
         }
       }
     }

@@ -30,6 +30,7 @@ constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 256;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+static_assert(BM * (BN + 1) * 4 <= STAGES * STAGE_BYTES, "the epilogue tile reuses the ring");
 
 struct Segs {
   int n;
@@ -121,46 +122,42 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
     mma_commit(done);
   }
   __syncwarp();
-  // epilogue: TMEM lanes [32 warp, 32 warp + 32) hold rows m0 + 32 warp + lane
+  // epilogue: TMEM lanes [32 warp, 32 warp + 32) hold rows m0 + 32 warp + lane.
+  // The tile goes through shared memory (the ring is idle once every MMA has
+  // completed) so that the FP64 (or FP32 partial) stores are coalesced rows.
   const bool ok = mbar_wait(done, 0, err, 3);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // tcgen05.ld is warp-collective: take the decision per warp
-  const bool go = __all_sync(0xffffffffu, ok) && !*(volatile int*)&abort_flag;
-  if (go && total > 0) {
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(taddr + c0, r);
-      if (row < M) {
-        if (ws) {
-          // split-K partial, summed later in FP64
-          float* wrow = ws + ((long long)blockIdx.z * M + row) * N;
+  const bool go = __syncthreads_and(ok && !*(volatile int*)&abort_flag) != 0;
+  if (go) {
+    constexpr int PITCH = BN + 1;  // odd pitch: conflict-free column writes
+    float* tile = reinterpret_cast<float*>(smem);
+    const int lrow = warp * 32 + lane;
+    if (total > 0) {
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(taddr + c0, r);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = n0 + c0 + j;
-            if (col < N) wrow[col] = __uint_as_float(r[j]);
-          }
-        } else {
-          double* crow = C + (long long)row * ldc;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = n0 + c0 + j;
-            if (col < N) {
-              const double acc = (double)__uint_as_float(r[j]);
-              crow[col] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * crow[col]);
-            }
-          }
-        }
+        for (int j = 0; j < 16; ++j) tile[lrow * PITCH + c0 + j] = __uint_as_float(r[j]);
       }
     }
-  } else if (go && ws) {
-    // an empty chunk (K shorter than the grid) contributes zeros
-    const int row = m0 + warp * 32 + lane;
-    if (row < M) {
-      float* wrow = ws + ((long long)blockIdx.z * M + row) * N;
-      for (int j = 0; j < BN; ++j)
-        if (n0 + j < N) wrow[n0 + j] = 0.f;
+    __syncthreads();
+    const int rows = min(BM, M - m0);
+    for (int rr = 0; rr < rows; ++rr) {
+      const long long row = m0 + rr;
+      for (int c = threadIdx.x; c < BN; c += NTHREADS) {
+        const int col = n0 + c;
+        if (col >= N) break;
+        const float a = total > 0 ? tile[rr * PITCH + c] : 0.f;
+        if (ws) {
+          // split-K partial, summed later
+          ws[((long long)blockIdx.z * M + row) * N + col] = a;
+        } else {
+          double* cp = C + row * ldc + col;
+          const double acc = (double)a;
+          *cp = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *cp);
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -200,20 +197,28 @@ __global__ void splitk_reduce_kernel(double* __restrict__ C, long long ldc,
 
 // FP64 [rows][K] (row stride ld) -> nsplit BF16 planes [nsplit][rows][Kp], zero padded.
 // The value is rounded to FP32 once (24 significant bits, as many as three
-// planes hold) and split with exact FP32 subtractions.
+// planes hold) and split with exact FP32 subtractions.  Each thread converts a
+// run of 8 consecutive values of one row and writes 16 bytes per plane.
 __global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double* __restrict__ in,
                                   long long rows, long long K, long long ld, long long Kp,
                                   int nsplit, long long plane_stride) {
-  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
-    const double* x = in + r * ld;
-    __nv_bfloat16* o = out + r * Kp;
-    for (long long k = threadIdx.x; k < Kp; k += blockDim.x) {
-      float f = (k < K) ? (float)x[k] : 0.f;
-      for (int s = 0; s < nsplit; ++s) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(f);
-        o[(long long)s * plane_stride + k] = h;
-        f -= __bfloat162float(h);
+  const long long runs = Kp / 8, total = rows * runs;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+    const double* x = in + r * ld + k0;
+    float f[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = (k0 + j < K) ? (float)x[j] : 0.f;
+    for (int s = 0; s < nsplit; ++s) {
+      __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        h[j] = __float2bfloat16_rn(f[j]);
+        f[j] -= __bfloat162float(h[j]);
       }
+      *reinterpret_cast<uint4*>(out + (long long)s * plane_stride + r * Kp + k0) =
+          *reinterpret_cast<const uint4*>(h);
     }
   }
 }
@@ -255,7 +260,7 @@ void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t ro
   const int64_t Kp = padded_k(K), total = rows * Kp;
   if (total == 0) return;
   if (plane_stride <= 0) plane_stride = total;
-  const int g = (int)std::min<int64_t>(rows, 152 * 16);
+  const int g = (int)std::min<int64_t>((rows * (Kp / 8) + 255) / 256, 152 * 16);
   split_bf16_kernel<<<g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit, plane_stride);
   count_launch();
   check_launch("split_bf16");

@@ -153,11 +153,23 @@ __global__ void copy_rows_kernel(double* __restrict__ out, const double* __restr
       ioff += c * st.istride[d];
       ooff += c * st.ostride[d];
     }
-    for (int j = t; j < len; j += width) {
-      const double v = in[ioff + j * is_last];
-      double* o = out + ooff + j * os_last;
-      if (PLAIN) *o = v;
-      else *o = (beta == 0.0) ? alpha * v : fma(alpha, v, beta * *o);
+    // four independent loads in flight per thread
+    for (int j0 = t; j0 < len; j0 += 4 * width) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u * width;
+        v[u] = (j < len) ? in[ioff + j * is_last] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u * width;
+        if (j < len) {
+          double* o = out + ooff + j * os_last;
+          if (PLAIN) *o = v[u];
+          else *o = (beta == 0.0) ? alpha * v[u] : fma(alpha, v[u], beta * *o);
+        }
+      }
     }
   }
 }
