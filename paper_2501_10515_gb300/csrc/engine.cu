@@ -154,7 +154,7 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
     Bp = Btmp.p();
   }
   const std::string cl = bat + Ml + Nl;
-  if (level_ > 0 && nb == 1 && 2.0 * Ms * Ns * Ks >= min_flops_) {
+  if (level_ > 0 && nb == 1 && Ms > 1 && Ns > 1 && 2.0 * Ms * Ns * Ks >= min_flops_) {
     // tensor-core path: A as [M][K], B as [N][K] (K contiguous), split into BF16 planes
     const double* Am = A.p;
     OT Am_t, Bn_t;
@@ -208,6 +208,17 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
     return;
   }
   const int64_t lda = ta ? Ms : Ks, ldb = tb ? Ks : Ns;
+  if (Ns == 1 && nb == 1 && Ks > 0) {
+    // matrix-vector product: memory-bound, FP64 on every path
+    if (sp.c == cl) {
+      k::gemv_f64(s_, ta, Ms, Ks, alpha, Ap, lda, Bp, beta, C.p);
+    } else {
+      OT Ct(shape_of(cl), s_);
+      k::gemv_f64(s_, ta, Ms, Ks, 1.0, Ap, lda, Bp, 0.0, Ct.p());
+      perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
+    }
+    return;
+  }
   if (sp.c == cl) {
     k::gemm_f64(s_, ta, tb, Ms, Ns, Ks, alpha, Ap, lda, Ms * Ks, Bp, ldb, Ks * Ns, beta, C.p, Ns,
                 Ms * Ns, nb);
@@ -723,15 +734,29 @@ void State::ladder(const T& t2, const T& r2) {
   box_copy(s_, Z1_.p(), {v, 1}, Yfull_.p() + o, {n, 1}, {oo * n, v});
   box_copy(s_, YC_.p(), {nc, 1}, Yfull_.p(), {n, 1}, {oo * n, o});
   if (pcol >= 0) box_copy(s_, YC_.p() + o, {nc}, Yfull_.p() + pcol, {n}, {oo * n});
-  k::gemm_f64(s_, false, true, oo * n, v, nc, 1.0, YC_.p(), nc, 0, LamV, nc, 0, 1.0, Z1_.p(), v, 0,
-              1);
+  const int lev = es_.level();
+  if (lev > 0) {
+    // tensor-core states: the K = |C| products as FP64-class digit planes
+    es_.set_split(4, err_.as<int>(), tc_min_flops_);
+    es_("mk,ak->ma", 1.0, T(YC_.p(), {oo * n, nc}), T((double*)LamV, {v, nc}), 1.0,
+        T(Z1_.p(), {oo * n, v}));
+  } else {
+    k::gemm_f64(s_, false, true, oo * n, v, nc, 1.0, YC_.p(), nc, 0, LamV, nc, 0, 1.0, Z1_.p(), v,
+                0, 1);
+  }
   box_copy(s_, r2.p, {vv, 1}, Z1_.p() + (int64_t)o * v, {(int64_t)n * v, 1}, {oo, vv}, 1.0, 1.0);
   box_copy(s_, Z1C_.p(), {(int64_t)nc * v, v, 1}, Z1_.p(), {(int64_t)n * v, v, 1}, {oo, o, v});
   if (pcol >= 0)
     box_copy(s_, Z1C_.p() + (int64_t)o * v, {(int64_t)nc * v, 1}, Z1_.p() + (int64_t)pcol * v,
              {(int64_t)n * v, 1}, {oo, v});
-  k::gemm_f64(s_, false, false, v, v, nc, 1.0, LamV, nc, 0, Z1C_.p(), v, (int64_t)nc * v, 1.0,
-              r2.p, v, vv, oo);
+  if (lev > 0) {
+    es_("ak,xkb->xab", 1.0, T((double*)LamV, {v, nc}), T(Z1C_.p(), {oo, nc, v}), 1.0,
+        T(r2.p, {oo, v, v}));
+    es_.set_split(lev, err_.as<int>(), tc_min_flops_);
+  } else {
+    k::gemm_f64(s_, false, false, v, v, nc, 1.0, LamV, nc, 0, Z1C_.p(), v, (int64_t)nc * v, 1.0,
+                r2.p, v, vv, oo);
+  }
 }
 
 // Terms bilinear in T2 with intermediates built from (t, u = 2t - t^T) and

@@ -13,6 +13,11 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
               const double* B, int64_t ldb, int64_t sB, double beta, double* C,
               int64_t ldc, int64_t sC, int64_t batch);
 
+// y[m] = alpha * sum_k op(A)[m][k] x[k] + beta * y[m] (op(A) is M x K;
+// ta: A stored K x M).  A warp per row (ta = false) or a thread per row.
+void gemv_f64(cudaStream_t s, bool ta, int64_t M, int64_t K, double alpha, const double* A,
+              int64_t lda, const double* x, double beta, double* y);
+
 // out[strided] = alpha * in[strided] + beta * out over an nd-dimensional
 // index box `shape` (strides in elements, one per dimension).
 void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride,

@@ -216,6 +216,31 @@ __global__ void copy_transpose_kernel(double* __restrict__ out, const double* __
   }
 }
 
+__global__ void gemv_rows_kernel(int64_t M, int64_t K, double alpha, const double* __restrict__ A,
+                                 int64_t lda, const double* __restrict__ x, double beta,
+                                 double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; m < M;
+       m += (int64_t)gridDim.x * blockDim.x / 32) {
+    const double* a = A + m * lda;
+    double acc = 0.0;
+    for (int64_t k = lane; k < K; k += 32) acc = fma(a[k], x[k], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[m] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * y[m]);
+  }
+}
+
+__global__ void gemv_cols_kernel(int64_t M, int64_t K, double alpha, const double* __restrict__ A,
+                                 int64_t lda, const double* __restrict__ x, double beta,
+                                 double* __restrict__ y) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t k = 0; k < K; ++k) acc = fma(A[k * lda + m], x[k], acc);
+    y[m] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * y[m]);
+  }
+}
+
 __global__ void fill_kernel(double* x, double v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -597,6 +622,23 @@ void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const 
     is[0] = os[0] = 1;
     m = 1;
   }
+  // merge neighbouring dimensions that are contiguous on both sides
+  {
+    int w = 0;
+    for (int d = 1; d < m; ++d) {
+      if (is[w] == is[d] * sh[d] && os[w] == os[d] * sh[d] && sh[w] * sh[d] <= (1ll << 30)) {
+        sh[w] *= sh[d];
+        is[w] = is[d];
+        os[w] = os[d];
+      } else {
+        ++w;
+        sh[w] = sh[d];
+        is[w] = is[d];
+        os[w] = os[d];
+      }
+    }
+    m = w + 1;
+  }
   const bool plain = alpha == 1.0 && beta == 0.0;
   const int last = m - 1;
   // the input-contiguous dimension, if it is not the last one
@@ -635,8 +677,11 @@ void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const 
       rows *= sh[d];
     }
     const int len = (int)sh[last];
-    int per = 1;
-    while (per < 32 && 256 / (per * 2) >= len) per *= 2;  // several short rows per block
+    // threads per row: about four values each, 32..256; the rest of the block
+    // takes further rows
+    int width = 32;
+    while (width < 256 && 4 * width < len) width *= 2;
+    const int per = 256 / width;
     const int64_t blocks = (rows + per - 1) / per;
     const int g = (int)std::min<int64_t>(blocks, 152 * 16);
     if (plain)
@@ -657,6 +702,18 @@ void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const 
   }
   count_launch();
   check_launch("strided_copy");
+}
+
+void gemv_f64(cudaStream_t s, bool ta, int64_t M, int64_t K, double alpha, const double* A,
+              int64_t lda, const double* x, double beta, double* y) {
+  if (M <= 0) return;
+  if (ta)
+    gemv_cols_kernel<<<grid_for(M), 256, 0, s>>>(M, K, alpha, A, lda, x, beta, y);
+  else
+    gemv_rows_kernel<<<(int)std::min<int64_t>((M * 32 + 255) / 256, 152 * 16), 256, 0, s>>>(
+        M, K, alpha, A, lda, x, beta, y);
+  count_launch();
+  check_launch("gemv_f64");
 }
 
 void fill(cudaStream_t s, double* x, double v, int64_t n) {
