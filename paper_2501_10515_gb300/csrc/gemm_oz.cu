@@ -306,65 +306,80 @@ __device__ __forceinline__ long long scaled_int(double x, int sh) {
   return (b >> 63) ? -q : q;
 }
 
-// One block per row (a warp per row when rows are short): row exponent from
-// max |x|, then the balanced digits, in integer arithmetic.
-__global__ void oz_split_kernel(__nv_bfloat16* __restrict__ out, int32_t* __restrict__ exps,
-                                const double* __restrict__ in, long long rows, long long K,
-                                long long ld, long long Kp, long long plane_stride) {
-  // groups of `width` threads share a row
-  const int width = (Kp <= 256) ? 32 : (int)blockDim.x;
-  const int groups = blockDim.x / width, g = threadIdx.x / width, t = threadIdx.x % width;
-  __shared__ unsigned long long red[32];
-  __shared__ int row_e[8];
-  for (long long r0 = (long long)blockIdx.x * groups; r0 < rows; r0 += (long long)gridDim.x * groups) {
-    const long long r = r0 + g;
-    const bool live = r < rows;
-    const double* x = in + (live ? r : 0) * ld;
-    unsigned long long mx = 0;
-    if (live)
-      for (long long k = t; k < K; k += width) mx = max(mx, abs_bits(x[k]));
-    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (width == 32) {
-      if (t == 0) red[g] = mx;
-    } else if ((threadIdx.x & 31) == 0) {
-      red[threadIdx.x >> 5] = mx;
-    }
-    __syncthreads();
-    if (t == 0 && live) {
-      unsigned long long m = red[g];
-      if (width != 32)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
-      int e = 0;
-      if (m >= 0x7ff0000000000000ull) {
-        e = kNonFinite;
-      } else if (m != 0) {
-        int E;
-        frexp(__longlong_as_double((long long)m), &E);  // max |x| = f 2^E, f in [1/2, 1)
-        e = E + 1;                                      // max |x| < 2^(e - 1)
-      }
-      row_e[g] = e;
-      exps[r] = e;
-    }
-    __syncthreads();
-    if (live) {
-      const int e = row_e[g];
-      for (long long k = t; k < Kp; k += width) {
-        long long q = 0;
-        if (e != kNonFinite && k < K) q = scaled_int(x[k], L - e);  // |q| <= 2^41
-        // balanced base-2^7 digits from the least significant end
-        __nv_bfloat16 dig[NSLICE];
+// Digit split in three passes over runs of 8 values of one row (any row
+// length keeps the whole GPU busy):
+//  1. the largest high word of |x| per row (exponent and top mantissa bits)
+//     by atomicMax into exps (as unsigned), zeroed before;
+//  2. that word -> the row exponent e (max |x| < 2^(e - 1)), in place;
+//  3. the balanced digits of rint(x 2^(42 - e)) in integer arithmetic,
+//     16-byte stores per plane.
+// A row whose largest |x| is below 2^-1054 (a subnormal with no bit in the
+// high word) counts as zero.
+__global__ void oz_rowmax_kernel(unsigned* __restrict__ hmax, const double* __restrict__ in,
+                                 long long rows, long long K, long long ld, long long Kp) {
+  const long long runs = Kp / 8, total = rows * runs;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+    const double* x = in + r * ld + k0;
+    unsigned m = 0;
 #pragma unroll
-        for (int s = NSLICE - 1; s >= 1; --s) {
-          const long long d = ((q + 64) & 127) - 64;
-          q = (q - d) >> BETA;
-          dig[s] = __float2bfloat16_rn(ldexpf((float)d, -BETA * s));
-        }
-        dig[0] = __float2bfloat16_rn((float)q);
-#pragma unroll
-        for (int s = 0; s < NSLICE; ++s) out[(long long)s * plane_stride + r * Kp + k] = dig[s];
-      }
+    for (int j = 0; j < 8; ++j)
+      if (k0 + j < K) m = max(m, (unsigned)(abs_bits(x[j]) >> 32));
+    // one atomic per warp when its 32 runs share a row (long rows), else per run
+    const unsigned active = __activemask();
+    const long long r0 = __shfl_sync(active, r, __ffs(active) - 1);
+    if (active == 0xffffffffu && __all_sync(active, r == r0)) {
+      for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(active, m, off));
+      if ((threadIdx.x & 31) == 0 && m) atomicMax(hmax + r, m);
+    } else if (m) {
+      atomicMax(hmax + r, m);
     }
-    __syncthreads();
+  }
+}
+
+__global__ void oz_exponent_kernel(int32_t* __restrict__ exps, long long rows) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+       r += (long long)gridDim.x * blockDim.x) {
+    const unsigned h = (unsigned)exps[r];
+    int e = 0;
+    if (h >= 0x7ff00000u) {
+      e = kNonFinite;
+    } else if (h >= 0x00100000u) {
+      e = (int)(h >> 20) - 1021;  // normal: max |x| in [2^(E-1023), 2^(E-1022))
+    } else if (h != 0) {
+      e = (31 - __clz(h)) + 32 - 1072;  // subnormal: leading mantissa bit
+    }
+    exps[r] = e;
+  }
+}
+
+__global__ void oz_digits_kernel(__nv_bfloat16* __restrict__ out, const int32_t* __restrict__ exps,
+                                 const double* __restrict__ in, long long rows, long long K,
+                                 long long ld, long long Kp, long long plane_stride) {
+  const long long runs = Kp / 8, total = rows * runs;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+    const int e = exps[r];
+    const double* x = in + r * ld + k0;
+    __align__(16) __nv_bfloat16 dig[NSLICE][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      long long q = 0;
+      if (e != kNonFinite && k0 + j < K) q = scaled_int(x[j], L - e);  // |q| <= 2^41
+#pragma unroll
+      for (int s = NSLICE - 1; s >= 1; --s) {
+        const long long d = ((q + 64) & 127) - 64;
+        q = (q - d) >> BETA;
+        dig[s][j] = __float2bfloat16_rn(ldexpf((float)d, -BETA * s));
+      }
+      dig[0][j] = __float2bfloat16_rn((float)q);
+    }
+#pragma unroll
+    for (int s = 0; s < NSLICE; ++s)
+      *reinterpret_cast<uint4*>(out + (long long)s * plane_stride + r * Kp + k0) =
+          *reinterpret_cast<const uint4*>(dig[s]);
   }
 }
 
@@ -398,10 +413,13 @@ void split(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const double* i
   if (rows <= 0) return;
   const int64_t Kp = padded_k(K);
   if (plane_stride <= 0) plane_stride = rows * Kp;
-  const int per = (Kp <= 256) ? 8 : 1;  // rows per block: a warp each for short rows
-  const int g = (int)std::min<int64_t>((rows + per - 1) / per, 152 * 8);
-  oz_split_kernel<<<g, 256, 0, s>>>(planes, exps, in, rows, K, ld, Kp, plane_stride);
-  count_launch();
+  const int64_t runs = rows * (Kp / 8);
+  const int g = (int)std::min<int64_t>((runs + 255) / 256, 152 * 16);
+  ASCC_CUDA(cudaMemsetAsync(exps, 0, sizeof(int32_t) * (size_t)rows, s));
+  oz_rowmax_kernel<<<g, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, rows, K, ld, Kp);
+  oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
+  oz_digits_kernel<<<g, 256, 0, s>>>(planes, exps, in, rows, K, ld, Kp, plane_stride);
+  count_launch(3);
   check_launch("oz_split");
 }
 

@@ -25,30 +25,51 @@ namespace ascc {
 namespace tc {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, NTHREADS = 128;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TMEM_COLS = 256;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-static_assert(BM * (BN + 1) * 4 <= STAGES * STAGE_BYTES, "the epilogue tile reuses the ring");
+constexpr int BM = 128, BN = 256, BK = 64, NTHREADS = 128;
+constexpr int TK = 32;                           // K tile of the ring (64-byte swizzle rows)
+constexpr int EPI_BYTES = BM * (BN + 1) * 4;     // FP32 epilogue tile (odd pitch)
 
-struct Segs {
-  int n;
-  int a[6];
-  int b[6];
+// Ring geometry per split level: every stage holds all LEVEL planes of A
+// (128 x 32) and of B (256 x 32) for one K tile, so the plane products of a
+// K tile reuse the loaded tiles.
+template <int LEVEL>
+struct Ring {
+  static constexpr int A_TILE = BM * TK * 2;     // 8 KB
+  static constexpr int B_TILE = BN * TK * 2;     // 16 KB
+  static constexpr int A_BYTES = LEVEL * A_TILE;
+  static constexpr int STAGE_BYTES = LEVEL * (A_TILE + B_TILE);
+  static constexpr int STAGES = LEVEL == 3 ? 3 : LEVEL == 2 ? 4 : 6;
+  static constexpr int RING_BYTES = STAGES * STAGE_BYTES;
+  static constexpr int BODY = RING_BYTES > EPI_BYTES ? RING_BYTES : EPI_BYTES;
+  static constexpr int SMEM_BYTES = BODY + 1024 /*align*/ + 256 /*barriers*/;
+  // plane products (u of A, w of B), the small planes first; the leading
+  // product (0, 0) has a TMEM accumulator of its own and the cross products
+  // share a second one, so that the large running sum is rounded once per K
+  // step (the tensor core's FP32 accumulation truncates)
+  static constexpr int NPROD = LEVEL == 1 ? 1 : LEVEL == 2 ? 3 : 6;
+  static constexpr int NACC = LEVEL == 1 ? 1 : 2;
+  static constexpr int TMEM_COLS = NACC == 1 ? 256 : 512;
+  __host__ __device__ static constexpr int pa(int i) {
+    return LEVEL == 1 ? 0 : LEVEL == 2 ? (i == 0 ? 1 : 0) : (i == 0 ? 2 : i == 1 || i == 3 ? 1 : 0);
+  }
+  __host__ __device__ static constexpr int pb(int i) {
+    return LEVEL == 1 ? 0 : LEVEL == 2 ? (i == 1 ? 1 : 0) : (i == 2 ? 2 : i == 1 || i == 4 ? 1 : 0);
+  }
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 };
 
 using namespace ptx;
 
+template <int LEVEL>
 __global__ void __launch_bounds__(NTHREADS, 1)
-gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ CUtensorMap a1,
-               const __grid_constant__ CUtensorMap a2, const __grid_constant__ CUtensorMap b0,
-               const __grid_constant__ CUtensorMap b1, const __grid_constant__ CUtensorMap b2,
-               Segs segs, int M, int N, int num_kt, int kt_chunk, double alpha, double beta,
+gemm_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+               int M, int N, int num_kt, int kt_chunk, double alpha, double beta,
                double* __restrict__ C, long long ldc, float* __restrict__ ws, int* err) {
+  using G = Ring<LEVEL>;
+  constexpr int STAGES = G::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = (uint64_t*)(smem + G::BODY);
   uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 2);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -68,7 +89,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_holder)),
-                 "r"(TMEM_COLS)
+                 "r"(G::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -76,15 +97,13 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_holder;
-  // split K: this CTA covers k-tiles [kt0, kt0 + nkt) of every segment
+  // split K: this CTA covers the K tiles [kt0, kt0 + nkt)
   const int kt0 = blockIdx.z * kt_chunk;
   const int nkt = max(0, min(kt_chunk, num_kt - kt0));
-  const int total = segs.n * nkt;
+  const int total = nkt;
 
   if (warp == 0 && lane == 0) {
-    // TMA producer
-    const CUtensorMap* am[3] = {&a0, &a1, &a2};
-    const CUtensorMap* bm[3] = {&b0, &b1, &b2};
+    // TMA producer: all planes of A and B of one K tile per stage
     for (int it = 0; it < total; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (uint32_t)((it / STAGES) & 1);
@@ -93,14 +112,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
         break;
       }
       if (*(volatile int*)&abort_flag) break;
-      const int seg = it / nkt, kt = kt0 + it % nkt;
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-      tma_load_2d(sa, am[segs.a[seg]], full0 + 8 * s, kt * BK, m0);
-      tma_load_2d(sa + A_BYTES, bm[segs.b[seg]], full0 + 8 * s, kt * BK, n0);
+      const int kx = (kt0 + it) * TK;
+      const uint32_t sa = smem_u32(smem + s * G::STAGE_BYTES);
+      mbar_expect_tx(full0 + 8 * s, G::STAGE_BYTES);
+      tma_load_3d(sa, &amap, full0 + 8 * s, kx, m0, 0);
+      tma_load_3d(sa + G::A_BYTES, &bmap, full0 + 8 * s, kx, n0, 0);
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
+    // MMA issuer: every plane product of the K tile from the same stage
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
     for (int it = 0; it < total; ++it) {
       const int s = it % STAGES;
@@ -110,12 +129,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t sa = smem_u32(smem + s * G::STAGE_BYTES), sb = sa + G::A_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t ad = sw128_desc(sa + kk * 32);
-        const uint64_t bd = sw128_desc(sa + A_BYTES + kk * 32);
-        mma_bf16(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+      for (int p = 0; p < G::NPROD; ++p) {
+        // accumulator 0: the leading product; 1: the cross products (the
+        // first of them is p = 0)
+        const bool lead = G::pa(p) == 0 && G::pb(p) == 0;
+        const uint32_t acc = (G::NACC == 2 && !lead) ? 256u : 0u;
+        const bool first = it == 0 && (lead || p == 0);
+#pragma unroll
+        for (int kk = 0; kk < TK / 16; ++kk) {
+          const uint64_t ad = sw64_desc(sa + G::pa(p) * G::A_TILE + kk * 32);
+          const uint64_t bd = sw64_desc(sb + G::pb(p) * G::B_TILE + kk * 32);
+          mma_bf16(tmem + acc, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+        }
       }
       mma_commit(empty0 + 8 * s);
     }
@@ -137,8 +164,16 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
       for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t r[16];
         tmem_ld16(taddr + c0, r);
+        if (G::NACC == 2) {
+          uint32_t q[16];
+          tmem_ld16(taddr + 256 + c0, q);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) tile[lrow * PITCH + c0 + j] = __uint_as_float(r[j]);
+          for (int j = 0; j < 16; ++j)
+            tile[lrow * PITCH + c0 + j] = __uint_as_float(r[j]) + __uint_as_float(q[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tile[lrow * PITCH + c0 + j] = __uint_as_float(r[j]);
+        }
       }
     }
     __syncthreads();
@@ -164,7 +199,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap a0, const __grid_constant__ C
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_COLS)
+                 "r"(G::TMEM_COLS)
                  : "memory");
   }
 }
@@ -223,14 +258,17 @@ __global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double*
   }
 }
 
-CUtensorMap make_map(const __nv_bfloat16* base, int64_t rows, int64_t Kp, int box_rows) {
+// 3-D map over the planes [level][rows][Kp] (plane stride in elements): one
+// box brings all planes of a 32-wide K tile, 64-byte swizzle.
+CUtensorMap make_planes_map(const __nv_bfloat16* base, int64_t rows, int64_t Kp,
+                            int64_t plane_stride, int level, int box_rows) {
   CUtensorMap m;
-  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(Kp * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)level};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(plane_stride * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, (cuuint32_t)level};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(ASCC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return m;
@@ -287,35 +325,37 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   static std::once_flag attr_once;
   cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [&] {
-    attr_err = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    SMEM_BYTES);
+    attr_err = cudaFuncSetAttribute(gemm_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Ring<1>::SMEM_BYTES);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(gemm_tc_kernel<2>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Ring<2>::SMEM_BYTES);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(gemm_tc_kernel<3>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Ring<3>::SMEM_BYTES);
   });
   ASCC_CUDA(attr_err);
   const int64_t Kp = padded_k(K);
-  CUtensorMap am[3], bm[3];
-  for (int u = 0; u < 3; ++u) {
-    const int uu = u < level ? u : 0;
-    am[u] = make_map(A + (int64_t)uu * M * Kp, M, Kp, BM);
-    bm[u] = make_map(B + (int64_t)uu * (b_plane_stride > 0 ? b_plane_stride : N * Kp), N, Kp, BN);
-  }
-  // products with the small planes first (accumulated before the large ones)
-  Segs sg;
-  if (level == 1) {
-    sg = {1, {0}, {0}};
-  } else if (level == 2) {
-    sg = {3, {1, 0, 0}, {0, 1, 0}};
-  } else {
-    sg = {6, {2, 1, 0, 1, 0, 0}, {0, 1, 2, 0, 1, 0}};
-  }
+  const CUtensorMap am = make_planes_map(A, M, Kp, M * Kp, level, BM);
+  const CUtensorMap bm =
+      make_planes_map(B, N, Kp, b_plane_stride > 0 ? b_plane_stride : N * Kp, level, BN);
   count_flops(2.0 * (double)M * N * K);
-  const int num_kt = (int)(Kp / BK);
+  const int num_kt = (int)(Kp / TK);
   const int kt_chunk = (num_kt + splitk - 1) / splitk;
   dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splitk);
   ASCC_REQUIRE(grid.y <= 65535, "gemm_split: N too large");
-  gemm_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(am[0], am[1], am[2], bm[0], bm[1], bm[2], sg,
-                                                    (int)M, (int)N, num_kt, kt_chunk, alpha, beta,
-                                                    C, (long long)ldc, splitk > 1 ? ws : nullptr,
-                                                    err);
+  float* w = splitk > 1 ? ws : nullptr;
+  if (level == 1)
+    gemm_tc_kernel<1><<<grid, NTHREADS, Ring<1>::SMEM_BYTES, s>>>(
+        am, bm, (int)M, (int)N, num_kt, kt_chunk, alpha, beta, C, (long long)ldc, w, err);
+  else if (level == 2)
+    gemm_tc_kernel<2><<<grid, NTHREADS, Ring<2>::SMEM_BYTES, s>>>(
+        am, bm, (int)M, (int)N, num_kt, kt_chunk, alpha, beta, C, (long long)ldc, w, err);
+  else
+    gemm_tc_kernel<3><<<grid, NTHREADS, Ring<3>::SMEM_BYTES, s>>>(
+        am, bm, (int)M, (int)N, num_kt, kt_chunk, alpha, beta, C, (long long)ldc, w, err);
   count_launch();
   check_launch("gemm_tc");
   if (splitk > 1) {
