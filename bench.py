@@ -256,6 +256,13 @@ def run_server_workload(args, kind):
         a[2] += 1
         a[3] += int(x["status"] == 0)
     lat = np.array([b - a for a, b, _, _ in per_req.values()])
+    failures = []
+    for x in res:
+        if x["status"] != 0 and len(failures) < 24:
+            r = reqs[sub[x["request_id"]]]
+            st = r["states"][x["state_index"]] if x["state_index"] >= 0 else "request"
+            failures.append({"o": r["o"], "v": r["v"], "seed": r["seed"], "state": st,
+                             "status": int(x["status"]), "iterations": int(x["iterations"])})
     solves = sum(v[2] for v in per_req.values())
     ok = sum(v[3] for v in per_req.values())
     line = {
@@ -270,6 +277,7 @@ def run_server_workload(args, kind):
                    "arrival_rate_per_s": args.rate if kind == "serve" else None},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "requests": len(reqs), "states": solves, "converged_states": ok, "wall_s": wall,
+        "not_converged": failures,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -484,7 +484,7 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
 // hand-over and whenever the corrected iteration converges, so that the
 // accepted amplitudes satisfy the FP64 equations.
 int State::level_for_phase() const {
-  if (opt_.precision == ASCC_FP64_TC) return 4;
+  if (opt_.precision == ASCC_FP64_TC || fallback_) return 4;
   if (opt_.precision != ASCC_MIXED_BF16) return 0;
   return polish_ ? 3 : 2;
 }
@@ -910,6 +910,8 @@ void State::reset() {
   polish_ = false;
   need_refresh_ = false;
   have_corr_ = false;
+  fallback_ = false;
+  polish_its_ = 0;
   have_prev_ = false;
   done_ = false;
   status_ = ASCC_ERR_NOT_CONVERGED;
@@ -985,6 +987,14 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
       status_ = ASCC_OK;
       done_ = true;
       break;
+    }
+    if (lev == 3 && ++polish_its_ >= 30 + opt_.diis_dim) {
+      // the corrected iteration stalls (slowly converging states): continue with
+      // FP64-class residuals in every step, with a fresh DIIS history
+      fallback_ = true;
+      have_prev_ = false;
+      slots_.clear();
+      next_slot_ = 0;
     }
     if (it >= opt_.max_iter) {
       status_ = ASCC_ERR_NOT_CONVERGED;

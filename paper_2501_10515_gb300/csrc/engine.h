@@ -164,6 +164,10 @@ class State {
   OT t_, r_, hist_t_, hist_e_, scal_, work_, coef_, eps_eff_;
   DevBuf err_;           // int: device-side timeout codes of the tensor-core GEMM
   bool polish_ = false, need_refresh_ = false, have_corr_ = false;
+  // mixed precision: the defect-corrected polishing gave way to FP64-class
+  // residuals throughout (it stalled); polish_its_ counts its iterations
+  bool fallback_ = false;
+  int polish_its_ = 0;
   int fp64_evals_ = 0;
   OT corr_;  // FP64-minus-polishing residual correction (mixed precision)
   double tc_min_flops_ = 4e7;  // contractions below this stay FP64 (ASCC_TC_MIN_FLOPS overrides)
