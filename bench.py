@@ -476,10 +476,13 @@ def main():
                      "frac": achieved / peak, "traffic": None,
                      "kernel": {"fp64": "gemm_f64_kernel", "mixed": "gemm_tc_kernel",
                                 "fp64tc": "gemm_oz_kernel"}[args.precision] +
-                               " (particle-particle ladder: its operand splits and GEMMs)",
+                               " (the particle-particle ladder's pair-row GEMM, M = o(o+1)/2, "
+                               "N = K = v^2, with its split-K reduction)",
                      "peak_source": unit_note,
-                     "achieved_note": "algorithmic flops of the ladder (one product per "
-                                      "multiply-add) over its CUDA-event time",
+                     "achieved_note": "algorithmic flops of that launch, 2 o(o+1)/2 v^4 (one "
+                                      "product per multiply-add), over its CUDA-event time on "
+                                      "the state's stream, averaged over the launches of the "
+                                      "timed solves; mma_* count every BF16 plane product",
                      "mma_tflops": mma_rate,
                      "mma_frac": mma_rate / peak},
         "residual_tflops": tflops,

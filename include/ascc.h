@@ -94,6 +94,13 @@ typedef struct {
   int32_t polish_iter; /* reserved                                             */
   double polish_tol;   /* mixed precision: max |R| at which the 3-product phase */
                        /*   hands over to the FP64-corrected polishing phase     */
+  int32_t ladder_stream; /* the bare (xc|bd) block of the particle-particle ladder:
+                            1 = rebuilt in ~1 GB x-chunks inside every residual
+                            (no stored block; about twice the ladder work),
+                            -1 = stored once per molecule, 0 = stored unless its
+                            planes would take more than 60 % of the free device
+                            memory when the state is created                    */
+  int32_t reserved2;
 } ascc_options;
 
 typedef struct {
@@ -180,10 +187,12 @@ ascc_status ascc_iterate(ascc_ctx* ctx, int32_t max_steps, ascc_result* res);
 
 /* Profiling of the dense particle-particle ladder contraction: when enabled,
  * each launch is bracketed by CUDA events on the context's stream.
- * ascc_get_profile reports the summed event time (ms), the number of
- * launches and their flops: 2 v^2 (o^3 v + o(o+1)/2 v^2) each (the dense
- * 2 o^2 v^2 (o+v) v with the pair symmetry of t2 used for the virtual rows),
- * and the same times the plane products the tensor cores execute. */
+ * ascc_get_profile reports the summed event time (ms) of the dominant
+ * ladder launch (the GEMM of the o(o+1)/2 pair rows against the v^2 virtual
+ * rows of (xc|bd), with its split-K reduction; the whole ladder when the
+ * block is streamed), the number of such launches and their flops:
+ * 2 (o(o+1)/2) v^4 each (2 v^2 (o^3 v + o(o+1)/2 v^2) when streamed), and the
+ * same times the plane products the tensor cores execute. */
 typedef struct {
   double ladder_ms;
   double ladder_flops;

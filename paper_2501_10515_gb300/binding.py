@@ -29,7 +29,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("linearize", C.c_int32), ("triples", C.c_int32),
                 ("pl_hole", C.c_int32), ("pl_particle", C.c_int32), ("r_tol", C.c_double),
                 ("e_tol", C.c_double), ("max_iter", C.c_int32), ("diis_dim", C.c_int32),
-                ("diis_start", C.c_int32), ("polish_iter", C.c_int32), ("polish_tol", C.c_double)]
+                ("diis_start", C.c_int32), ("polish_iter", C.c_int32), ("polish_tol", C.c_double),
+                ("ladder_stream", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class Result(C.Structure):

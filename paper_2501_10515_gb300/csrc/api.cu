@@ -64,6 +64,7 @@ Options to_options(const ascc_options* o) {
   r.diis_start = o->diis_start;
   r.polish_iter = o->polish_iter;
   r.polish_tol = o->polish_tol;
+  r.ladder_stream = o->ladder_stream;
   return r;
 }
 
@@ -134,6 +135,8 @@ ascc_status ascc_default_options(ascc_options* opt) {
   opt->diis_start = 3;
   opt->polish_iter = 50;
   opt->polish_tol = 1e-5;
+  opt->ladder_stream = 0;
+  opt->reserved2 = 0;
   return ASCC_OK;
 }
 
@@ -408,9 +411,15 @@ size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux, const ascc_optio
   double mol = 8.0 * (P * n * n + n * n + P * V * V + P * n * V);
   // ladder blocks: FP64 (+ its build temporary), or the BF16 split planes
   // (mixed) and the six digit planes (mixed, FP64_TC) with ~2 GB of build chunks
-  if (!digits) mol += 8.0 * n * V * V * V * 2.0;
-  if (mixed) mol += 2.0 * 3.0 * n * V * kp;
-  if (digits) mol += 2.0 * 6.0 * n * V * kq + 4.0 * n * V + 2.2e9;
+  const bool stream = opt && opt->ladder_stream == 1;
+  if (stream) {
+    // rebuilt per residual: one ~1 GB FP64 chunk, its permutation temporary and planes
+    mol += 3.5 * (double)(1 << 30);
+  } else {
+    if (!digits) mol += 8.0 * n * V * V * V * 2.0;
+    if (mixed) mol += 2.0 * 3.0 * n * V * kp;
+    if (digits) mol += 2.0 * 6.0 * n * V * kq + 4.0 * n * V + 2.2e9;
+  }
   const double o2v2 = O * O * V * V, namp = O * V + o2v2;
   double state = 8.0 * (namp * (2.0 * m + 4.0) + P * n * n * 1.2 + 24.0 * o2v2 +
                         O * O * n * n * 3.0 + O * O * n * V * 4.0);

@@ -467,7 +467,28 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
     ASCC_CUDA(cudaStreamSynchronize(s));
   }
   ASCC_CUDA(cudaStreamSynchronize(mol_->stream));
-  if (opt_.precision == ASCC_MIXED_BF16) {
+  if (const char* env = std::getenv("ASCC_LADDER_CHUNK_MB"))
+    stream_chunk_bytes_ = std::max<int64_t>(1, std::atoll(env)) << 20;
+  {
+    // store the (xc|bd) blocks once per molecule, or rebuild chunks per residual
+    const double rows = (double)n_ * v_, K = (double)v_ * v_;
+    const double kp = std::ceil(K / 64.0) * 64.0, kq = std::ceil(K / 32.0) * 32.0;
+    double need = 0.0;
+    const bool have = mol_->Gext.buf.bytes() || mol_->Gext_bf16.bytes() || mol_->Gext_oz.bytes();
+    if (opt_.precision == ASCC_MIXED_BF16) need = rows * (6.0 * kp + 12.0 * kq);
+    else if (opt_.precision == ASCC_FP64_TC) need = rows * 12.0 * kq;
+    else need = rows * 16.0 * K;
+    if (opt_.ladder_stream == 1) {
+      stream_ladder_ = true;
+    } else if (opt_.ladder_stream == 0 && !have) {
+      size_t freeb = 0, totalb = 0;
+      ASCC_CUDA(cudaMemGetInfo(&freeb, &totalb));
+      stream_ladder_ = need > 0.6 * (double)freeb;
+    }
+  }
+  if (stream_ladder_) {
+    // nothing stored: ladder_streamed() rebuilds the block in x-chunks
+  } else if (opt_.precision == ASCC_MIXED_BF16) {
     mol_->ensure_bf16_ladder();
     mol_->ensure_oz_ladder();  // FP64-class polishing evaluations
   } else if (opt_.precision == ASCC_FP64_TC) {
@@ -620,18 +641,28 @@ void State::ladder(const T& t2, const T& r2) {
   Molecule& M = *mol_;
   const int64_t vv = (int64_t)v * v;
   // Y[i][j][x][b] = sum_cd t[i][j][c][d] (xc|bd)
+  // profiling brackets the dominant launch: the virtual-row GEMM (kernel and
+  // its split-K reduction), or the whole streamed ladder
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  if (profile_) {
+  auto prof_begin = [&]() {
+    if (!profile_) return;
     ASCC_CUDA(cudaEventCreate(&ev0));
     ASCC_CUDA(cudaEventCreate(&ev1));
     ASCC_CUDA(cudaEventRecord(ev0, s_));
-  }
+  };
+  auto prof_end = [&]() {
+    if (profile_) ASCC_CUDA(cudaEventRecord(ev1, s_));
+  };
   // (xc|bd) = (bd|xc) and t_ji^dc = t_ij^cd give Y_ji^{ab} = Y_ij^{ba} for the
   // virtual rows x = o+a: those come from the o(o+1)/2 pairs i <= j only; the
   // occupied rows x = k need every pair.
   const int64_t npair = (int64_t)o * (o + 1) / 2, ovr = (int64_t)o * v, vvr = vv;
   k::gather_pairs(s_, tpair_.p(), t2.p, o, vv);
-  if (es_.level() == 4) {
+  if (stream_ladder_) {
+    prof_begin();
+    ladder_streamed(t2);
+    prof_end();
+  } else if (es_.level() == 4) {
     const int64_t K = vv, Kq = oz::padded_k(K), rows = (int64_t)n * v;
     const __nv_bfloat16* G = M.Gext_oz.as<__nv_bfloat16>();
     const int32_t* eG = M.Gext_oz_exp.as<int32_t>();
@@ -646,8 +677,10 @@ void State::ladder(const T& t2, const T& r2) {
     // virtual rows: pairs i <= j
     oz::split(s_, pa, ea, tpair_.p(), npair, K, K);
     ws = static_cast<long long*>(es_.scratch(2, oz::ws_bytes(npair, vvr)));
+    prof_begin();
     oz::gemm(s_, npair, vvr, K, 1.0, pa, ea, 0, G + ovr * Kq, eG + ovr, rows * Kq, 0.0, Yvv_.p(),
              vvr, ws, err_.as<int>(), oz::splitk_for(npair, vvr, K));
+    prof_end();
   } else if (es_.level() > 0) {
     const int lev = es_.level();
     const int64_t K = vv, Kp = tc::padded_k(K), rows = (int64_t)n * v;
@@ -668,23 +701,28 @@ void State::ladder(const T& t2, const T& r2) {
     z = tc::splitk_for(npair, vvr, K);
     ws = z > 1 ? static_cast<float*>(es_.scratch(2, sizeof(float) * (size_t)(z * npair * vvr)))
                : nullptr;
+    prof_begin();
     tc::gemm_split(s_, npair, vvr, K, lev, 1.0, pa, G + ovr * Kp, 0.0, Yvv_.p(), vvr,
                    err_.as<int>(), z, ws, rows * Kp);
+    prof_end();
   } else {
     const double* G = M.Gext.p();
     k::gemm_f64(s_, false, true, (int64_t)o * o, ovr, vv, 1.0, t2.p, vv, 0, G, vv, 0, 0.0,
                 Yov_.p(), ovr, 0, 1);
+    prof_begin();
     k::gemm_f64(s_, false, true, npair, vvr, vv, 1.0, tpair_.p(), vv, 0, G + ovr * vv, vv,
                 0, 0.0, Yvv_.p(), vvr, 0, 1);
+    prof_end();
   }
   // Y[i][j][k][b] = Yov[ij][k b];  Y[i][j][o+a][b] from the pair products
   box_copy(s_, Y_.p(), {(int64_t)n * v, 1}, Yov_.p(), {ovr, 1}, {(int64_t)o * o, ovr});
   k::scatter_pairs(s_, Y_.p(), Yvv_.p(), o, v, n);
   if (profile_) {
-    ASCC_CUDA(cudaEventRecord(ev1, s_));
     events_.push_back({ev0, ev1});
     ladder_launches_ += 1;
-    const double fl = 2.0 * (double)vv * ((double)o * o * o * v + (double)npair * vv);
+    const double fl = stream_ladder_
+                          ? 2.0 * (double)vv * ((double)o * o * o * v + (double)npair * vv)
+                          : 2.0 * (double)npair * vvr * vv;
     ladder_flops_ += fl;
     ladder_mma_flops_ += fl * (es_.level() == 4   ? oz::products()
                                : es_.level() > 0 ? tc::products_for(es_.level())
@@ -756,6 +794,89 @@ void State::ladder(const T& t2, const T& r2) {
   } else {
     k::gemm_f64(s_, false, false, v, v, nc, 1.0, LamV, nc, 0, Z1C_.p(), v, (int64_t)nc * v, 1.0,
                 r2.p, v, vv, oo);
+  }
+}
+
+// The ladder GEMMs with the bare block rebuilt chunk by chunk: for x in a
+// chunk of orbitals, (xc|bd) = sum_P B[P][x][o+c] B[P][o+b][o+d] is built with
+// FP64-class contractions (6 products for the 3-product phase), split for the
+// state's precision and multiplied into the Yov (occupied x, all pairs) or Yvv
+// (virtual x, pairs i <= j) columns of that chunk.  Nothing of size n v^3 is
+// kept between calls.
+void State::ladder_streamed(const T& t2) {
+  const int o = o_, v = v_, n = n_, P = naux_;
+  Molecule& M = *mol_;
+  const int lev = es_.level();
+  const int64_t vv = (int64_t)v * v, v3 = vv * v, ovr = (int64_t)o * v, vvr = vv;
+  const int64_t npair = (int64_t)o * (o + 1) / 2, oo = (int64_t)o * o;
+  int64_t xc = std::max<int64_t>(1, stream_chunk_bytes_ / (8 * v3));
+  xc = std::min<int64_t>(xc, n);
+  if (!stream_gc_.buf.bytes() || stream_gc_.t.shape[0] < xc) {
+    stream_ac_.make({P, xc, v}, s_);
+    stream_gc_.make({xc, v, v, v}, s_);
+  }
+  // the t operands (all pairs, pairs i <= j) in the state's number format, once
+  const bool digits = lev == 4;
+  const int64_t Kp = digits ? oz::padded_k(vv) : tc::padded_k(vv);
+  const int planes = digits ? oz::NSLICE : lev;
+  __nv_bfloat16 *a_occ = nullptr, *a_vir = nullptr;
+  int32_t *e_occ = nullptr, *e_vir = nullptr;
+  if (lev > 0) {
+    const size_t need = sizeof(__nv_bfloat16) * (size_t)(planes * (oo + npair) * Kp);
+    if (stream_a_.bytes() < need) stream_a_.alloc(need, s_);
+    a_occ = stream_a_.as<__nv_bfloat16>();
+    a_vir = a_occ + (int64_t)planes * oo * Kp;
+    if (digits) {
+      if (stream_ae_.bytes() < sizeof(int32_t) * (size_t)(oo + npair))
+        stream_ae_.alloc(sizeof(int32_t) * (size_t)(oo + npair), s_);
+      e_occ = stream_ae_.as<int32_t>();
+      e_vir = e_occ + oo;
+      oz::split(s_, a_occ, e_occ, t2.p, oo, vv, vv);
+      oz::split(s_, a_vir, e_vir, tpair_.p(), npair, vv, vv);
+    } else {
+      tc::split_bf16(s_, a_occ, t2.p, oo, vv, vv, lev);
+      tc::split_bf16(s_, a_vir, tpair_.p(), npair, vv, vv, lev);
+    }
+  }
+  const int build = lev == 2 ? 3 : 4;
+  for (int g = 0; g < 2; ++g) {
+    const int64_t xbeg = g == 0 ? 0 : o, xend = g == 0 ? o : n;
+    const int64_t rows_a = g == 0 ? oo : npair, ldc = g == 0 ? ovr : vvr;
+    for (int64_t x0 = xbeg; x0 < xend; x0 += xc) {
+      const int64_t nx = std::min<int64_t>(xc, xend - x0), rows = nx * v;
+      box_copy(s_, stream_ac_.p(), {nx * v, v, 1}, M.Bnv.p() + x0 * v, {(int64_t)n * v, v, 1},
+               {P, nx, v});
+      es_.set_split(build, err_.as<int>(), 0.0);
+      es_("Pxc,Pbd->xbcd", 1.0, T(stream_ac_.p(), {P, nx, v}), M.Bvv.t, 0.0,
+          T(stream_gc_.p(), {nx, v, v, v}));
+      es_.set_split(lev, err_.as<int>(), tc_min_flops_);
+      double* C = (g == 0 ? Yov_.p() : Yvv_.p()) + (x0 - xbeg) * v;
+      if (lev == 0) {
+        k::gemm_f64(s_, false, true, rows_a, rows, vv, 1.0, g == 0 ? t2.p : tpair_.p(), vv, 0,
+                    stream_gc_.p(), vv, 0, 0.0, C, ldc, 0, 1);
+        continue;
+      }
+      const size_t bneed = sizeof(__nv_bfloat16) * (size_t)(planes * rows * Kp);
+      if (stream_b_.bytes() < bneed) stream_b_.alloc(bneed, s_);
+      auto* bp = stream_b_.as<__nv_bfloat16>();
+      if (digits) {
+        if (stream_be_.bytes() < sizeof(int32_t) * (size_t)rows)
+          stream_be_.alloc(sizeof(int32_t) * (size_t)rows, s_);
+        oz::split(s_, bp, stream_be_.as<int32_t>(), stream_gc_.p(), rows, vv, vv);
+        auto* ws = static_cast<long long*>(es_.scratch(2, oz::ws_bytes(rows_a, rows)));
+        oz::gemm(s_, rows_a, rows, vv, 1.0, g == 0 ? a_occ : a_vir, g == 0 ? e_occ : e_vir, 0, bp,
+                 stream_be_.as<int32_t>(), 0, 0.0, C, ldc, ws, err_.as<int>(),
+                 oz::splitk_for(rows_a, rows, vv));
+      } else {
+        tc::split_bf16(s_, bp, stream_gc_.p(), rows, vv, vv, lev);
+        const int z = tc::splitk_for(rows_a, rows, vv);
+        float* ws = z > 1 ? static_cast<float*>(
+                                es_.scratch(2, sizeof(float) * (size_t)(z * rows_a * rows)))
+                          : nullptr;
+        tc::gemm_split(s_, rows_a, rows, vv, lev, 1.0, g == 0 ? a_occ : a_vir, bp, 0.0, C, ldc,
+                       err_.as<int>(), z, ws);
+      }
+    }
   }
 }
 
@@ -990,11 +1111,9 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     }
     if (lev == 3 && ++polish_its_ >= 30 + opt_.diis_dim) {
       // the corrected iteration stalls (slowly converging states): continue with
-      // FP64-class residuals in every step, with a fresh DIIS history
+      // FP64-class residuals in every step; the history of corrected residuals
+      // is kept (they are FP64-class up to the drift of the correction)
       fallback_ = true;
-      have_prev_ = false;
-      slots_.clear();
-      next_slot_ = 0;
     }
     if (it >= opt_.max_iter) {
       status_ = ASCC_ERR_NOT_CONVERGED;

@@ -86,6 +86,7 @@ struct Options {
   int max_iter = 200, diis_dim = 16, diis_start = 3;
   int polish_iter = 50;
   double polish_tol = 1e-5;
+  int ladder_stream = 0;  // 1: rebuild (xc|bd) chunks per residual; -1: store; 0: auto
 };
 
 // One state (ground or one-CSF excited) of a molecule.
@@ -133,6 +134,8 @@ class State {
   void build_state_integrals();
   void dress(const double* t1);
   void ladder(const T& t2, const T& r2);
+  // the ladder GEMMs against (xc|bd) chunks rebuilt in this call
+  void ladder_streamed(const T& t2);
   void quad_terms(const T& t, const T& u, const T& Z, const T& r2, double sign);
 
   std::shared_ptr<Molecule> mol_;
@@ -178,6 +181,11 @@ class State {
   OT goooo_, gooov_, goovv_, govov_, gvovo_, gvoov_, gvvoo_, Lvoov_, Lovov_;
   OT u_, m_, um_, Z_, WC_, WD_, Wq_, Fvv_, Foo_, X_, Y_, Yfull_, Z1_, tt_, Yoo_, YC_, Z1C_;
   OT tpair_, Yvv_, Yov_;  // pair-symmetric ladder operands
+  // streamed ladder: chunk buffers and the t operand's planes
+  bool stream_ladder_ = false;
+  int64_t stream_chunk_bytes_ = (int64_t)1 << 30;
+  OT stream_ac_, stream_gc_;
+  DevBuf stream_a_, stream_ae_, stream_b_, stream_be_;
 };
 
 }  // namespace ascc

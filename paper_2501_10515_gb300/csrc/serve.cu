@@ -208,6 +208,7 @@ ascc::Options options_from(const ascc_options* o) {
   r.diis_start = o->diis_start;
   r.polish_iter = o->polish_iter;
   r.polish_tol = o->polish_tol;
+  r.ladder_stream = o->ladder_stream;
   return r;
 }
 
