@@ -188,6 +188,11 @@ def run_reference(args, wl):
     return 0
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of the pair-row ladder GEMM
+# (3-product variant) per launch, from ncu at M=210 N=40000 K=8192
+# (1.3239 GB + 0.1206 GB) scaled by 40000 / 8192
+LADDER_TRAFFIC = {("c2", "mixed"): 7.05e9}
+
 DTYPES = {"fp64": "f64", "mixed": "bf16x3-split/f64",
           "fp64tc": "f64 via bf16 digit-plane tensor-core products"}
 
@@ -473,7 +478,13 @@ def main():
                 "h2d_bytes_per_step": int(eps_p.nbytes + B_p.nbytes), "d2h_bytes_per_step": 56},
         "gpu_launches": int(p1.launches - p0.launches),
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": LADDER_TRAFFIC.get((args.workload,
+                                                                            args.precision)),
+                     "traffic_note": ("DRAM bytes of one 3-product launch of this GEMM from the "
+                                      "ncu capture in profiles/ (K = 8192), scaled to K = v^2 "
+                                      "(reads and split-K partials both grow with K)"
+                                      if (args.workload, args.precision) in LADDER_TRAFFIC
+                                      else None),
                      "kernel": {"fp64": "gemm_f64_kernel", "mixed": "gemm_tc_kernel",
                                 "fp64tc": "gemm_oz_kernel"}[args.precision] +
                                " (the particle-particle ladder's pair-row GEMM, M = o(o+1)/2, "
