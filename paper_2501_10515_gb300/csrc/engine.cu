@@ -1085,14 +1085,13 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     const int it = iter_++;
     if (lev == 2) ++iter_low_;
     if (lev == 2 && std::isfinite(r_last_) && r_last_ <= opt_.polish_tol) {
-      // hand over to the polishing precision: the stored error vectors carry the
-      // coarser residual, so the DIIS history restarts; re-evaluate (with an
-      // FP64 correction) before testing convergence
+      // hand over to the polishing precision and re-evaluate (with an FP64-class
+      // correction) before testing convergence.  The DIIS history is kept: its
+      // error vectors carry the coarser residual but age out within diis_dim
+      // steps, and slowly converging states need the long history
       polish_ = true;
       need_refresh_ = true;
       have_prev_ = false;
-      slots_.clear();
-      next_slot_ = 0;
     }
     if (!std::isfinite(e_last_) || !std::isfinite(r_last_)) {
       status_ = ASCC_ERR_DIVERGED;
