@@ -500,10 +500,10 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
 }
 
 // Mixed precision: 3 BF16 products (16 significant bits) until max|R| reaches
-// polish_tol, then 6 products (24 bits) with an FP64 defect correction: the
-// residual is R3(t) + [R64(t0) - R3(t0)], refreshed from an FP64 evaluation at
-// hand-over and whenever the corrected iteration converges, so that the
-// accepted amplitudes satisfy the FP64 equations.
+// polish_tol, then 6 products (24 bits) with a defect correction: the residual
+// is R6(t) + [R64(t0) - R6(t0)] with R64 the FP64-class (digit-plane)
+// residual, refreshed at hand-over and whenever the corrected iteration
+// converges, so that the accepted amplitudes satisfy the FP64 equations.
 int State::level_for_phase() const {
   if (opt_.precision == ASCC_FP64_TC || fallback_) return 4;
   if (opt_.precision != ASCC_MIXED_BF16) return 0;
@@ -1048,10 +1048,10 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     const int lev = level_for_phase();
     bool refreshed = false;
     if (lev == 3 && need_refresh_) {
-      // FP64 polishing: the FP64 residual and the 6-product residual at the
-      // same amplitudes; their difference corrects the following iterations
-      // (defect correction), and this step itself uses the FP64 residual.
-      // FP64-class residual: exact digit-plane products on the tensor cores
+      // polishing: the FP64-class residual (exact digit-plane products on the
+      // tensor cores) and the 6-product residual at the same amplitudes; their
+      // difference corrects the following iterations (defect correction), and
+      // this step itself uses the FP64-class residual
       es_.set_split(4, err_.as<int>(), tc_min_flops_);
       residual(t_.p(), r_.p(), scal_.p());
       es_.set_split(3, err_.as<int>(), tc_min_flops_);

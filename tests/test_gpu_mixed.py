@@ -71,7 +71,7 @@ def test_mixed_solve_matches_fp64_oracle(o, v, seed, exc, lin):
     ref = oracle_ascc.solve_state(s.eps, s.B, o, hole, part, linearize=lin, pl_hole=o - 1,
                                   pl_particle=0)
     assert ref.converged and res.status == 0
-    # the FP64-corrected polishing phase lands on the FP64 fixed point
+    # the polishing phase, corrected by FP64-class residuals, lands on the FP64 fixed point
     assert abs(res.energy - ref.energy) < 1e-8, (res.energy, ref.energy)
     assert res.iterations_low > 0 and res.fp64_evaluations >= 1
 
