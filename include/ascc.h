@@ -115,7 +115,7 @@ typedef struct {
 } ascc_result;
 
 /* Fills *opt with defaults: FP64, PLASCC, triples off, r_tol 1e-8, e_tol 1e-10,
- * max_iter 200, DIIS 16 / start 3, polish 1e-5.  Returns ASCC_OK. */
+ * max_iter 200, DIIS 16 / start 3, polish 1e-6.  Returns ASCC_OK. */
 ascc_status ascc_default_options(ascc_options* opt);
 
 /* Creates a context for one state of one molecule (Secs. II.A-II.B).

@@ -134,7 +134,7 @@ ascc_status ascc_default_options(ascc_options* opt) {
   opt->diis_dim = 16;
   opt->diis_start = 3;
   opt->polish_iter = 50;
-  opt->polish_tol = 1e-5;
+  opt->polish_tol = 1e-6;
   opt->ladder_stream = 0;
   opt->reserved2 = 0;
   return ASCC_OK;

@@ -85,7 +85,7 @@ struct Options {
   double r_tol = 1e-8, e_tol = 1e-10;
   int max_iter = 200, diis_dim = 16, diis_start = 3;
   int polish_iter = 50;
-  double polish_tol = 1e-5;
+  double polish_tol = 1e-6;
   int ladder_stream = 0;  // 1: rebuild (xc|bd) chunks per residual; -1: store; 0: auto
 };
 

@@ -74,4 +74,4 @@ def test_footprint_by_precision_and_streaming(lib):
 
 def test_default_options_keep_the_ladder_block_automatic(lib):
     opt = binding.default_options()
-    assert opt.ladder_stream == 0 and opt.polish_tol == 1e-5
+    assert opt.ladder_stream == 0 and opt.polish_tol == 1e-6
