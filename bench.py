@@ -35,11 +35,11 @@ SERVE_NOTE = ("scaled-down serving trace: o log-uniform [5,20], v log-uniform [5
               "excited states per molecule plus its ground state, Poisson arrivals")
 WORKLOADS = {
     "c2": dict(o=20, v=200, seed=0, hole=19, particle=3,
-               name="ascc-fp64 o=20 v=200 naux=660 excitation 19->3 (PLASCC)"),
+               name="ascc solve o=20 v=200 naux=660 excitation 19->3 (PLASCC), max|R| <= 1e-8"),
     "c1": dict(o=4, v=20, seed=0, hole=3, particle=0,
-               name="ascc-fp64 o=4 v=20 naux=72 excitation 3->0 (PLASCC)"),
+               name="ascc solve o=4 v=20 naux=72 excitation 3->0 (PLASCC), max|R| <= 1e-8"),
     "c3": dict(o=30, v=300, seed=0, hole=29, particle=0,
-               name="ascc-mixed o=30 v=300 naux=990 excitation 29->0 (PLASCC)"),
+               name="ascc solve o=30 v=300 naux=990 excitation 29->0 (PLASCC), max|R| <= 1e-8"),
 }
 FP64_NOMINAL_TFLOPS = 1.25
 
