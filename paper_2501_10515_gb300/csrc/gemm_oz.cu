@@ -231,16 +231,36 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     const int c = threadIdx.x % BN, col = n0 + c;
     if (col < N) {
       const int32_t b = eb[col];
-      for (int rr = threadIdx.x / BN; rr < rows; rr += RPP) {
-        const long long v = tile[rr * PITCH + c], row = m0 + rr;
-        if (gridDim.z == 1) {
-          const int32_t a = ea[row];
-          const double val = (a == kNonFinite || b == kNonFinite)
-                                 ? __longlong_as_double(0x7ff8000000000000ll)
-                                 : ldexp((double)v, a + b - (2 * BETA + UNIT));
-          double* cp = C + row * ldc + col;
-          *cp = (beta == 0.0) ? alpha * val : fma(alpha, val, beta * *cp);
-        } else {
+      if (gridDim.z == 1) {
+        // RB rows per thread at a time: their row exponents and old values of
+        // C are loaded before the first store (RB loads in flight, not one
+        // round trip to memory per row)
+        constexpr int RB = 8;
+        for (int r0 = threadIdx.x / BN; r0 < rows; r0 += RB * RPP) {
+          int32_t a[RB];
+          double old[RB];
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            const int rr = r0 + u * RPP;
+            a[u] = rr < rows ? ea[m0 + rr] : 0;
+            old[u] = (rr < rows && beta != 0.0) ? C[(long long)(m0 + rr) * ldc + col] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            const int rr = r0 + u * RPP;
+            if (rr < rows) {
+              const long long v = tile[rr * PITCH + c];
+              const double val = (a[u] == kNonFinite || b == kNonFinite)
+                                     ? __longlong_as_double(0x7ff8000000000000ll)
+                                     : ldexp((double)v, a[u] + b - (2 * BETA + UNIT));
+              C[(long long)(m0 + rr) * ldc + col] =
+                  (beta == 0.0) ? alpha * val : fma(alpha, val, beta * old[u]);
+            }
+          }
+        }
+      } else {
+        for (int rr = threadIdx.x / BN; rr < rows; rr += RPP) {
+          const long long v = tile[rr * PITCH + c], row = m0 + rr;
           atomicAdd(ws + row * N + col, (unsigned long long)v);
         }
       }

@@ -177,20 +177,38 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
       }
     }
     __syncthreads();
-    const int rows = min(BM, M - m0);
-    for (int rr = 0; rr < rows; ++rr) {
-      const long long row = m0 + rr;
-      for (int c = threadIdx.x; c < BN; c += NTHREADS) {
-        const int col = n0 + c;
-        if (col >= N) break;
-        const float a = total > 0 ? tile[rr * PITCH + c] : 0.f;
-        if (ws) {
-          // split-K partial, summed later
-          ws[((long long)blockIdx.z * M + row) * N + col] = a;
-        } else {
-          double* cp = C + row * ldc + col;
-          const double acc = (double)a;
-          *cp = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *cp);
+    const int rows = min(BM, M - m0), cols = min(BN, N - n0);
+    if (ws || beta == 0.0) {
+      // store-only: split-K partials (summed later) or alpha * tile
+      for (int rr = 0; rr < rows; ++rr) {
+        const long long row = m0 + rr;
+        for (int c = threadIdx.x; c < cols; c += NTHREADS) {
+          const int col = n0 + c;
+          const float a = total > 0 ? tile[rr * PITCH + c] : 0.f;
+          if (ws)
+            ws[((long long)blockIdx.z * M + row) * N + col] = a;
+          else
+            C[row * ldc + col] = alpha * (double)a;
+        }
+      }
+    } else {
+      // C = alpha * tile + beta * C: the old values of RB rows are loaded
+      // before the first store, so that each thread has RB loads in flight
+      // instead of one round trip to memory per row
+      constexpr int RB = 16;
+      for (int r0 = 0; r0 < rows; r0 += RB) {
+        for (int c = threadIdx.x; c < cols; c += NTHREADS) {
+          double old[RB];
+#pragma unroll
+          for (int u = 0; u < RB; ++u)
+            old[u] = (r0 + u < rows) ? C[(long long)(m0 + r0 + u) * ldc + n0 + c] : 0.0;
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            if (r0 + u < rows) {
+              const float a = total > 0 ? tile[(r0 + u) * PITCH + c] : 0.f;
+              C[(long long)(m0 + r0 + u) * ldc + n0 + c] = fma(alpha, (double)a, beta * old[u]);
+            }
+          }
         }
       }
     }
@@ -202,6 +220,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
                  "r"(G::TMEM_COLS)
                  : "memory");
   }
+}
+
+// One step of the compensated split-K sum: hi + x by Fast2Sum, its rounding
+// error into lo.
+__device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
+  const float t = hi + x;
+  lo += (fabsf(hi) >= fabsf(x)) ? (hi - t) + x : (x - t) + hi;
+  hi = t;
 }
 
 // C = alpha * sum_z ws[z] + beta * C.  The FP32 partials are summed in FP32
@@ -217,15 +243,54 @@ __global__ void splitk_reduce_kernel(double* __restrict__ C, long long ldc,
          n += (long long)gridDim.x * blockDim.x) {
       const long long idx = m * N + n;
       float hi = 0.f, lo = 0.f;
-      for (int z = 0; z < nz; ++z) {
-        const float x = ws[(long long)z * total + idx];
-        const float t = hi + x;
-        lo += (fabsf(hi) >= fabsf(x)) ? (hi - t) + x : (x - t) + hi;
-        hi = t;
-      }
+      for (int z = 0; z < nz; ++z) comp_add(hi, lo, ws[(long long)z * total + idx]);
       const double acc = (double)hi + (double)lo;
       double* c = C + m * ldc + n;
       *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *c);
+    }
+  }
+}
+
+// The same sums when N is a multiple of 4 and the partials are 16-byte
+// aligned: each thread takes four neighbouring columns with 16-byte loads and
+// keeps four K-chunks in flight.  Every element is summed in the same order as
+// above, so the results are identical.
+__global__ void splitk_reduce4_kernel(double* __restrict__ C, long long ldc,
+                                      const float* __restrict__ ws, long long M, long long N,
+                                      int nz, double alpha, double beta) {
+  const long long n4 = N / 4, total4 = M * n4;
+  const float4* __restrict__ w4 = reinterpret_cast<const float4*>(ws);
+  for (long long m = blockIdx.y; m < M; m += gridDim.y) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
+         q += (long long)gridDim.x * blockDim.x) {
+      const long long idx4 = m * n4 + q;
+      float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+      int z = 0;
+      for (; z + 4 <= nz; z += 4) {
+        float4 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = w4[(long long)(z + u) * total4 + idx4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          comp_add(hi[0], lo[0], x[u].x);
+          comp_add(hi[1], lo[1], x[u].y);
+          comp_add(hi[2], lo[2], x[u].z);
+          comp_add(hi[3], lo[3], x[u].w);
+        }
+      }
+      for (; z < nz; ++z) {
+        const float4 x = w4[(long long)z * total4 + idx4];
+        comp_add(hi[0], lo[0], x.x);
+        comp_add(hi[1], lo[1], x.y);
+        comp_add(hi[2], lo[2], x.z);
+        comp_add(hi[3], lo[3], x.w);
+      }
+      double* c = C + m * ldc + 4 * q;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const double acc = (double)hi[e] + (double)lo[e];
+        c[e] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * c[e]);
+      }
     }
   }
 }
@@ -359,10 +424,16 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   count_launch();
   check_launch("gemm_tc");
   if (splitk > 1) {
-    const unsigned gx = (unsigned)std::min<int64_t>((N + 255) / 256, 64);
     const unsigned gy = (unsigned)std::min<int64_t>(M, 65535);
-    splitk_reduce_kernel<<<dim3(gx, gy), 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk, alpha,
-                                                     beta);
+    if (N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0) {
+      const unsigned gx = (unsigned)std::min<int64_t>((N / 4 + 255) / 256, 64);
+      splitk_reduce4_kernel<<<dim3(gx, gy), 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk,
+                                                          alpha, beta);
+    } else {
+      const unsigned gx = (unsigned)std::min<int64_t>((N + 255) / 256, 64);
+      splitk_reduce_kernel<<<dim3(gx, gy), 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk,
+                                                       alpha, beta);
+    }
     count_launch();
     check_launch("splitk_reduce");
   }

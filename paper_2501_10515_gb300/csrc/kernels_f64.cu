@@ -89,12 +89,18 @@ gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
   for (int i = 0; i < 4; ++i) {
     const int64_t gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
+    // the row's four old values of C are loaded before its first store
+    double old[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      old[j] = (beta != 0.0 && gn < N) ? C[gm * ldc + gn] : 0.0;
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
-      double* c = C + gm * ldc + gn;
-      *c = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+      C[gm * ldc + gn] = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * old[j]);
     }
   }
 }
@@ -138,36 +144,47 @@ __global__ void strided_copy_kernel(double* __restrict__ out, const double* __re
 
 // Row-wise copy: the last dimension is walked by the threads (len values per
 // row, `per` rows per block pass), the outer index is decomposed once per row.
-// PLAIN (alpha = 1, beta = 0) moves the bits without FP64 arithmetic.
-template <bool PLAIN>
+// Long rows are cut into nseg segments of seglen values, so that a few long
+// rows still spread over the whole GPU.  PLAIN (alpha = 1, beta = 0) moves the
+// bits without FP64 arithmetic.  I is the type of the row-index arithmetic:
+// 32-bit whenever rows * nseg < 2^31 (the divisions are then a few times
+// cheaper), 64-bit otherwise.
+template <bool PLAIN, typename I>
 __global__ void copy_rows_kernel(double* __restrict__ out, const double* __restrict__ in,
                                  int64_t rows, int len, int per, Strides st, int64_t is_last,
-                                 int64_t os_last, double alpha, double beta) {
+                                 int64_t os_last, double alpha, double beta, int nseg,
+                                 int seglen) {
   const int sub = threadIdx.x / (blockDim.x / per), t = threadIdx.x % (blockDim.x / per);
   const int width = blockDim.x / per;
-  for (int64_t row = (int64_t)blockIdx.x * per + sub; row < rows; row += (int64_t)gridDim.x * per) {
-    int64_t rem = row, ioff = 0, ooff = 0;
+  const I units = (I)rows * (I)nseg;
+  for (I u = (I)blockIdx.x * per + sub; u < units; u += (I)gridDim.x * per) {
+    const I row = u / (I)nseg;
+    const int jb = (int)(u - row * (I)nseg) * seglen;
+    const int je = min(len, jb + seglen);
+    I rem = row;
+    int64_t ioff = 0, ooff = 0;
     for (int d = st.nd - 1; d >= 0; --d) {
-      const int64_t c = rem % st.shape[d];
-      rem /= st.shape[d];
-      ioff += c * st.istride[d];
-      ooff += c * st.ostride[d];
+      const I sh = (I)st.shape[d];
+      const I c = rem % sh;
+      rem /= sh;
+      ioff += (int64_t)c * st.istride[d];
+      ooff += (int64_t)c * st.ostride[d];
     }
     // four independent loads in flight per thread
-    for (int j0 = t; j0 < len; j0 += 4 * width) {
+    for (int j0 = jb + t; j0 < je; j0 += 4 * width) {
       double v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = j0 + u * width;
-        v[u] = (j < len) ? in[ioff + j * is_last] : 0.0;
+      for (int q = 0; q < 4; ++q) {
+        const int j = j0 + q * width;
+        v[q] = (j < je) ? in[ioff + j * is_last] : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = j0 + u * width;
-        if (j < len) {
+      for (int q = 0; q < 4; ++q) {
+        const int j = j0 + q * width;
+        if (j < je) {
           double* o = out + ooff + j * os_last;
-          if (PLAIN) *o = v[u];
-          else *o = (beta == 0.0) ? alpha * v[u] : fma(alpha, v[u], beta * *o);
+          if (PLAIN) *o = v[q];
+          else *o = (beta == 0.0) ? alpha * v[q] : fma(alpha, v[q], beta * *o);
         }
       }
     }
@@ -177,25 +194,29 @@ __global__ void copy_rows_kernel(double* __restrict__ out, const double* __restr
 // Tiled transpose: dimension a is contiguous in the input and the last
 // dimension b in the output; 32 x 32 tiles go through shared memory so that
 // both the loads and the stores are coalesced.  The other dimensions (st)
-// are decomposed once per tile.
-template <bool PLAIN>
+// are decomposed once per tile, in 32-bit arithmetic (I) whenever the tile
+// count is below 2^31.
+template <bool PLAIN, typename I>
 __global__ void copy_transpose_kernel(double* __restrict__ out, const double* __restrict__ in,
                                       int64_t na, int64_t nb, int64_t outer, Strides st,
                                       int64_t is_b, int64_t os_a, double alpha, double beta) {
   __shared__ double tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int64_t ta_n = (na + 31) / 32, tb_n = (nb + 31) / 32;
-  const int64_t ntiles = outer * ta_n * tb_n;
-  for (int64_t tid = blockIdx.x; tid < ntiles; tid += gridDim.x) {
-    const int64_t tb = tid % tb_n, ta = (tid / tb_n) % ta_n, q = tid / (tb_n * ta_n);
-    int64_t rem = q, ioff = 0, ooff = 0;
+  const I ta_n = (I)((na + 31) / 32), tb_n = (I)((nb + 31) / 32);
+  const I ntiles = (I)outer * ta_n * tb_n;
+  for (I tid = blockIdx.x; tid < ntiles; tid += gridDim.x) {
+    const I tq = tid / tb_n;
+    const I tb = tid - tq * tb_n, ta = tq % ta_n, q = tq / ta_n;
+    I rem = q;
+    int64_t ioff = 0, ooff = 0;
     for (int d = st.nd - 1; d >= 0; --d) {
-      const int64_t c = rem % st.shape[d];
-      rem /= st.shape[d];
-      ioff += c * st.istride[d];
-      ooff += c * st.ostride[d];
+      const I sh = (I)st.shape[d];
+      const I c = rem % sh;
+      rem /= sh;
+      ioff += (int64_t)c * st.istride[d];
+      ooff += (int64_t)c * st.ostride[d];
     }
-    const int64_t a0 = ta * 32, b0 = tb * 32;
+    const int64_t a0 = (int64_t)ta * 32, b0 = (int64_t)tb * 32;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int64_t a = a0 + tx, b = b0 + ty + 8 * i;
@@ -659,12 +680,19 @@ void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const 
     }
     const int64_t tiles = outer * ((sh[a] + 31) / 32) * ((sh[last] + 31) / 32);
     const int g = (int)std::min<int64_t>(tiles, 152 * 16);
-    if (plain)
-      copy_transpose_kernel<true><<<g, dim3(32, 8), 0, s>>>(out, in, sh[a], sh[last], outer, st,
-                                                            is[last], os[a], alpha, beta);
+    const bool narrow = tiles < ((int64_t)1 << 31);
+    if (plain && narrow)
+      copy_transpose_kernel<true, uint32_t><<<g, dim3(32, 8), 0, s>>>(
+          out, in, sh[a], sh[last], outer, st, is[last], os[a], alpha, beta);
+    else if (plain)
+      copy_transpose_kernel<true, int64_t><<<g, dim3(32, 8), 0, s>>>(
+          out, in, sh[a], sh[last], outer, st, is[last], os[a], alpha, beta);
+    else if (narrow)
+      copy_transpose_kernel<false, uint32_t><<<g, dim3(32, 8), 0, s>>>(
+          out, in, sh[a], sh[last], outer, st, is[last], os[a], alpha, beta);
     else
-      copy_transpose_kernel<false><<<g, dim3(32, 8), 0, s>>>(out, in, sh[a], sh[last], outer, st,
-                                                             is[last], os[a], alpha, beta);
+      copy_transpose_kernel<false, int64_t><<<g, dim3(32, 8), 0, s>>>(
+          out, in, sh[a], sh[last], outer, st, is[last], os[a], alpha, beta);
   } else if (os[last] == 1 || is[last] == 1) {
     // rows along the last dimension (coalesced on at least one side)
     Strides st;
@@ -682,14 +710,30 @@ void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const 
     int width = 32;
     while (width < 256 && 4 * width < len) width *= 2;
     const int per = 256 / width;
-    const int64_t blocks = (rows + per - 1) / per;
+    // fewer rows than the 2432 blocks of a full grid: cut the rows into
+    // segments of at least 1024 values (a multiple of one 4 x 256 pass)
+    int nseg = 1, seglen = len;
+    if (per == 1 && rows < 152 * 16 && len > 2048) {
+      const int64_t want = std::min<int64_t>((152 * 16 + rows - 1) / rows, (len + 1023) / 1024);
+      seglen = (int)(((len + want - 1) / want + 1023) / 1024 * 1024);
+      nseg = (len + seglen - 1) / seglen;
+    }
+    const int64_t blocks = (rows * nseg + per - 1) / per;
     const int g = (int)std::min<int64_t>(blocks, 152 * 16);
-    if (plain)
-      copy_rows_kernel<true><<<g, 256, 0, s>>>(out, in, rows, len, per, st, is[last], os[last],
-                                               alpha, beta);
+    // 32-bit row arithmetic needs rows * nseg plus one grid stride below 2^31
+    const bool narrow = rows * nseg + (int64_t)g * per < ((int64_t)1 << 31);
+    if (plain && narrow)
+      copy_rows_kernel<true, uint32_t><<<g, 256, 0, s>>>(out, in, rows, len, per, st, is[last],
+                                                         os[last], alpha, beta, nseg, seglen);
+    else if (plain)
+      copy_rows_kernel<true, int64_t><<<g, 256, 0, s>>>(out, in, rows, len, per, st, is[last],
+                                                        os[last], alpha, beta, nseg, seglen);
+    else if (narrow)
+      copy_rows_kernel<false, uint32_t><<<g, 256, 0, s>>>(out, in, rows, len, per, st, is[last],
+                                                          os[last], alpha, beta, nseg, seglen);
     else
-      copy_rows_kernel<false><<<g, 256, 0, s>>>(out, in, rows, len, per, st, is[last], os[last],
-                                                alpha, beta);
+      copy_rows_kernel<false, int64_t><<<g, 256, 0, s>>>(out, in, rows, len, per, st, is[last],
+                                                         os[last], alpha, beta, nseg, seglen);
   } else {
     Strides st;
     st.nd = m;
