@@ -126,33 +126,6 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
     return sh;
   };
 
-  // operand A in (bat, M, K) or (bat, K, M)
-  bool ta = false;
-  const double* Ap = A.p;
-  OT Atmp;
-  if (sp.a == bat + Ml + Kl) {
-    ta = false;
-  } else if (sp.a == bat + Kl + Ml) {
-    ta = true;
-  } else {
-    std::string want = bat + Ml + Kl;
-    Atmp.make(shape_of(want), s_);
-    perm((sp.a + "->" + want).c_str(), 1.0, A, 0.0, Atmp.t);
-    Ap = Atmp.p();
-  }
-  bool tb = false;
-  const double* Bp = B.p;
-  OT Btmp;
-  if (sp.b == bat + Kl + Nl) {
-    tb = false;
-  } else if (sp.b == bat + Nl + Kl) {
-    tb = true;
-  } else {
-    std::string want = bat + Kl + Nl;
-    Btmp.make(shape_of(want), s_);
-    perm((sp.b + "->" + want).c_str(), 1.0, B, 0.0, Btmp.t);
-    Bp = Btmp.p();
-  }
   const std::string cl = bat + Ml + Nl;
   if (level_ > 0 && nb == 1 && Ms > 1 && Ns > 1 && 2.0 * Ms * Ns * Ks >= min_flops_) {
     // tensor-core path: A as [M][K], B as [N][K] (K contiguous), split into BF16 planes
@@ -206,6 +179,34 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
       perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
     }
     return;
+  }
+  // FP64 paths: operand A in (bat, M, K) or (bat, K, M), B in (bat, K, N) or
+  // (bat, N, K); other layouts are permuted first
+  bool ta = false;
+  const double* Ap = A.p;
+  OT Atmp;
+  if (sp.a == bat + Ml + Kl) {
+    ta = false;
+  } else if (sp.a == bat + Kl + Ml) {
+    ta = true;
+  } else {
+    std::string want = bat + Ml + Kl;
+    Atmp.make(shape_of(want), s_);
+    perm((sp.a + "->" + want).c_str(), 1.0, A, 0.0, Atmp.t);
+    Ap = Atmp.p();
+  }
+  bool tb = false;
+  const double* Bp = B.p;
+  OT Btmp;
+  if (sp.b == bat + Kl + Nl) {
+    tb = false;
+  } else if (sp.b == bat + Nl + Kl) {
+    tb = true;
+  } else {
+    std::string want = bat + Kl + Nl;
+    Btmp.make(shape_of(want), s_);
+    perm((sp.b + "->" + want).c_str(), 1.0, B, 0.0, Btmp.t);
+    Bp = Btmp.p();
   }
   const int64_t lda = ta ? Ms : Ks, ldb = tb ? Ks : Ns;
   if (Ns == 1 && nb == 1 && Ks > 0) {
@@ -897,7 +898,21 @@ void State::quad_terms(const T& t, const T& u, const T& Z, const T& r2, double s
   es_("klbd,ldkc->bc", -1.0, u, govov_.t, 0.0, Fvv_.t);
   es_("ljcd,kdlc->kj", 1.0, u, govov_.t, 0.0, Foo_.t);
   es_("ijac,bc->ijab", sign, t, Fvv_.t, 1.0, Z);
-  es_("ikab,kj->ijab", -sign, t, Foo_.t, 1.0, Z);
+  foo_term(t, Foo_.p(), -sign, Z);
+}
+
+// Z_ijab += alpha sum_k t_ikab W_kj: an o x o matrix applied along the second
+// index, in place (tensor-core tiles would be mostly padding at N = K = o).
+// FP64 sums on the FP64 and FP64-class paths, FP32 sums at the split-BF16
+// levels (at least as accurate as their products).
+void State::foo_term(const T& t, const double* W, double alpha, const T& Z) {
+  const int lev = es_.level();
+  if (o_ <= 32) {
+    k::axis_matrix(s_, lev >= 1 && lev <= 3, Z.p, t.p, W, o_, o_, o_, (int64_t)v_ * v_, alpha,
+                   1.0);
+  } else {
+    es_("ikab,kj->ijab", alpha, t, T(const_cast<double*>(W), {o_, o_}), 1.0, Z);
+  }
 }
 
 void State::residual(const double* tv, double* rv, double* energy) {
@@ -937,7 +952,7 @@ void State::residual(const double* tv, double* rv, double* energy) {
     box_copy(s_, Fvv.p(), {v, 1}, F_.p() + (int64_t)o * n + o, {n, 1}, {v, v});
     box_copy(s_, Foo.p(), {o, 1}, F_.p(), {n, 1}, {o, o});
     es_("ijac,bc->ijab", 1.0, t2, Fvv.t, 1.0, Z_.t);
-    es_("ikab,kj->ijab", -1.0, t2, Foo.t, 1.0, Z_.t);
+    foo_term(t2, Foo.p(), -1.0, Z_.t);
   }
   es_.set_split(lev, err_.as<int>(), tc_min_flops_);
   quad_terms(t2, u_.t, Z_.t, r2, 1.0);

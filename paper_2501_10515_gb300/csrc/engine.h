@@ -137,6 +137,7 @@ class State {
   // the ladder GEMMs against (xc|bd) chunks rebuilt in this call
   void ladder_streamed(const T& t2);
   void quad_terms(const T& t, const T& u, const T& Z, const T& r2, double sign);
+  void foo_term(const T& t, const double* W, double alpha, const T& Z);
 
   std::shared_ptr<Molecule> mol_;
   Options opt_;

@@ -15,6 +15,12 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
 
 // y[m] = alpha * sum_k op(A)[m][k] x[k] + beta * y[m] (op(A) is M x K;
 // ta: A stored K x M).  A warp per row (ta = false) or a thread per row.
+// C[x][j][y] = alpha sum_k A[x][k][y] W[k][j] + beta C[x][j][y] (row-major;
+// K, J <= 32): a small matrix applied along one axis of a large tensor, read
+// and written in place.  fp32 = false sums in FP64 in ascending k (the order
+// of gemm_f64); fp32 = true rounds A and W to FP32 and sums in FP32.
+void axis_matrix(cudaStream_t s, bool fp32, double* C, const double* A, const double* W,
+                 int64_t X, int K, int J, int64_t Y, double alpha, double beta);
 void gemv_f64(cudaStream_t s, bool ta, int64_t M, int64_t K, double alpha, const double* A,
               int64_t lda, const double* x, double beta, double* y);
 

@@ -71,8 +71,7 @@ gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
       Bs[kk][nn] = val;
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < TK; ++kk) {
+    auto step = [&](int kk) {
       double a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
@@ -82,6 +81,16 @@ gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    };
+    if (K - k0 >= TK) {
+#pragma unroll
+      for (int kk = 0; kk < TK; ++kk) step(kk);
+    } else {
+      // last, partial K tile: the zero-filled rows would only add 0 * 0 on
+      // the FP64 units, the scarce ones on this part (a K = 1 outer product
+      // would pay 16 times its work)
+      const int kn = (int)(K - k0);
+      for (int kk = 0; kk < kn; ++kk) step(kk);
     }
     __syncthreads();
   }
@@ -234,6 +243,50 @@ __global__ void copy_transpose_kernel(double* __restrict__ out, const double* __
       }
     }
     __syncthreads();
+  }
+}
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+// One (x, y) column per thread: its K values of A stay in registers and all J
+// outputs are formed from W in shared memory; the old values of C are loaded
+// eight at a time before their stores.  Reads A once and C once: HBM-bound
+// in FP32, FP64-unit-bound in FP64.
+template <typename CT>
+__global__ void axis_matrix_kernel(double* __restrict__ C, const double* __restrict__ A,
+                                   const double* __restrict__ W, int64_t X, int K, int J,
+                                   int64_t Y, double alpha, double beta) {
+  __shared__ CT w[32 * 32];
+  for (int e = threadIdx.x; e < K * J; e += blockDim.x) w[e] = (CT)W[e];
+  __syncthreads();
+  const int64_t total = X * Y;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = idx / Y, y = idx - x * Y;
+    const double* a = A + x * (int64_t)K * Y + y;
+    double* c = C + x * (int64_t)J * Y + y;
+    CT av[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) av[k] = k < K ? (CT)a[k * Y] : CT(0);
+    for (int j0 = 0; j0 < J; j0 += 8) {
+      double old[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        old[u] = (beta != 0.0 && j0 + u < J) ? c[(int64_t)(j0 + u) * Y] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u;
+        if (j < J) {
+          CT acc = CT(0);
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if (k < K) acc = fma_t(av[k], w[k * J + j], acc);
+          const double r = (double)acc;
+          c[(int64_t)j * Y] = (beta == 0.0) ? alpha * r : fma(alpha, r, beta * old[u]);
+        }
+      }
+    }
   }
 }
 
@@ -746,6 +799,21 @@ void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const 
   }
   count_launch();
   check_launch("strided_copy");
+}
+
+void axis_matrix(cudaStream_t s, bool fp32, double* C, const double* A, const double* W,
+                 int64_t X, int K, int J, int64_t Y, double alpha, double beta) {
+  ASCC_REQUIRE(K >= 1 && K <= 32 && J >= 1 && J <= 32, "axis_matrix: K and J in 1..32");
+  const int64_t total = X * Y;
+  if (total <= 0) return;
+  count_flops(2.0 * (double)total * K * J);
+  const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  if (fp32)
+    axis_matrix_kernel<float><<<g, 256, 0, s>>>(C, A, W, X, K, J, Y, alpha, beta);
+  else
+    axis_matrix_kernel<double><<<g, 256, 0, s>>>(C, A, W, X, K, J, Y, alpha, beta);
+  count_launch();
+  check_launch("axis_matrix");
 }
 
 void gemv_f64(cudaStream_t s, bool ta, int64_t M, int64_t K, double alpha, const double* A,
