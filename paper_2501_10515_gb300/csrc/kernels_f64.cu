@@ -229,15 +229,10 @@ __global__ void copy_transpose_kernel(double* __restrict__ out, const double* __
       ooff += (int64_t)c * st.ostride[d];
     }
     const int64_t a0 = (int64_t)ta * 32, b0 = (int64_t)tb * 32;
-    // with beta, this thread's four old outputs are loaded together with its
-    // four inputs, before the tile is exchanged
-    double old[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int64_t a = a0 + tx, b = b0 + ty + 8 * i;
       if (a < na && b < nb) tile[ty + 8 * i][tx] = in[ioff + a + b * is_b];
-      const int64_t ob = b0 + tx, oa = a0 + ty + 8 * i;
-      old[i] = (!PLAIN && beta != 0.0 && oa < na && ob < nb) ? out[ooff + oa * os_a + ob] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -247,7 +242,7 @@ __global__ void copy_transpose_kernel(double* __restrict__ out, const double* __
         const double v = tile[tx][ty + 8 * i];
         double* o = out + ooff + a * os_a + b;
         if (PLAIN) *o = v;
-        else *o = (beta == 0.0) ? alpha * v : fma(alpha, v, beta * old[i]);
+        else *o = (beta == 0.0) ? alpha * v : fma(alpha, v, beta * *o);
       }
     }
     __syncthreads();
@@ -508,26 +503,22 @@ __global__ void scatter_pairs_kernel(double* Y, const double* Yvv, int o, int v,
 // Denominators: bare eps for the primary amplitudes (every index h or p) of a
 // one-CSF state and for the ground state; eps_eff (h and p at their mean) for
 // all other amplitudes of a one-CSF state.
-// I: type of the index arithmetic, 32-bit whenever the amplitude count (plus
-// one grid stride) is below 2^31.
-template <typename I>
 __global__ void jacobi_kernel(double* tn, double* e, const double* t, const double* r,
                               const double* eps, const double* eps_eff, int o, int v, int hole,
                               int particle, const int32_t* t3idx, int64_t n3) {
-  const I n1 = (I)o * (I)v, n2 = n1 * n1, total = n1 + n2 + (I)n3;
-  const I vi = (I)v, oi = (I)o;
-  for (I idx = blockIdx.x * (I)blockDim.x + threadIdx.x; idx < total;
-       idx += (I)gridDim.x * blockDim.x) {
+  const int64_t n1 = (int64_t)o * v, n2 = n1 * n1, total = n1 + n2 + n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
     double D;
     if (idx < n1) {
-      const int i = (int)(idx / vi), a = (int)(idx % vi);
+      const int i = (int)(idx / v), a = (int)(idx % v);
       const double* ee = (i == hole && a == particle) ? eps : eps_eff;
       D = ee[i] - ee[o + a];
     } else if (idx < n1 + n2) {
-      I q = idx - n1;
-      const int b = (int)(q % vi); q /= vi;
-      const int a = (int)(q % vi); q /= vi;
-      const int j = (int)(q % oi); q /= oi;
+      int64_t q = idx - n1;
+      const int b = (int)(q % v); q /= v;
+      const int a = (int)(q % v); q /= v;
+      const int j = (int)(q % o); q /= o;
       const int i = (int)q;
       const bool prim = i == hole && j == hole && a == particle && b == particle;
       const double* ee = prim ? eps : eps_eff;
@@ -918,13 +909,8 @@ void jacobi(cudaStream_t s, double* tn, double* e, const double* t, const double
             const double* eps, const double* eps_eff, int o, int v, int hole, int particle,
             const int32_t* t3idx, int64_t n3) {
   const int64_t total = (int64_t)o * v + (int64_t)o * o * v * v + n3;
-  const int g = grid_for(total);
-  if (total + (int64_t)g * 256 < ((int64_t)1 << 31))
-    jacobi_kernel<uint32_t><<<g, 256, 0, s>>>(tn, e, t, r, eps, eps_eff, o, v, hole, particle,
-                                              t3idx, n3);
-  else
-    jacobi_kernel<int64_t><<<g, 256, 0, s>>>(tn, e, t, r, eps, eps_eff, o, v, hole, particle,
-                                             t3idx, n3);
+  jacobi_kernel<<<grid_for(total), 256, 0, s>>>(tn, e, t, r, eps, eps_eff, o, v, hole, particle,
+                                                t3idx, n3);
   count_launch();
   check_launch("jacobi");
 }
