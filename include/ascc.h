@@ -59,9 +59,11 @@ typedef enum {
 /* Precision of the residual contractions.
  *   ASCC_FP64        every contraction in FP64 (DFMA).
  *   ASCC_MIXED_BF16  large contractions on the BF16 tensor cores, 3 then 6
- *                    split products, with defect correction from FP64-class
- *                    evaluations (ASCC_FP64_TC contractions); the accepted
- *                    amplitudes satisfy the FP64 equations to r_tol.
+ *                    split products (the occupied Fock-like terms, an o x o
+ *                    matrix along one index, as FP32 sums), with defect
+ *                    correction from FP64-class evaluations (ASCC_FP64_TC
+ *                    contractions); the accepted amplitudes satisfy the FP64
+ *                    equations to r_tol.
  *   ASCC_FP64_TC     every large contraction as exact BF16 digit-plane
  *                    products on the tensor cores (ascc_gemm_fp64_tc, error
  *                    1e-12 to 5e-12 of |A||B|); iterations follow the FP64 path. */
