@@ -28,8 +28,9 @@ R1 is the alpha-single projection and R2 the alpha-beta double projection.
 Partial linearisation (Sec. II.C): the terms bilinear in T2 are collected in
 quad(t, t); PLASCC subtracts quad(m, m) with m = T2^M (mixed doubles).
 
-The mixed-triples slice (Sec. II.B.1) is evaluated in spin orbitals by
-spinorb.residual; that path is only used for small systems.
+The mixed-triples slice (Sec. II.B.1) is evaluated on the slice by
+t3slice.residual (the spin-orbital terms of spinorb, one spin case at a time
+on spatial blocks).
 """
 from __future__ import annotations
 
@@ -167,11 +168,8 @@ def residual(hbar, Bbar, o, t1, t2, linearize=False, hole=None, particle=None,
     En = energy_from_blocks(t2, blk)
     R3 = None
     if t3_idx is not None and len(t3_idx):
-        from . import spinorb
-        g = ham.eri_from_df(Bbar)
-        t3 = amp.t3_dense(t3_idx, t3_vals, o, v)
-        _, r1x, r2x, r3 = spinorb.residual(hbar, g, t1, t2, t3, linearize=linearize,
-                                            hole=hole, particle=particle, triples_only=True)
+        from . import t3slice
+        r1x, r2x, R3 = t3slice.residual(blk.F, blk.B, o, t2, t3_idx, t3_vals, hole, particle,
+                                        linearize=linearize)
         R1 += r1x; R2 += r2x
-        R3 = amp.t3_gather(r3, t3_idx)
     return En, R1, R2, R3

@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libascc.so")
 OBJ = os.path.join(HERE, "_build")
-SOURCES = ["kernels_f64.cu", "gemm_tc.cu", "gemm_oz.cu", "engine.cu", "api.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["kernels_f64.cu", "gemm_tc.cu", "gemm_oz.cu", "engine.cu", "t3p.cu", "api.cu", "noalloc.cu",
+           "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -31,7 +32,7 @@ def _newer(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh", ".inc"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "ascc.h"))
     objs = []
     jobs = []

@@ -20,6 +20,7 @@
 #include "gemm_oz.h"
 #include "gemm_tc.h"
 #include "kernels.h"
+#include "t3p.h"
 
 namespace ascc {
 
@@ -406,10 +407,7 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
                    opt_.precision == ASCC_FP64_TC,
                "precision must be ASCC_FP64, ASCC_MIXED_BF16 or ASCC_FP64_TC");
   ASCC_REQUIRE(opt_.diis_dim >= 1 && opt_.diis_dim <= 32, "diis_dim in 1..32");
-  if (opt_.triples && hole_ >= 0) {
-    t3idx_host_ = t3p_index(o_, v_, hole_, particle_);
-    ASCC_REQUIRE(n3() == 0, "the T3' slice is not available in this build");
-  }
+  if (opt_.triples && hole_ >= 0) t3idx_host_ = t3p_index(o_, v_, hole_, particle_);
   nu_ = v_ + (hole_ >= 0 ? 1 : 0);
   const int64_t N = namp();
   t_.make({N}, s);
@@ -498,6 +496,105 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
     mol_->ensure_fp64_ladder();
   }
   build_state_integrals();
+  if (n3() > 0) setup_triples();
+}
+
+// Packed T3' order -> positions in the blocks TA..TD (see t3p.h): h is moved
+// into the j slot and p into the b slot, each swap flipping the sign; TA and
+// TC also receive the antisymmetric partner (c, b) / (k, j).
+void State::setup_triples() {
+  const int o = o_, v = v_, h = hole_, p = particle_;
+  t3p_ = std::make_unique<T3pProgram>(o, v, naux_, h, p);
+  const int64_t N3 = n3();
+  std::vector<int64_t> dst(N3), dst2(N3);
+  std::vector<signed char> sgn(N3);
+  const int64_t oA = t3p_->block_offset(0), oB = t3p_->block_offset(1),
+                oC = t3p_->block_offset(2), oD = t3p_->block_offset(3);
+  for (int64_t q = 0; q < N3; ++q) {
+    const int32_t* x = &t3idx_host_[6 * q];
+    int i = x[0], j = x[1], kk = x[2], a = x[3], b = x[4], c = x[5];
+    int sg = 1;
+    int64_t d1 = -1, d2 = -1;
+    if (i == h && (j == h || kk == h)) {
+      if (j != h) { std::swap(j, kk); sg = -sg; }
+      if (a == p) {
+        d1 = oA + ((int64_t)kk * v + b) * v + c;
+        d2 = oA + ((int64_t)kk * v + c) * v + b;
+      } else {
+        if (b != p) { std::swap(b, c); sg = -sg; }
+        d1 = oB + ((int64_t)kk * v + a) * v + c;
+      }
+    } else if (i == h) {
+      if (b != p) { std::swap(b, c); sg = -sg; }
+      d1 = oC + ((int64_t)j * o + kk) * v + c;
+      d2 = oC + ((int64_t)kk * o + j) * v + c;
+    } else {
+      if (j != h) { std::swap(j, kk); sg = -sg; }
+      if (b != p) { std::swap(b, c); sg = -sg; }
+      d1 = oD + ((int64_t)i * o + kk) * v + c;
+    }
+    dst[q] = d1;
+    dst2[q] = d2;
+    sgn[q] = (signed char)sg;
+  }
+  t3dst_.alloc(sizeof(int64_t) * N3, s_);
+  t3dst2_.alloc(sizeof(int64_t) * N3, s_);
+  t3sgn_.alloc(N3, s_);
+  t3idx_.alloc(sizeof(int32_t) * 6 * N3, s_);
+  ASCC_CUDA(cudaMemcpyAsync(t3dst_.as<int64_t>(), dst.data(), sizeof(int64_t) * N3,
+                            cudaMemcpyHostToDevice, s_));
+  ASCC_CUDA(cudaMemcpyAsync(t3dst2_.as<int64_t>(), dst2.data(), sizeof(int64_t) * N3,
+                            cudaMemcpyHostToDevice, s_));
+  ASCC_CUDA(cudaMemcpyAsync(t3sgn_.as<signed char>(), sgn.data(), N3, cudaMemcpyHostToDevice, s_));
+  ASCC_CUDA(cudaMemcpyAsync(t3idx_.as<int32_t>(), t3idx_host_.data(), sizeof(int32_t) * 6 * N3,
+                            cudaMemcpyHostToDevice, s_));
+  t3blk_.make({t3p_->block_elements()}, s_);
+  r3blk_.make({t3p_->block_elements()}, s_);
+  t3ws_.make({t3p_->workspace_elements()}, s_);
+  t3ts_.make({o, o, v, v}, s_);
+  if (opt_.linearize) t3nm_.make({o, o, v, v}, s_);
+  ASCC_CUDA(cudaStreamSynchronize(s_));
+}
+
+// R3' and the T3' terms of R1 and R2 by the generated program (t3p.h); the
+// partially linearised state drops the T2^M T2^M and T2^M T3' parts of R3'
+// (Sec. II.C).
+void State::triples(const T& t2, const double* t3, const T& r1, const T& r2, double* r3) {
+  const T3pProgram& P = *t3p_;
+  const int64_t nb = P.block_elements(), N3 = n3();
+  k::t3p_unpack(s_, t3blk_.p(), nb, t3, t3dst_.as<int64_t>(), t3dst2_.as<int64_t>(),
+                t3sgn_.as<signed char>(), N3);
+  k::fill(s_, r3blk_.p(), 0.0, nb);
+  double* base[T3P_NBASE] = {};
+  base[T3P_F] = F_.p();
+  base[T3P_B] = Bhat_.p();
+  for (int b = 0; b < 4; ++b) {
+    base[T3P_TA + b] = t3blk_.p() + P.block_offset(b);
+    base[T3P_RA + b] = r3blk_.p() + P.block_offset(b);
+  }
+  base[T3P_R1] = r1.p;
+  base[T3P_R2] = r2.p;
+  double* ws = t3ws_.p();
+  auto bind = [&](double* t) {
+    // ts = t - t^(i<->j), the same-spin doubles of the singlet
+    es_.perm("ijab->jiab", -1.0, T(t, {o_, o_, v_, v_}), 0.0, t3ts_.t);
+    k::axpby(s_, t3ts_.p(), t, 1.0, 1.0, n2());
+    base[T3P_T2] = t;
+    base[T3P_TS] = t3ts_.p();
+  };
+  P.run(es_, s_, T3P_PRO, base, 1.0, ws);
+  bind(t2.p);
+  P.run(es_, s_, T3P_LIN, base, 1.0, ws);
+  P.run(es_, s_, T3P_QUAD, base, 1.0, ws);
+  if (opt_.linearize) {
+    bind(m_.p());
+    P.run(es_, s_, T3P_QUAD, base, -1.0, ws);
+    k::axpby(s_, t3nm_.p(), t2.p, 1.0, 0.0, n2());
+    k::axpby(s_, t3nm_.p(), m_.p(), -1.0, 1.0, n2());
+    bind(t3nm_.p());
+  }
+  P.run(es_, s_, T3P_MIX, base, 1.0, ws);
+  k::t3p_gather(s_, r3, r3blk_.p(), t3dst_.as<int64_t>(), t3sgn_.as<signed char>(), N3);
 }
 
 // Mixed precision: 3 BF16 products (16 significant bits) until max|R| reaches
@@ -964,6 +1061,7 @@ void State::residual(const double* tv, double* rv, double* energy) {
   }
   es_.perm("ijab->jiba", 1.0, Z_.t, 1.0, r2);
   k::axpby(s_, r2.p, Z_.p(), 1.0, 1.0, n2);
+  if (n3() > 0) triples(t2, tv + n1 + n2, r1, r2, rv + n1 + n2);
   // ---- energy: <phi0|H-hat|phi0> + sum t_ij^ab L_iajb
   k::reference_energy(s_, scal_.p() + 8, hhat_.p(), n, goooo_.p(), o);
   {
@@ -1147,7 +1245,7 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     double* tn = hist_t_.p() + (int64_t)slot * N;
     double* en = hist_e_.p() + (int64_t)slot * N;
     k::jacobi(s_, tn, en, t_.p(), r_.p(), mol_->eps.p(), eps_eff_.p(), o_, v_, hole_, particle_,
-              n3() ? reinterpret_cast<const int32_t*>(t3idx_.p()) : nullptr, n3());
+              n3() ? t3idx_.as<int32_t>() : nullptr, n3());
     k::jacobi_pairs(s_, tn, en, t_.p(), r_.p(), eps_eff_.p(), F_.p(), o_, v_, hole_, particle_);
     k::dot_rows(s_, en, hist_e_.p(), N, m, N, scal_.p() + 32, work_.p());
     std::vector<double> row(m);

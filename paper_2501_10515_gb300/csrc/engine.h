@@ -77,6 +77,8 @@ struct Molecule {
   size_t bytes() const;
 };
 
+class T3pProgram;
+
 struct Options {
   int precision = ASCC_FP64;
   int linearize = 1;
@@ -137,6 +139,9 @@ class State {
   // the ladder GEMMs against (xc|bd) chunks rebuilt in this call
   void ladder_streamed(const T& t2);
   void quad_terms(const T& t, const T& u, const T& Z, const T& r2, double sign);
+  // T3' slice: its residual R3' and its contributions to R1 and R2
+  void triples(const T& t2, const double* t3, const T& r1, const T& r2, double* r3);
+  void setup_triples();
   void foo_term(const T& t, const double* W, double alpha, const T& Z);
 
   std::shared_ptr<Molecule> mol_;
@@ -161,7 +166,12 @@ class State {
   int nu_;               // v (+1 with the hole slot of an excited state)
   Einsum es_;
   std::vector<int32_t> t3idx_host_;
-  OT t3idx_;             // int32 [n3][6] stored in a double-sized buffer
+  DevBuf t3idx_;         // int32 [n3][6]
+  // T3' program, packed-slice <-> block maps, blocks of t3 and of R3', its
+  // workspace and the t2 - t2^(i<->j) operand of each binding
+  std::unique_ptr<T3pProgram> t3p_;
+  DevBuf t3dst_, t3dst2_, t3sgn_;
+  OT t3blk_, r3blk_, t3ws_, t3ts_, t3nm_;
   // per-state constant integrals of the ladder corrections
   OT Gh1, Gh2, Gh3, GooP;
   // amplitudes, residual, DIIS

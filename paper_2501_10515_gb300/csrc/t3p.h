@@ -1,0 +1,91 @@
+// The mixed-triples slice T3' of a one-CSF state (arXiv 2501.10515,
+// Sec. II.B.1): the alpha-beta-beta triples with at least three primary spin
+// orbitals among h-up, h-down, p-up, p-down, their residual R3' and their
+// contributions to R1 and R2, with the partial linearisation of Sec. II.C.
+//
+// Storage.  The packed amplitudes (the order of ascc_t3p_indices: (i, j < k,
+// a, b < c) lexicographic) are unpacked into four dense blocks that
+// partition the slice by the set of primary spin orbitals an element holds:
+//   TA[k][b][c] = t3[h,h,k,p,b,c]            [o][v][v]  (antisymmetric in b, c)
+//   TB[k][a][c] = t3[h,h,k,a,p,c], a != p    [o][v][v]
+//   TC[j][k][c] = t3[h,j,k,p,p,c], j,k != h  [o][o][v]  (antisymmetric in j, k)
+//   TD[i][k][c] = t3[i,h,k,p,p,c], i != h    [o][o][v]
+// (zero at every excluded position), and R3' is formed in the same blocks.
+//
+// Evaluation.  A generated program (t3p_program.inc, written by gen_t3p.py
+// from the spin-orbital triples equations) of dense contractions over these
+// blocks, the dressed Fock matrix, the dressed DF factor and t2, run through
+// the engine's einsum planner.  Its four sections are run with the t2
+// operand bound to:
+//   pro  (R1, R2 from T3'; R3' from [H,T3'])      no t2
+//   lin  (R3' from [H,T2])                         T2
+//   quad (R3' from 1/2[[H,T2],T2])                 T2, and for PLASCC again
+//                                                  with T2^M and weight -1
+//   mix  (R3' from [[H,T2],T3'])                   T2 (ASCC) or T2 - T2^M (PLASCC)
+#pragma once
+
+#include "engine.h"
+
+namespace ascc {
+
+struct T3pTensor {
+  int kind;          // 0 base operand, 1 slice of a base operand, 2 intermediate
+  int base;          // base operand index (kinds 0, 1)
+  const char* spec;  // slice selector, one character per base dimension
+  const char* dims;  // o / v / P per dimension
+  int section;
+};
+
+struct T3pOp {
+  int section;
+  int kind;          // 0 slice, 1 contraction into `out`, 2 contraction accumulated into an output
+  int out, a, b;
+  const char* spec;  // einsum labels of a, b and the result
+  double alpha;
+  int base;          // slice: the base operand; accumulate: the output base operand
+  const char* outspec;
+};
+
+// Base operands of the program, in the order of its tables.
+enum T3pBase { T3P_F = 0, T3P_B, T3P_T2, T3P_TS, T3P_TA, T3P_TB, T3P_TC, T3P_TD, T3P_R1,
+               T3P_R2, T3P_RA, T3P_RB, T3P_RC, T3P_RD, T3P_NBASE };
+enum T3pSection { T3P_PRO = 0, T3P_LIN, T3P_QUAD, T3P_MIX };
+
+class T3pProgram {
+ public:
+  // o, v, naux: sizes; h, p: the primary hole and particle.
+  T3pProgram(int o, int v, int naux, int h, int p);
+  // Device workspace of the intermediates (elements of double), with
+  // intermediates whose lifetimes do not overlap sharing memory.
+  int64_t workspace_elements() const { return ws_elems_; }
+  // Runs one section; base[T3pBase] points at the base operands (t2 / ts of
+  // the binding of that section); scale multiplies every accumulation.
+  void run(const Einsum& es, cudaStream_t s, int section, double* const* base, double scale,
+           double* ws) const;
+  // Sizes of the four blocks (elements) and the offsets of TA..TD (RA..RD)
+  // in one concatenated buffer.
+  int64_t block_elements() const { return blk_off_[4]; }
+  int64_t block_offset(int b) const { return blk_off_[b]; }
+
+ private:
+  std::vector<int64_t> base_shape(int b) const;
+  void select(int b, const char* spec, int64_t* offset, std::vector<int64_t>& shape,
+              std::vector<int64_t>& stride) const;
+  int o_, v_, n_, naux_, h_, p_;
+  std::vector<std::vector<int64_t>> shape_;
+  std::vector<int64_t> offset_;  // element offset of each slice / intermediate
+  int64_t ws_elems_ = 0, acc_off_ = 0;
+  int64_t blk_off_[5];
+};
+
+namespace k {
+// Packed slice <-> blocks.  dst[q] = element offset of amplitude q in the
+// concatenated [TA|TB|TC|TD] buffer, sgn[q] its sign; dst2/sgn2 the
+// antisymmetric partner position in TA or TC (-1 if none).
+void t3p_unpack(cudaStream_t s, double* blocks, int64_t nblk, const double* t3,
+                const int64_t* dst, const int64_t* dst2, const signed char* sgn, int64_t n3);
+void t3p_gather(cudaStream_t s, double* r3, const double* blocks, const int64_t* dst,
+                const signed char* sgn, int64_t n3);
+}  // namespace k
+
+}  // namespace ascc

@@ -1,0 +1,76 @@
+"""The mixed-triples slice T3' (Sec. II.B.1) on the GPU against the CPU oracle.
+
+R1, R2 and R3' of the full ASCC / PLASCC residual with T3' on, element by
+element through the C ABI, and converged solves.  Bars as for the T1/T2
+residual: relative residual norm <= 1e-9, energies within 1e-10 Eh (FP64 and
+FP64-class paths).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import amplitudes as amp
+from oracle import ascc as oracle_ascc
+from oracle import spinadapted as sa
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-9
+E_TOL = 1e-10
+
+
+def _ctx(s, hole, part, **kw):
+    import paper_2501_10515_gb300 as pkg
+    return pkg.Context(s.o, s.v, s.naux, s.eps, s.B, hole=hole, particle=part, triples=1, **kw)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _amplitudes(o, v, hole, part, n3, seed):
+    t1, t2, t3 = synth.random_amplitudes(o, v, seed=seed, scale=0.05, n_t3=n3)
+    g1, g2, _ = amp.initial_guess(o, v, hole, part)
+    return t1 + g1, t2 + g2, t3
+
+
+def _oracle(s, hole, part, t1, t2, t3, lin, idx):
+    hbar, Bbar, _ = oracle_ascc.prepare(s.eps, s.B, s.o, hole, part)
+    return sa.residual(hbar, Bbar, s.o, t1, t2, linearize=lin, hole=hole, particle=part,
+                       t3_idx=idx, t3_vals=t3)
+
+
+@pytest.mark.parametrize("o,v,seed,hole,part", [(3, 6, 1, 2, 0), (4, 7, 2, 1, 4), (2, 5, 3, 0, 2)])
+def test_slice_order_matches_oracle(o, v, seed, hole, part):
+    s = synth.make_system(o, v, seed=seed)
+    ctx = _ctx(s, hole, part, linearize=1)
+    assert np.array_equal(ctx.t3_indices(), amp.t3p_index(o, v, hole, part))
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("lin", [False, True])
+@pytest.mark.parametrize("o,v,seed,hole,part", [(3, 6, 1, 2, 0), (4, 7, 2, 1, 4), (4, 9, 5, 3, 8)])
+def test_residual_with_triples_matches_oracle(o, v, seed, hole, part, lin, precision):
+    s = synth.make_system(o, v, seed=seed)
+    idx = amp.t3p_index(o, v, hole, part)
+    t1, t2, t3 = _amplitudes(o, v, hole, part, len(idx), seed + 50)
+    ctx = _ctx(s, hole, part, linearize=int(lin), precision=precision)
+    E, r1, r2, r3 = ctx.residual(t1, t2, t3)
+    Eo, r1o, r2o, r3o = _oracle(s, hole, part, t1, t2, t3, lin, idx)
+    assert _rel(r1, r1o) <= REL_TOL
+    assert _rel(r2, r2o) <= REL_TOL
+    assert _rel(r3, r3o) <= REL_TOL
+    assert abs(E - Eo) <= E_TOL
+
+
+@pytest.mark.parametrize("lin", [False, True])
+def test_solve_with_triples_matches_oracle(lin):
+    o, v, hole, part = 3, 7, 2, 0
+    s = synth.make_system(o, v, seed=2)
+    ref = oracle_ascc.solve_state(s.eps, s.B, o, hole, part, linearize=lin, triples=True)
+    ctx = _ctx(s, hole, part, linearize=int(lin))
+    res = ctx.solve()
+    assert ref.converged and res.status == 0
+    assert abs(res.energy - ref.energy) <= E_TOL
+    t1, t2, t3 = ctx.get_state()
+    assert np.abs(t3 - ref.t3).max() < 1e-7

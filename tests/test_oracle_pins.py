@@ -175,6 +175,31 @@ def test_bruteforce_spinorbital_spinadapted_agree(o, v, exc, linearize, triples)
         assert np.abs(R3a - R3b).max() < tol
 
 
+@pytest.mark.parametrize("o,v,hole,part", [(3, 6, 2, 0), (4, 7, 1, 4), (4, 8, 0, 7)])
+@pytest.mark.parametrize("linearize", [False, True])
+def test_slice_oracle_matches_spinorbital(o, v, hole, part, linearize):
+    """O-SL (the T3' terms evaluated on the four slice blocks, t3slice) equals
+    the dense spin-orbital triples of O-SO at sizes beyond brute force."""
+    from oracle import t3slice
+    s, h, _ = system(o, v, seed=6, sigma=0.15)
+    hb, Bb = ham.similarity_transform(h, s.B, o, hole, part)
+    idx = amp.t3p_index(o, v, hole, part)
+    t1, t2, t3 = random_amplitudes(o, v, seed=12, scale=0.1, n_t3=len(idx))
+    blk = sa.dressed_blocks(hb, Bb, o, t1)
+    r1, r2, r3 = t3slice.residual(blk.F, blk.B, o, t2, idx, t3, hole, part, linearize=linearize)
+    _, r1s, r2s, R3s = so.residual(hb, ham.eri_from_df(Bb), t1, t2, amp.t3_dense(idx, t3, o, v),
+                                   linearize=linearize, hole=hole, particle=part,
+                                   triples_only=True)
+    tol = 1e-12 * max(1.0, np.abs(R3s).max())
+    assert np.abs(r1 - r1s).max() < tol
+    assert np.abs(r2 - r2s).max() < tol
+    assert np.abs(r3 - amp.t3_gather(R3s, idx)).max() < tol
+    # the blocks partition the slice: unpacking and gathering is the identity
+    X = t3slice.blocks_from_slice(idx, t3, o, v, hole, part)
+    R = {'R' + k[1]: X[k] for k in X}
+    assert np.array_equal(t3slice.gather(idx, R, o, v, hole, part), t3)
+
+
 def test_linearisation_changes_the_residual():
     """PLASCC differs from ASCC exactly by the T2^M T2^M terms (Sec. II.C)."""
     o, v = 3, 5
