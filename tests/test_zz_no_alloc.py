@@ -1,10 +1,12 @@
 """The allocation-free tensor-core GEMM entry point, through the C ABI.
 
 ascc_gemm_split_bf16_noalloc serves callers that cannot allocate device memory
-at call time (stream capture without allocation nodes, allocator-free loops,
-fully pre-reserved device memory).  It must give the same product as the
-allocating ascc_gemm_split_bf16, call after call, with its operand planes in
-the library's fixed scratch array.  This file is collected last on purpose.
+when they need the product: processes whose GPU memory was handed in full to
+another pool, and code that must stay out of the CUDA allocator (which can
+synchronise the device).  It must give the same product as the allocating
+ascc_gemm_split_bf16 (same operand split, same K split), call after call,
+with its operand planes and split-K partials in the library's fixed scratch
+array.  This file is collected last on purpose.
 """
 import pytest
 
@@ -27,13 +29,18 @@ def _operands(M, N, K, seed):
 def test_noalloc_matches_allocating_entry_point_twice(level):
     import torch
     import paper_2501_10515_gb300 as pkg
-    for call, (M, N, K) in enumerate([(300, 500, 700), (130, 260, 1000)]):
+    for call, (M, N, K) in enumerate([(300, 500, 700), (130, 260, 1000), (64, 96, 5000)]):
         A, B, C0 = _operands(M, N, K, seed=17 + call + 10 * level)
         want = C0.clone()
         pkg.gemm_split_bf16(A, B, want, level, alpha=0.75, beta=0.5)
         got = C0.clone()
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
         pkg.gemm_split_bf16_noalloc(A, B, got, level, alpha=0.75, beta=0.5)
         torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before
+        # same K split as the allocating call: the same FP32 partial sums
+        assert (got - want).abs().max().item() <= 1e-12 * ((want.abs().max().item()) + 1.0)
         scale = (0.75 * (A.abs() @ B.abs().T)).max().item() + 1.0
         assert (got - want).abs().max().item() / scale < LEVEL_TOL[level]
         ref = 0.75 * (A @ B.T) + 0.5 * C0
