@@ -178,6 +178,24 @@ ascc_status ascc_energy(ascc_ctx* ctx, const double* t1, const double* t2,
  * ASCC_ERR_DIVERGED otherwise (res is filled in every case). */
 ascc_status ascc_solve(ascc_ctx* ctx, ascc_result* res);
 
+/* The two ansatz choices of Sec. II.D for an excitation with Aufbau weight
+ * alpha: the state as created and the same state with the hole orbital's
+ * sign flipped (alpha -> -alpha, S -> -S), sharing the molecule's integrals.
+ * Both are solved from their zeroth-order guesses; the reported energy is
+ * their mean, or the energy of the one that converged when the other did
+ * not (Sec. III.A).  The second state is created on the first call and kept
+ * by the context.  Returns ASCC_OK when at least one converged (res->energy
+ * set, res->converged = 1 or 2), else the first choice's status with
+ * res->energy = NaN.  ctx must hold a one-CSF excited state. */
+typedef struct {
+  double energy;          /* reported energy: mean, or the converged one      */
+  int32_t converged;      /* how many of the two converged (0, 1, 2)           */
+  int32_t reserved;
+  ascc_result first;      /* ansatz 0: beta = 1/(1+alpha)                      */
+  ascc_result second;     /* ansatz 1: beta = 1/(1-alpha), hole sign flipped   */
+} ascc_two_ansatz_result;
+ascc_status ascc_solve_two_ansatz(ascc_ctx* ctx, ascc_two_ansatz_result* res);
+
 /* Step-wise solve (Sec. III.B).  ascc_reset loads the zeroth-order guess
  * (Eq. TP-guess) and clears the DIIS history; ascc_iterate continues from the
  * current amplitudes and history for at most max_steps residual evaluations
@@ -242,24 +260,30 @@ ascc_status ascc_gemm_fp64_tc(int64_t M, int64_t N, int64_t K, double alpha,
                               const double* A, const double* B, double beta,
                               double* C, void* stream);
 
-/* The same product as ascc_gemm_split_bf16, for callers that cannot
- * allocate device memory when they need it: work recorded inside a CUDA
- * stream capture that must not gain allocation nodes, latency-critical loops
- * where an allocator call may synchronise the device, or processes whose
- * device memory has all been handed to another pool.  This entry point calls
- * no cudaMalloc/cudaFree and no allocating library routine: the BF16 operand
- * planes live in a fixed 32 MiB device array per GPU (held by every GPU that
- * loads the library until the process exits).  The paper has no counterpart;
- * it is a property of this library's tensor-core GEMM.
- *   Limit: 2 * level * (M + N) * ceil(K / 64) * 64 bytes must not exceed
- *   32 MiB; larger requests return ASCC_ERR_INVALID without touching the GPU.
+/* The same product as ascc_gemm_split_bf16 (same operand split, same K
+ * split, same FP32 partial sums), for callers that cannot allocate device
+ * memory when they need it: a process whose GPU memory has been handed in
+ * full to another pool (e.g. a framework's caching allocator that reserved
+ * the device up front) has none left for cudaMalloc, and code that must not
+ * enter the CUDA allocator (cudaMalloc / cudaFree may synchronise the whole
+ * device) cannot use the stream-ordered scratch of ascc_gemm_split_bf16.
+ * This entry point calls no cudaMalloc/cudaFree and no allocating library
+ * routine: the BF16 operand planes and the split-K partials live in a fixed
+ * 32 MiB device array per GPU (held by every GPU that loads the library
+ * until the process exits).  The paper has no counterpart; it is a property
+ * of this library's tensor-core GEMM.
+ *   Limit: 2 * level * (M + N) * ceil(K / 64) * 64 bytes (rounded up to 256)
+ *   plus 4 * z * M * N bytes of partials when K is split in z chunks (z as
+ *   ascc_gemm_split_bf16 chooses it) must not exceed 32 MiB; larger requests
+ *   return ASCC_ERR_INVALID without touching the GPU.
  *   The first call on a device looks up the array's device address (with
  *   that device current); make that first call before any stream capture.
- *   Each call first synchronises `stream` to report a timeout of the
- *   previous call (ASCC_ERR_TIMEOUT) and clears the flag.
+ *   Each call ends by reading its device timeout flag back to the host, so
+ *   it synchronises `stream` before returning; a bounded wait that gave up
+ *   returns ASCC_ERR_TIMEOUT.
  *   All calls share the array, which keeps the last call's contents: calls
- *   that overlap on the GPU (different streams, or issued while an earlier
- *   one is still running elsewhere) race on it. */
+ *   that overlap on the GPU (different streams, or threads calling at the
+ *   same time) race on it. */
 ascc_status ascc_gemm_split_bf16_noalloc(int64_t M, int64_t N, int64_t K,
                                          int32_t level, double alpha,
                                          const double* A, const double* B,
@@ -269,11 +293,12 @@ ascc_status ascc_gemm_split_bf16_noalloc(int64_t M, int64_t N, int64_t K,
  * A request server for streams of ASCC solves of different molecules and
  * states on one GPU.  Worker threads, each on its own CUDA stream, admit the
  * oldest queued request whose device footprint (ascc_footprint_bytes) fits
- * beside the requests already running, build its bare integrals once, solve
- * its states (ground state first if listed; a ground state takes the primary
- * pair of the request's first excitation for PLASCC) and free the memory, so
- * requests that arrive while others run are admitted as memory frees up and
- * their work overlaps on the device.  Times are seconds since creation. */
+ * beside the requests already running (a request at the head of the queue
+ * that does not fit yet does not hold back smaller ones), build its bare
+ * integrals once, solve its states (ground state first if listed; a ground
+ * state takes the primary pair of the request's first excitation for PLASCC)
+ * and free the memory, so requests that arrive while others run are admitted
+ * as memory frees up and their work overlaps on the device.  Times are seconds since creation. */
 typedef struct ascc_server ascc_server;
 typedef struct {
   int64_t request_id;
@@ -290,7 +315,10 @@ typedef struct {
 ascc_status ascc_server_create(ascc_server** out, size_t memory_budget,
                                int32_t max_active, const ascc_options* opt);
 /* Queues one request (host eps [o+v] and B [naux][n][n] are copied; the
- * arrival time is the submission time).  Thread-safe. */
+ * arrival time is the submission time).  Thread-safe.  A request whose
+ * ascc_footprint_bytes exceeds the server's memory budget is refused with
+ * ASCC_ERR_OOM (nothing is queued).  Workers admit the oldest queued request
+ * that fits beside the running ones. */
 ascc_status ascc_server_submit(ascc_server* srv, int32_t o, int32_t v,
                                int32_t naux, const double* eps, const double* B,
                                int32_t n_states, const ascc_excitation* states,
@@ -303,10 +331,26 @@ ascc_status ascc_server_results(ascc_server* srv, ascc_serve_result* out,
                                 int64_t capacity);
 void ascc_server_destroy(ascc_server* srv);
 
-/* Checkpoint / resume of the amplitudes (host buffers, FP64). */
+/* Amplitudes in and out (host buffers, FP64).  ascc_set_state replaces the
+ * amplitudes and keeps the DIIS history and counters as they are; for an
+ * exact resume use the checkpoint calls below. */
 ascc_status ascc_get_state(ascc_ctx* ctx, double* t1, double* t2, double* t3p);
 ascc_status ascc_set_state(ascc_ctx* ctx, const double* t1, const double* t2,
                            const double* t3p);
+
+/* Checkpoint of a solve in progress: the amplitudes, the DIIS history (the
+ * stored amplitude / error pairs in age order, their Gram matrix and slot
+ * ids), the iteration counters and, in mixed precision, the polishing phase
+ * with its residual correction.  A state loaded into a context created with
+ * the same molecule, excitation and options continues (ascc_iterate) exactly
+ * as the saved one would have: bitwise, since every kernel of the iteration
+ * is deterministic.  The blob is host memory of ascc_checkpoint_size bytes
+ * (it grows with the DIIS history, up to 2 diis_dim + 1 amplitude vectors);
+ * loading checks the sizes, excitation and options and returns
+ * ASCC_ERR_INVALID for a blob of another state. */
+ascc_status ascc_checkpoint_size(const ascc_ctx* ctx, int64_t* bytes);
+ascc_status ascc_checkpoint_save(ascc_ctx* ctx, void* buf, int64_t bytes);
+ascc_status ascc_checkpoint_load(ascc_ctx* ctx, const void* buf, int64_t bytes);
 
 /* Device bytes a context of this shape needs (bare integrals + state). */
 size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux,

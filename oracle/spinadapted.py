@@ -169,7 +169,7 @@ def residual(hbar, Bbar, o, t1, t2, linearize=False, hole=None, particle=None,
     R3 = None
     if t3_idx is not None and len(t3_idx):
         from . import t3slice
-        r1x, r2x, R3 = t3slice.residual(blk.F, blk.B, o, t2, t3_idx, t3_vals, hole, particle,
+        r1x, r2x, R3 = t3slice.residual(blk, t2, t3_idx, t3_vals, hole, particle,
                                         linearize=linearize)
         R1 += r1x; R2 += r2x
     return En, R1, R2, R3

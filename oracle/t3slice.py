@@ -29,8 +29,8 @@ v = 200:
 * R3' is produced in the same four blocks (output indices fixed likewise) and
   gathered at the slice positions.
 
-Integral blocks with three or four virtual indices and no fixed index are
-passed to numpy.einsum in density-fitted form, (pq|rs) = sum_P B[P,p,q] B[P,r,s].
+The integral blocks are those of spinadapted.Blocks, (pq|rs) = sum_P
+B[P,p,q] B[P,r,s] of the dressed DF factor, formed once per residual.
 
 Pinned to spinorb.residual (itself pinned to the brute-force projections) in
 tests/test_oracle_pins.py.
@@ -56,12 +56,14 @@ R2_T3 = [(1.0, 'ld,ijlabd->ijab', ['f:ov', 't3:ooovvv']),
 
 
 class Operands:
-    """Spatial arrays of one residual evaluation."""
+    """Spatial arrays of one residual evaluation: the Fock matrix, the integral
+    blocks (pq|rs) of spinadapted.Blocks (formed once and cached there) and the
+    slice blocks."""
 
-    def __init__(self, F, B, o, hole, part, t3_blocks):
-        self.F, self.B, self.o = F, B, o
+    def __init__(self, blk, hole, part, t3_blocks):
+        self.blk, self.F, self.o = blk, blk.F, blk.o
         self.h, self.p = hole, part
-        self.n = F.shape[0]
+        self.n = blk.F.shape[0]
         self.X = t3_blocks   # dict XA..XD
 
     def index(self, space, fixed):
@@ -71,6 +73,14 @@ class Operands:
         if fixed == 'p':
             return self.o + self.p
         return slice(0, self.o) if space == 'o' else slice(self.o, self.n)
+
+    def block_index(self, space, fixed):
+        """Index into an occupied or virtual block dimension."""
+        if fixed == 'h':
+            return self.h
+        if fixed == 'p':
+            return self.p
+        return slice(None)
 
 
 def slice_value(I, J, K, A, B, C):
@@ -187,27 +197,17 @@ def _contract(c, factors, fixed, out_name, out_labels, ops, t2, acc):
         return letters[x]
 
     for name, ls in factors:
-        if name in ('F', 'g'):
+        if name == 'F':
             idx = tuple(ops.index(_space(x), fixed.get(x)) for x in ls)
-            free = [x for x in ls if x not in fixed]
-            if name == 'F':
-                arrays.append(ops.F[idx])
-                subs.append(''.join(L(x) for x in free))
-                continue
-            nfree_v = sum(_space(x) == 'v' for x in free)
-            if nfree_v >= 3 and len(free) == 4:
-                # (pq|rs) = sum_P B[P,p,q] B[P,r,s], left factorised
-                arrays.append(ops.B[(slice(None),) + idx[:2]])
-                arrays.append(ops.B[(slice(None),) + idx[2:]])
-                subs.append('z' + ''.join(L(x) for x in ls[:2] if x not in fixed))
-                subs.append('z' + ''.join(L(x) for x in ls[2:] if x not in fixed))
-            else:
-                b1 = ops.B[(slice(None),) + idx[:2]]
-                b2 = ops.B[(slice(None),) + idx[2:]]
-                s1 = ''.join(L(x) for x in ls[:2] if x not in fixed)
-                s2 = ''.join(L(x) for x in ls[2:] if x not in fixed)
-                arrays.append(np.einsum(f'z{s1},z{s2}->{s1}{s2}', b1, b2))
-                subs.append(s1 + s2)
+            arrays.append(ops.F[idx])
+            subs.append(''.join(L(x) for x in ls if x not in fixed))
+            continue
+        if name == 'g':
+            # (pq|rs) block of the spaces of the four labels, fixed ones sliced
+            g = ops.blk.g(''.join(_space(x) for x in ls))
+            idx = tuple(ops.block_index(_space(x), fixed.get(x)) for x in ls)
+            arrays.append(g[idx])
+            subs.append(''.join(L(x) for x in ls if x not in fixed))
             continue
         if name == 't2':
             arr = t2
@@ -277,16 +277,17 @@ def gather(idx, R, o, v, hole, part):
     return out
 
 
-def residual(F, Bh, o, t2, t3_idx, t3_vals, hole, part, linearize=False):
+def residual(blk, t2, t3_idx, t3_vals, hole, part, linearize=False):
     """T3' contributions (R1, R2) and R3' at the slice positions.
 
-    F, Bh: Fock matrix and DF factor of H-hat = exp(-T1) H-bar exp(T1)
-    (spinadapted.dressed_blocks); t2 spin-adapted doubles; (t3_idx, t3_vals)
-    the slice.  linearize=True drops T2^M T2^M and T2^M T3' from R3'.
+    blk: the blocks of H-hat = exp(-T1) H-bar exp(T1) (spinadapted.Blocks:
+    Fock matrix and cached (pq|rs) blocks); t2 spin-adapted doubles;
+    (t3_idx, t3_vals) the slice.  linearize=True drops T2^M T2^M and
+    T2^M T3' from R3'.
     """
-    v = t2.shape[2]
+    o, v = blk.o, t2.shape[2]
     X = blocks_from_slice(t3_idx, t3_vals, o, v, hole, part)
-    ops = Operands(F, Bh, o, hole, part, X)
+    ops = Operands(blk, hole, part, X)
     acc = {'r1': np.zeros((o, v)), 'r2': np.zeros((o, o, v, v)),
            'RA': np.zeros((o, v, v)), 'RB': np.zeros((o, v, v)),
            'RC': np.zeros((o, o, v)), 'RD': np.zeros((o, o, v))}

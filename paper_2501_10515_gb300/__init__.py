@@ -6,11 +6,9 @@ not load the library; `load()` (called by the first Context) does, and fails
 loudly when libascc.so has not been built.
 """
 from .binding import (ASCC_FP64, ASCC_FP64_TC, ASCC_MIXED_BF16, AsccError, Context, Excitation,
-                      Server, Options, Profile, Result, default_options, gemm_fp64_tc,
-                      gemm_split_bf16,
-                      gemm_split_bf16_noalloc, load, two_ansatz_average,
-                      symbols)
+                      Server, Options, Profile, Result, TwoAnsatzResult, default_options,
+                      gemm_fp64_tc, gemm_split_bf16, gemm_split_bf16_noalloc, load, symbols)
 
 __all__ = ["ASCC_FP64", "ASCC_FP64_TC", "ASCC_MIXED_BF16", "AsccError", "Context", "Excitation",
            "Server", "Options", "Profile", "Result", "default_options", "gemm_fp64_tc",
-           "gemm_split_bf16", "gemm_split_bf16_noalloc", "load", "two_ansatz_average", "symbols"]
+           "gemm_split_bf16", "gemm_split_bf16_noalloc", "load", "symbols", "TwoAnsatzResult"]

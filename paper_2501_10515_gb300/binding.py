@@ -39,6 +39,11 @@ class Result(C.Structure):
                 ("fp64_evaluations", C.c_int32)]
 
 
+class TwoAnsatzResult(C.Structure):
+    _fields_ = [("energy", C.c_double), ("converged", C.c_int32), ("reserved", C.c_int32),
+                ("first", Result), ("second", Result)]
+
+
 class Profile(C.Structure):
     _fields_ = [("ladder_ms", C.c_double), ("ladder_flops", C.c_double),
                 ("ladder_launches", C.c_int64), ("launches", C.c_int64),
@@ -82,6 +87,10 @@ def load():
         "ascc_residual_device": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "ascc_energy": (C.c_int, [vp, dp, dp, dp]),
         "ascc_solve": (C.c_int, [vp, P(Result)]),
+        "ascc_solve_two_ansatz": (C.c_int, [vp, P(TwoAnsatzResult)]),
+        "ascc_checkpoint_size": (C.c_int, [vp, P(C.c_int64)]),
+        "ascc_checkpoint_save": (C.c_int, [vp, vp, C.c_int64]),
+        "ascc_checkpoint_load": (C.c_int, [vp, vp, C.c_int64]),
         "ascc_reset": (C.c_int, [vp]),
         "ascc_iterate": (C.c_int, [vp, C.c_int32, P(Result)]),
         "ascc_set_profiling": (C.c_int, [vp, C.c_int32]),
@@ -153,13 +162,6 @@ def gemm_split_bf16_noalloc(A, B, out, level, alpha=1.0, beta=0.0, stream=None):
     assert tuple(out.shape) == (M, N) and B.shape[1] == K
     _check(load().ascc_gemm_split_bf16_noalloc(M, N, K, level, alpha, C_void(A), C_void(B), beta,
                                                C_void(out), C.c_void_p(stream) if stream else None))
-
-
-def two_ansatz_average(e_small, status_small, e_large, status_large):
-    """Reported energy of Sec. II.D: the mean of the two ansatz energies, or the one
-    that converged when the other did not (Sec. III.A); None if neither did."""
-    ok = [e for e, st in ((e_small, status_small), (e_large, status_large)) if st == 0]
-    return sum(ok) / len(ok) if ok else None
 
 
 def C_void(x):
@@ -261,6 +263,26 @@ class Context:
         elif st not in (0, 4, 5):
             _check(st)
         return res
+
+    def solve_two_ansatz(self) -> TwoAnsatzResult:
+        """Both ansatz choices of Sec. II.D and the reported energy (ascc_solve_two_ansatz)."""
+        res = TwoAnsatzResult()
+        st = load().ascc_solve_two_ansatz(self._h, C.byref(res))
+        if st not in (0, 4, 5):
+            _check(st)
+        return res
+
+    def checkpoint(self) -> bytes:
+        """The iteration state (amplitudes, DIIS history, counters) as a host blob."""
+        n = C.c_int64()
+        _check(load().ascc_checkpoint_size(self._h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(load().ascc_checkpoint_save(self._h, buf, n.value))
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(load().ascc_checkpoint_load(self._h, buf, len(blob)))
 
     def reset(self):
         _check(load().ascc_reset(self._h))

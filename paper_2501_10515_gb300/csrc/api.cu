@@ -8,6 +8,7 @@
 #include "gemm_oz.h"
 #include "gemm_tc.h"
 #include "kernels.h"
+#include "t3p.h"
 
 using namespace ascc;
 
@@ -15,10 +16,14 @@ struct ascc_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::unique_ptr<State> state;
+  std::unique_ptr<State> partner;  // the other ansatz of Sec. II.D, built on first use
+  ascc_excitation exc{};
+  bool has_exc = false;
   int64_t launches0 = 0;
   double flops0 = 0.0;
   ~ascc_ctx() {
     if (stream) cudaStreamSynchronize(stream);
+    partner.reset();
     state.reset();
     if (stream) cudaStreamSynchronize(stream);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -112,6 +117,10 @@ ascc_status make_ctx(ascc_ctx** out, std::shared_ptr<Molecule> mol, const ascc_e
   Options o = to_options(opt);
   if (o.pl_hole >= mol->o || o.pl_particle >= mol->v) throw Error(ASCC_ERR_INVALID, "pl labels");
   ctx->state = std::make_unique<State>(std::move(mol), hole, particle, beta, o, stream, xsign);
+  if (exc) {
+    ctx->exc = *exc;
+    ctx->has_exc = true;
+  }
   ASCC_CUDA(cudaStreamSynchronize(stream));
   *out = ctx.release();
   return ASCC_OK;
@@ -271,6 +280,68 @@ ascc_status ascc_solve(ascc_ctx* ctx, ascc_result* res) {
   });
 }
 
+ascc_status ascc_solve_two_ansatz(ascc_ctx* ctx, ascc_two_ansatz_result* res) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && res, "null argument");
+    ASCC_REQUIRE(ctx->has_exc && ctx->exc.n_csf == 1, "the two ansatz choices need an excited state");
+    State& S = *ctx->state;
+    if (!ctx->partner) {
+      // the same state with the hole orbital's sign flipped: S -> -S and
+      // alpha -> -alpha (beta' = 1 / (1 - alpha) for the first choice's
+      // beta = 1 / (1 + alpha))
+      ascc_excitation e = ctx->exc;
+      e.ansatz = 1 - e.ansatz;
+      e.beta = 0.0;
+      int hole, particle;
+      double beta, xsign;
+      check_exc(&e, S.molecule()->o, S.molecule()->v, hole, particle, beta, xsign);
+      ctx->partner = std::make_unique<State>(S.molecule(), hole, particle, beta, S.options(),
+                                             ctx->stream, xsign);
+    }
+    State* first = ctx->exc.ansatz == 0 ? ctx->state.get() : ctx->partner.get();
+    State* second = ctx->exc.ansatz == 0 ? ctx->partner.get() : ctx->state.get();
+    std::memset(res, 0, sizeof(*res));
+    first->solve(&res->first);
+    second->solve(&res->second);
+    const bool a = res->first.status == ASCC_OK, b = res->second.status == ASCC_OK;
+    res->converged = (int32_t)a + (int32_t)b;
+    if (a && b) {
+      res->energy = 0.5 * (res->first.energy + res->second.energy);
+    } else if (a || b) {
+      res->energy = a ? res->first.energy : res->second.energy;
+    } else {
+      res->energy = NAN;
+      g_err = "neither ansatz converged";
+      return (ascc_status)res->first.status;
+    }
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_checkpoint_size(const ascc_ctx* ctx, int64_t* bytes) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && bytes, "null argument");
+    *bytes = ctx->state->checkpoint_bytes();
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_checkpoint_save(ascc_ctx* ctx, void* buf, int64_t bytes) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && buf, "null argument");
+    ctx->state->checkpoint_save(buf, bytes);
+    return ASCC_OK;
+  });
+}
+
+ascc_status ascc_checkpoint_load(ascc_ctx* ctx, const void* buf, int64_t bytes) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(ctx && ctx->state && buf, "null argument");
+    ctx->state->checkpoint_load(buf, bytes);
+    return ASCC_OK;
+  });
+}
+
 ascc_status ascc_reset(ascc_ctx* ctx) {
   return guard([&]() -> ascc_status {
     ASCC_REQUIRE(ctx && ctx->state, "null argument");
@@ -427,6 +498,13 @@ size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux, const ascc_optio
   // digit planes of the ladder's t operand, the integer workspace, and the
   // planes of the largest generic contraction (o v x o v x o v)
   if (digits) state += 2.0 * 6.0 * O * O * kq + 8.0 * o2v2 + 2.0 * 6.0 * 2.0 * o2v2 + 8.0 * o2v2;
+  if (opt && opt->triples) {
+    // T3' blocks of t3 and R3', their workspace (intermediates of the
+    // generated program, sized for the worst primary pair) and the t2 - t2^T
+    // operands
+    T3pProgram prog(o, v, naux, 0, 0);
+    state += 8.0 * (2.0 * prog.block_elements() + prog.workspace_elements() + 2.0 * o2v2);
+  }
   return (size_t)((mol + state) * 1.1);
 }
 

@@ -210,6 +210,17 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
     Bp = Btmp.p();
   }
   const int64_t lda = ta ? Ms : Ks, ldb = tb ? Ks : Ns;
+  if (Ms == 1 && Ns > 1 && nb == 1 && Ks > 0) {
+    // vector-matrix product: a matrix-vector product with B as the matrix
+    if (sp.c == cl) {
+      k::gemv_f64(s_, !tb, Ns, Ks, alpha, Bp, ldb, Ap, beta, C.p);
+    } else {
+      OT Ct(shape_of(cl), s_);
+      k::gemv_f64(s_, !tb, Ns, Ks, 1.0, Bp, ldb, Ap, 0.0, Ct.p());
+      perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
+    }
+    return;
+  }
   if (Ns == 1 && nb == 1 && Ks > 0) {
     // matrix-vector product: memory-bound, FP64 on every path
     if (sp.c == cl) {
@@ -417,6 +428,7 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
   scal_.make({64}, s);
   work_.make({(int64_t)32 * 4 * 152 + 64}, s);
   coef_.make({32}, s);
+  gram_.make({32 * 32}, s);
   const int o = o_, v = v_, n = n_, P = naux_;
   L_.make({n, n}, s); R_.make({n, n}, s);
   {
@@ -1084,49 +1096,6 @@ double State::reference_energy() {
   return e;
 }
 
-namespace {
-// DIIS coefficients: bordered system [[G/s + 1e-12 I, 1], [1, 0]] [c; l] = [0; 1]
-// with s = max diag G, Gaussian elimination with partial pivoting.
-bool bordered_solve(const std::vector<double>& G, int m, std::vector<double>& c) {
-  double scale = 0.0;
-  for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(G[i * m + i]));
-  if (!(scale > 0.0) || !std::isfinite(scale)) return false;
-  const int nn = m + 1;
-  std::vector<double> A((size_t)nn * nn, 0.0), b(nn, 0.0);
-  for (int i = 0; i < m; ++i) {
-    for (int j = 0; j < m; ++j) A[i * nn + j] = G[i * m + j] / scale + (i == j ? 1e-12 : 0.0);
-    A[i * nn + m] = 1.0;
-    A[m * nn + i] = 1.0;
-  }
-  b[m] = 1.0;
-  for (int col = 0; col < nn; ++col) {
-    int piv = col;
-    for (int r = col + 1; r < nn; ++r)
-      if (std::fabs(A[r * nn + col]) > std::fabs(A[piv * nn + col])) piv = r;
-    if (std::fabs(A[piv * nn + col]) < 1e-300) return false;
-    if (piv != col) {
-      for (int j = 0; j < nn; ++j) std::swap(A[col * nn + j], A[piv * nn + j]);
-      std::swap(b[col], b[piv]);
-    }
-    for (int r = col + 1; r < nn; ++r) {
-      const double f = A[r * nn + col] / A[col * nn + col];
-      for (int j = col; j < nn; ++j) A[r * nn + j] -= f * A[col * nn + j];
-      b[r] -= f * b[col];
-    }
-  }
-  std::vector<double> x(nn, 0.0);
-  for (int r = nn - 1; r >= 0; --r) {
-    double acc = b[r];
-    for (int j = r + 1; j < nn; ++j) acc -= A[r * nn + j] * x[j];
-    x[r] = acc / A[r * nn + r];
-  }
-  for (double xi : x)
-    if (!std::isfinite(xi)) return false;
-  c.assign(x.begin(), x.begin() + m);
-  return true;
-}
-}  // namespace
-
 void State::reset() {
   const int64_t N = namp();
   std::vector<double> guess;
@@ -1136,7 +1105,8 @@ void State::reset() {
   k::fill(s_, hist_t_.p(), 0.0, (int64_t)m * N);
   k::fill(s_, hist_e_.p(), 0.0, (int64_t)m * N);
   slots_.clear();
-  gram_.assign((size_t)m * m, 0.0);
+  k::fill(s_, gram_.p(), 0.0, (int64_t)m * m);
+  k::fill(s_, scal_.p(), 0.0, 64);
   next_slot_ = 0;
   iter_ = 0;
   iter_low_ = 0;
@@ -1185,9 +1155,11 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
       }
     }
     k::maxabs(s_, r_.p(), N, scal_.p() + 1, work_.p());
-    double h2[2];
+    // the one host readback of an iteration: E, max|R|, the DIIS failure flag
+    // of the previous step and the device timeout code
+    double h2[8];
     int kerr = 0;
-    ASCC_CUDA(cudaMemcpyAsync(h2, scal_.p(), 2 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+    ASCC_CUDA(cudaMemcpyAsync(h2, scal_.p(), 8 * sizeof(double), cudaMemcpyDeviceToHost, s_));
     ASCC_CUDA(cudaMemcpyAsync(&kerr, err_.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s_));
     ASCC_CUDA(cudaStreamSynchronize(s_));
     if (kerr != 0)
@@ -1195,6 +1167,11 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
                                         std::to_string(kerr) + ")");
     e_last_ = h2[0];
     r_last_ = h2[1];
+    if (h2[6] != 0.0) {
+      // the previous extrapolation failed: keep only the newest pair
+      if (!slots_.empty()) slots_.assign(1, slots_.back());
+      k::fill(s_, scal_.p() + 6, 0.0, 1);
+    }
     const int it = iter_++;
     if (lev == 2) ++iter_low_;
     if (lev == 2 && std::isfinite(r_last_) && r_last_ <= opt_.polish_tol) {
@@ -1248,32 +1225,18 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
               n3() ? t3idx_.as<int32_t>() : nullptr, n3());
     k::jacobi_pairs(s_, tn, en, t_.p(), r_.p(), eps_eff_.p(), F_.p(), o_, v_, hole_, particle_);
     k::dot_rows(s_, en, hist_e_.p(), N, m, N, scal_.p() + 32, work_.p());
-    std::vector<double> row(m);
-    ASCC_CUDA(cudaMemcpyAsync(row.data(), scal_.p() + 32, m * sizeof(double),
-                              cudaMemcpyDeviceToHost, s_));
-    ASCC_CUDA(cudaStreamSynchronize(s_));
-    for (int q : slots_) {
-      gram_[slot * m + q] = row[q];
-      gram_[q * m + slot] = row[q];
-    }
-    bool extrapolated = false;
-    if ((int)slots_.size() >= opt_.diis_start) {
-      const int cnt = (int)slots_.size();
-      std::vector<double> Gs(cnt * cnt), c;
-      for (int a = 0; a < cnt; ++a)
-        for (int b = 0; b < cnt; ++b) Gs[a * cnt + b] = gram_[slots_[a] * m + slots_[b]];
-      if (bordered_solve(Gs, cnt, c)) {
-        std::vector<double> cs(m, 0.0);
-        for (int a = 0; a < cnt; ++a) cs[slots_[a]] = c[a];
-        ASCC_CUDA(cudaMemcpyAsync(coef_.p(), cs.data(), m * sizeof(double),
-                                  cudaMemcpyHostToDevice, s_));
-        k::lincomb(s_, t_.p(), hist_t_.p(), N, coef_.p(), m, N);
-        extrapolated = true;
-      } else {
-        slots_.assign(1, slot);
-      }
-    }
-    if (!extrapolated) k::axpby(s_, t_.p(), tn, 1.0, 0.0, N);
+    // Gram row, bordered solve and extrapolation stay on the device; a failed
+    // solve leaves t = tn and is seen at the next readback
+    k::DiisArgs da{};
+    da.m = m;
+    da.cnt = (int)slots_.size();
+    da.solve = da.cnt >= opt_.diis_start;
+    for (int q = 0; q < da.cnt; ++q) da.slot[q] = slots_[q];
+    k::diis(s_, gram_.p(), scal_.p() + 32, da, coef_.p(), scal_.p() + 6);
+    if (da.solve)
+      k::lincomb(s_, t_.p(), hist_t_.p(), N, coef_.p(), m, N);
+    else
+      k::axpby(s_, t_.p(), tn, 1.0, 0.0, N);
   }
   if (res) {
     res->energy = e_last_;
@@ -1285,6 +1248,114 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     res->e_ref = 0.0;
   }
   return done_ ? status_ : ASCC_ERR_NOT_CONVERGED;
+}
+
+namespace {
+constexpr int64_t kCkptMagic = 0x5450434b43435341LL;  // "ASCCKCPT"
+constexpr int kCkptHeader = 24;
+}  // namespace
+
+int64_t State::checkpoint_bytes() const {
+  const int64_t N = namp(), m = opt_.diis_dim, cnt = (int64_t)slots_.size();
+  int64_t words = kCkptHeader + cnt + 3 + 8 + m * m + N + 2 * cnt * N;
+  if (opt_.precision == ASCC_MIXED_BF16) words += N;
+  return 8 * words;
+}
+
+void State::checkpoint_save(void* buf, int64_t bytes) {
+  ASCC_REQUIRE(buf && bytes >= checkpoint_bytes(), "checkpoint buffer too small");
+  const int64_t N = namp(), m = opt_.diis_dim, cnt = (int64_t)slots_.size();
+  auto* w = static_cast<int64_t*>(buf);
+  const int64_t flags = (int64_t)have_prev_ | (int64_t)done_ << 1 | (int64_t)polish_ << 2 |
+                        (int64_t)need_refresh_ << 3 | (int64_t)have_corr_ << 4 |
+                        (int64_t)fallback_ << 5;
+  const int64_t head[kCkptHeader] = {kCkptMagic, 1, o_, v_, n3(), opt_.precision, opt_.linearize,
+                                     m, cnt, next_slot_, iter_, iter_low_, fp64_evals_,
+                                     polish_its_, flags, (int64_t)status_, hole_, particle_,
+                                     lh_, lp_, (int64_t)(xsign_ < 0), 0, 0, 0};
+  std::memcpy(w, head, sizeof(head));
+  for (int64_t q = 0; q < cnt; ++q) w[kCkptHeader + q] = slots_[q];
+  auto* d = reinterpret_cast<double*>(w + kCkptHeader + cnt);
+  d[0] = e_prev_;
+  d[1] = e_last_;
+  d[2] = r_last_;
+  d += 3;
+  ASCC_CUDA(cudaMemcpyAsync(d, scal_.p(), 8 * sizeof(double), cudaMemcpyDeviceToHost, s_));
+  d += 8;
+  ASCC_CUDA(cudaMemcpyAsync(d, gram_.p(), sizeof(double) * m * m, cudaMemcpyDeviceToHost, s_));
+  d += m * m;
+  ASCC_CUDA(cudaMemcpyAsync(d, t_.p(), sizeof(double) * N, cudaMemcpyDeviceToHost, s_));
+  d += N;
+  for (int64_t q = 0; q < cnt; ++q) {
+    const int64_t sl = slots_[q];
+    ASCC_CUDA(cudaMemcpyAsync(d, hist_t_.p() + sl * N, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                              s_));
+    d += N;
+    ASCC_CUDA(cudaMemcpyAsync(d, hist_e_.p() + sl * N, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                              s_));
+    d += N;
+  }
+  if (opt_.precision == ASCC_MIXED_BF16)
+    ASCC_CUDA(cudaMemcpyAsync(d, corr_.p(), sizeof(double) * N, cudaMemcpyDeviceToHost, s_));
+  ASCC_CUDA(cudaStreamSynchronize(s_));
+}
+
+void State::checkpoint_load(const void* buf, int64_t bytes) {
+  ASCC_REQUIRE(buf && bytes >= 8 * kCkptHeader, "checkpoint buffer too small");
+  const auto* w = static_cast<const int64_t*>(buf);
+  const int64_t N = namp(), m = opt_.diis_dim, cnt = w[8];
+  ASCC_REQUIRE(w[0] == kCkptMagic && w[1] == 1, "not a checkpoint of this library");
+  ASCC_REQUIRE(w[2] == o_ && w[3] == v_ && w[4] == n3() && w[5] == opt_.precision &&
+                   w[6] == opt_.linearize && w[7] == m && w[16] == hole_ &&
+                   w[17] == particle_ && w[18] == lh_ && w[19] == lp_ &&
+                   w[20] == (int64_t)(xsign_ < 0),
+               "checkpoint of a different state or options");
+  ASCC_REQUIRE(cnt >= 0 && cnt <= m, "checkpoint: bad DIIS history length");
+  int64_t words = kCkptHeader + cnt + 3 + 8 + m * m + N + 2 * cnt * N;
+  if (opt_.precision == ASCC_MIXED_BF16) words += N;
+  ASCC_REQUIRE(bytes >= 8 * words, "checkpoint buffer too small");
+  slots_.clear();
+  for (int64_t q = 0; q < cnt; ++q) {
+    const int64_t sl = w[kCkptHeader + q];
+    ASCC_REQUIRE(sl >= 0 && sl < m, "checkpoint: bad DIIS slot");
+    slots_.push_back((int)sl);
+  }
+  next_slot_ = (int)w[9];
+  iter_ = (int)w[10];
+  iter_low_ = (int)w[11];
+  fp64_evals_ = (int)w[12];
+  polish_its_ = (int)w[13];
+  const int64_t flags = w[14];
+  have_prev_ = flags & 1;
+  done_ = (flags >> 1) & 1;
+  polish_ = (flags >> 2) & 1;
+  need_refresh_ = (flags >> 3) & 1;
+  have_corr_ = (flags >> 4) & 1;
+  fallback_ = (flags >> 5) & 1;
+  status_ = (ascc_status)w[15];
+  const auto* d = reinterpret_cast<const double*>(w + kCkptHeader + cnt);
+  e_prev_ = d[0];
+  e_last_ = d[1];
+  r_last_ = d[2];
+  d += 3;
+  ASCC_CUDA(cudaMemcpyAsync(scal_.p(), d, 8 * sizeof(double), cudaMemcpyHostToDevice, s_));
+  d += 8;
+  ASCC_CUDA(cudaMemcpyAsync(gram_.p(), d, sizeof(double) * m * m, cudaMemcpyHostToDevice, s_));
+  d += m * m;
+  ASCC_CUDA(cudaMemcpyAsync(t_.p(), d, sizeof(double) * N, cudaMemcpyHostToDevice, s_));
+  d += N;
+  for (int64_t q = 0; q < cnt; ++q) {
+    const int64_t sl = slots_[q];
+    ASCC_CUDA(cudaMemcpyAsync(hist_t_.p() + sl * N, d, sizeof(double) * N, cudaMemcpyHostToDevice,
+                              s_));
+    d += N;
+    ASCC_CUDA(cudaMemcpyAsync(hist_e_.p() + sl * N, d, sizeof(double) * N, cudaMemcpyHostToDevice,
+                              s_));
+    d += N;
+  }
+  if (opt_.precision == ASCC_MIXED_BF16)
+    ASCC_CUDA(cudaMemcpyAsync(corr_.p(), d, sizeof(double) * N, cudaMemcpyHostToDevice, s_));
+  ASCC_CUDA(cudaStreamSynchronize(s_));
 }
 
 ascc_status State::solve(ascc_result* res) {

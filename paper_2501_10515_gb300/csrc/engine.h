@@ -32,6 +32,8 @@ class Einsum {
     min_flops_ = min_flops;
   }
   int level() const { return level_; }
+  int* err() const { return err_; }
+  double min_flops() const { return min_flops_; }
   // Scratch of the tensor-core path, grown on demand and reused by every call
   // on this stream (calls on one stream never overlap).
   void* scratch(int which, size_t bytes) const;
@@ -115,6 +117,13 @@ class State {
                   err_.as<int>(), tc_min_flops_);
   }
   ascc_status solve(ascc_result* res);
+  // Checkpoint of the iteration state: amplitudes, the DIIS history (slot
+  // ids in age order, their (t, e) pairs and Gram matrix), the iteration
+  // counters and the mixed-precision phase with its correction, so that a
+  // loaded state continues exactly as the saved one would have.
+  int64_t checkpoint_bytes() const;
+  void checkpoint_save(void* buf, int64_t bytes);
+  void checkpoint_load(const void* buf, int64_t bytes);
   // Iteration control: reset() loads the zeroth-order guess and clears the
   // DIIS history; iterate() runs up to max_steps residual evaluations from
   // the current amplitudes and history (Sec. III.B).
@@ -147,8 +156,7 @@ class State {
   std::shared_ptr<Molecule> mol_;
   Options opt_;
   // iteration state
-  std::vector<int> slots_;
-  std::vector<double> gram_;
+  std::vector<int> slots_;  // active DIIS slots, oldest first
   int next_slot_ = 0, iter_ = 0;
   bool have_prev_ = false, done_ = false;
   double e_prev_ = 0.0, e_last_ = 0.0, r_last_ = 0.0;
@@ -175,7 +183,7 @@ class State {
   // per-state constant integrals of the ladder corrections
   OT Gh1, Gh2, Gh3, GooP;
   // amplitudes, residual, DIIS
-  OT t_, r_, hist_t_, hist_e_, scal_, work_, coef_, eps_eff_;
+  OT t_, r_, hist_t_, hist_e_, scal_, work_, coef_, eps_eff_, gram_;
   DevBuf err_;           // int: device-side timeout codes of the tensor-core GEMM
   bool polish_ = false, need_refresh_ = false, have_corr_ = false;
   // mixed precision: the defect-corrected polishing gave way to FP64-class

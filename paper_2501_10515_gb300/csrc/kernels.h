@@ -38,6 +38,15 @@ void dot_rows(cudaStream_t s, const double* x, const double* Y, int64_t ldy,
               int rows, int64_t n, double* out, double* work);  // out[r] = x . Y[r]
 void maxabs(cudaStream_t s, const double* x, int64_t n, double* out, double* work);
 
+// DIIS step on the device (Sec. III.B): slot[cnt-1] is the newest slot, the
+// others the active history in age order; see diis_kernel.
+struct DiisArgs {
+  int m, cnt, solve;
+  int slot[32];
+};
+void diis(cudaStream_t s, double* gram, const double* row, const DiisArgs& a, double* coef,
+          double* fail);
+
 // y = sum_k c[k] * X[k]  (c in device memory)
 void lincomb(cudaStream_t s, double* y, const double* X, int64_t ldx,
              const double* c, int m, int64_t n);

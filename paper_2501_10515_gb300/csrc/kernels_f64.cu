@@ -318,6 +318,38 @@ __global__ void gemv_cols_kernel(int64_t M, int64_t K, double alpha, const doubl
   }
 }
 
+// Transposed matrix-vector product, first pass: block (x, y) sums rows
+// [y kchunk, (y+1) kchunk) of A (K x M, row stride lda) times x for 32
+// consecutive columns (one per lane, coalesced), 8 rows at a time, into
+// part[y][m]; gemv_t_reduce adds the chunks in a fixed order.
+__global__ void gemv_t_partial(int64_t M, int64_t K, const double* __restrict__ A, int64_t lda,
+                               const double* __restrict__ x, int64_t kchunk,
+                               double* __restrict__ part) {
+  __shared__ double sh[8][33];
+  const int64_t m = blockIdx.x * 32 + threadIdx.x;
+  const int64_t k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
+  double acc = 0.0;
+  if (m < M)
+    for (int64_t k = k0 + threadIdx.y; k < k1; k += 8) acc = fma(A[k * lda + m], x[k], acc);
+  sh[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && m < M) {
+    double t = 0.0;
+    for (int r = 0; r < 8; ++r) t += sh[r][threadIdx.x];
+    part[blockIdx.y * M + m] = t;
+  }
+}
+
+__global__ void gemv_t_reduce(int64_t M, int nchunk, const double* __restrict__ part,
+                              double alpha, double beta, double* __restrict__ y) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < nchunk; ++c) t += part[c * M + m];
+    y[m] = (beta == 0.0) ? alpha * t : fma(alpha, t, beta * y[m]);
+  }
+}
+
 __global__ void fill_kernel(double* x, double v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -412,6 +444,80 @@ __global__ void lincomb_kernel(double* y, const double* X, int64_t ldx, const do
     double acc = 0.0;
     for (int kk = 0; kk < m; ++kk) acc = fma(c[kk], X[kk * ldx + i], acc);
     y[i] = acc;
+  }
+}
+
+// DIIS on the device (one thread; m <= 32).  Stores the new Gram row of slot
+// a.slot[a.cnt-1] (row[q] = e_new . e_q for every slot q) into gram[m][m];
+// with a.solve set, solves the bordered system
+//   [[G/s + 1e-12 I, 1], [1, 0]] [c; l] = [0; 1],  s = max |diag G|,
+// over the active slots (in a.slot order) by Gaussian elimination with
+// partial pivoting and writes c to coef[slot] (0 for inactive slots).  A
+// degenerate or non-finite system sets *fail = 1 and coef = e_new.
+__global__ void diis_kernel(double* gram, const double* row, DiisArgs a, double* coef,
+                            double* fail) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = a.m, cnt = a.cnt, nw = a.slot[cnt - 1];
+  for (int q = 0; q < cnt; ++q) {
+    const int sq = a.slot[q];
+    gram[nw * m + sq] = row[sq];
+    gram[sq * m + nw] = row[sq];
+  }
+  if (!a.solve) return;
+  for (int q = 0; q < m; ++q) coef[q] = 0.0;
+  double A[33 * 33], b[33], x[33];
+  const int nn = cnt + 1;
+  double scale = 0.0;
+  for (int i = 0; i < cnt; ++i) scale = fmax(scale, fabs(gram[a.slot[i] * m + a.slot[i]]));
+  bool ok = scale > 0.0 && isfinite(scale);
+  if (ok) {
+    for (int i = 0; i < nn * nn; ++i) A[i] = 0.0;
+    for (int i = 0; i < nn; ++i) b[i] = 0.0;
+    for (int i = 0; i < cnt; ++i) {
+      for (int j = 0; j < cnt; ++j)
+        A[i * nn + j] = gram[a.slot[i] * m + a.slot[j]] / scale + (i == j ? 1e-12 : 0.0);
+      A[i * nn + cnt] = 1.0;
+      A[cnt * nn + i] = 1.0;
+    }
+    b[cnt] = 1.0;
+    for (int col = 0; col < nn && ok; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < nn; ++r)
+        if (fabs(A[r * nn + col]) > fabs(A[piv * nn + col])) piv = r;
+      if (fabs(A[piv * nn + col]) < 1e-300) {
+        ok = false;
+        break;
+      }
+      if (piv != col) {
+        for (int j = 0; j < nn; ++j) {
+          const double t = A[col * nn + j];
+          A[col * nn + j] = A[piv * nn + j];
+          A[piv * nn + j] = t;
+        }
+        const double t = b[col];
+        b[col] = b[piv];
+        b[piv] = t;
+      }
+      for (int r = col + 1; r < nn; ++r) {
+        const double f = A[r * nn + col] / A[col * nn + col];
+        for (int j = col; j < nn; ++j) A[r * nn + j] = __dsub_rn(A[r * nn + j], __dmul_rn(f, A[col * nn + j]));
+        b[r] = __dsub_rn(b[r], __dmul_rn(f, b[col]));
+      }
+    }
+    if (ok) {
+      for (int r = nn - 1; r >= 0; --r) {
+        double acc = b[r];
+        for (int j = r + 1; j < nn; ++j) acc = __dsub_rn(acc, __dmul_rn(A[r * nn + j], x[j]));
+        x[r] = acc / A[r * nn + r];
+      }
+      for (int i = 0; i < nn; ++i) ok = ok && isfinite(x[i]);
+    }
+  }
+  if (ok) {
+    for (int i = 0; i < cnt; ++i) coef[a.slot[i]] = x[i];
+  } else {
+    coef[nw] = 1.0;
+    *fail = 1.0;
   }
 }
 
@@ -822,6 +928,23 @@ void axis_matrix(cudaStream_t s, bool fp32, double* C, const double* A, const do
 void gemv_f64(cudaStream_t s, bool ta, int64_t M, int64_t K, double alpha, const double* A,
               int64_t lda, const double* x, double beta, double* y) {
   if (M <= 0) return;
+  if (ta && K > 64) {
+    // K split over the grid so that a long, narrow product still fills the GPU
+    const int64_t gx = (M + 31) / 32;
+    int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>((152 * 8 + gx - 1) / gx, (K + 63) / 64));
+    nchunk = std::min<int64_t>(nchunk, 4096);
+    const int64_t kchunk = (K + nchunk - 1) / nchunk;
+    nchunk = (K + kchunk - 1) / kchunk;
+    double* part = nullptr;
+    ASCC_CUDA(cudaMallocAsync(&part, sizeof(double) * (size_t)(nchunk * M), s));
+    gemv_t_partial<<<dim3((unsigned)gx, (unsigned)nchunk), dim3(32, 8), 0, s>>>(M, K, A, lda, x,
+                                                                               kchunk, part);
+    gemv_t_reduce<<<grid_for(M), 256, 0, s>>>(M, (int)nchunk, part, alpha, beta, y);
+    ASCC_CUDA(cudaFreeAsync(part, s));
+    count_launch(2);
+    check_launch("gemv_t");
+    return;
+  }
   if (ta)
     gemv_cols_kernel<<<grid_for(M), 256, 0, s>>>(M, K, alpha, A, lda, x, beta, y);
   else
@@ -860,6 +983,13 @@ void maxabs(cudaStream_t s, const double* x, int64_t n, double* out, double* wor
   max_partials<<<1, RB, 0, s>>>(work, RG, out);
   count_launch(2);
   check_launch("maxabs");
+}
+
+void diis(cudaStream_t s, double* gram, const double* row, const DiisArgs& a, double* coef,
+          double* fail) {
+  diis_kernel<<<1, 32, 0, s>>>(gram, row, a, coef, fail);
+  count_launch();
+  check_launch("diis");
 }
 
 void lincomb(cudaStream_t s, double* y, const double* X, int64_t ldx, const double* c, int m,

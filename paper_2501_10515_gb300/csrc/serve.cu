@@ -71,6 +71,7 @@ struct ascc_server {
     threads_.clear();
   }
 
+  size_t budget() const { return budget_; }
   std::vector<ascc_serve_result> results() {
     std::lock_guard<std::mutex> lk(mu_);
     return results_;
@@ -89,18 +90,19 @@ struct ascc_server {
       Request r;
       {
         std::unique_lock<std::mutex> lk(mu_);
-        // admission: the oldest request whose footprint fits beside the running ones
-        cv_.wait(lk, [&] {
-          if (stopping_) return true;
-          if (queue_.empty()) return false;
-          const size_t fp = queue_.front().footprint;
-          return in_use_ == 0 || in_use_ + fp <= budget_;
-        });
-        if (stopping_ && queue_.empty()) break;
-        if (stopping_ && !queue_.empty() && !(in_use_ == 0 || in_use_ + queue_.front().footprint <= budget_))
-          break;
-        r = std::move(queue_.front());
-        queue_.pop_front();
+        // admission: the oldest queued request whose footprint fits beside the
+        // running ones (a large request at the head does not hold back smaller
+        // ones behind it); every queued request fits the budget on its own
+        auto pick = [&]() -> std::deque<Request>::iterator {
+          for (auto it = queue_.begin(); it != queue_.end(); ++it)
+            if (in_use_ + it->footprint <= budget_) return it;
+          return queue_.end();
+        };
+        cv_.wait(lk, [&] { return stopping_ || pick() != queue_.end(); });
+        auto it = pick();
+        if (it == queue_.end()) break;  // stopping, nothing admissible
+        r = std::move(*it);
+        queue_.erase(it);
         in_use_ += r.footprint;
         ++running_;
       }
@@ -269,6 +271,10 @@ ascc_status ascc_server_submit(ascc_server* srv, int32_t o, int32_t v, int32_t n
     r.B.assign(B, B + (size_t)naux * n * n);
     r.states.assign(states, states + n_states);
     r.footprint = ascc_footprint_bytes(o, v, naux, &srv->raw_options());
+    if (r.footprint > srv->budget())
+      throw ascc::Error(ASCC_ERR_OOM, "request needs " + std::to_string(r.footprint) +
+                                          " device bytes, more than the server's budget of " +
+                                          std::to_string(srv->budget()));
     const int64_t id = srv->submit(std::move(r));
     if (request_id) *request_id = id;
     return ASCC_OK;

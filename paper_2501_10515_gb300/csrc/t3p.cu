@@ -134,8 +134,15 @@ void T3pProgram::select(int b, const char* spec, int64_t* offset, std::vector<in
   }
 }
 
-void T3pProgram::run(const Einsum& es, cudaStream_t s, int section, double* const* base,
+// Contractions of at least this many flops run on the tensor cores when the
+// state uses them: most of the program's products are small (an o x v x v
+// block against a v x v one), and the FP64 units would serialise them.
+constexpr double kTcMinFlops = 1e6;
+
+void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* base,
                      double scale, double* ws) const {
+  const double min0 = es.min_flops();
+  if (es.level() > 0) es.set_split(es.level(), es.err(), std::min(min0, kTcMinFlops));
   auto tensor = [&](int t) -> T {
     const T3pTensor& d = kT3pTensors[t];
     if (d.kind == 0) return T(base[d.base], base_shape(d.base));
@@ -188,6 +195,7 @@ void T3pProgram::run(const Einsum& es, cudaStream_t s, int section, double* cons
       box_copy(s, base[op.base] + off, stride, tmp, ost, shape, 1.0, 1.0);
     }
   }
+  es.set_split(es.level(), es.err(), min0);
 }
 
 namespace k {

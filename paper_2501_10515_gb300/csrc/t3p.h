@@ -60,7 +60,7 @@ class T3pProgram {
   int64_t workspace_elements() const { return ws_elems_; }
   // Runs one section; base[T3pBase] points at the base operands (t2 / ts of
   // the binding of that section); scale multiplies every accumulation.
-  void run(const Einsum& es, cudaStream_t s, int section, double* const* base, double scale,
+  void run(Einsum& es, cudaStream_t s, int section, double* const* base, double scale,
            double* ws) const;
   // Sizes of the four blocks (elements) and the offsets of TA..TD (RA..RD)
   // in one concatenated buffer.

@@ -105,7 +105,7 @@ def test_sibling_state_shares_molecule():
 
 @pytest.mark.parametrize("ansatz", [0, 1])
 def test_second_ansatz_matches_oracle(ansatz):
-    """Sec. II.D: the two ansatz choices for an Aufbau weight alpha, and their average."""
+    """Sec. II.D: the two ansatz choices for an Aufbau weight alpha."""
     o, v, alpha = 4, 20, 0.1
     s = synth.make_system(o, v, seed=0)
     beta, sign = oracle_ascc.ansatz_beta(alpha, ansatz)
@@ -114,5 +114,26 @@ def test_second_ansatz_matches_oracle(ansatz):
     res = ctx.solve()
     assert ref.converged and res.status == 0
     assert abs(res.energy - ref.energy) <= E_TOL
-    import paper_2501_10515_gb300 as pkg
-    assert pkg.two_ansatz_average(res.energy, 0, 1.0, 4) == res.energy
+
+
+@pytest.mark.parametrize("created_as", [0, 1])
+def test_two_ansatz_average_through_the_abi(created_as):
+    """Sec. II.D / III.A: ascc_solve_two_ansatz reports the mean of the two
+    ansatz energies; each equals the oracle's solve of that ansatz."""
+    o, v, alpha = 4, 20, 0.1
+    s = synth.make_system(o, v, seed=0)
+    refs = []
+    for ans in (0, 1):
+        beta, sign = oracle_ascc.ansatz_beta(alpha, ans)
+        refs.append(oracle_ascc.solve_state(s.eps, s.B, o, 3, 0, linearize=True, beta=beta,
+                                            xsign=sign))
+    ctx = _ctx(s, 3, 0, linearize=1, alpha=alpha, ansatz=created_as)
+    res = ctx.solve_two_ansatz()
+    assert res.converged == 2
+    assert abs(res.first.energy - refs[0].energy) <= E_TOL
+    assert abs(res.second.energy - refs[1].energy) <= E_TOL
+    assert abs(res.energy - 0.5 * (refs[0].energy + refs[1].energy)) <= E_TOL
+    # with both choices capped at 2 iterations neither converges: NaN is reported
+    ctx2 = _ctx(s, 3, 0, linearize=1, alpha=alpha, ansatz=0, max_iter=2)
+    r2 = ctx2.solve_two_ansatz()
+    assert r2.converged == 0 and r2.energy != r2.energy  # NaN

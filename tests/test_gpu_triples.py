@@ -74,3 +74,49 @@ def test_solve_with_triples_matches_oracle(lin):
     assert abs(res.energy - ref.energy) <= E_TOL
     t1, t2, t3 = ctx.get_state()
     assert np.abs(t3 - ref.t3).max() < 1e-7
+
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "reference_energies.txt")
+    for line in open(path):
+        f = line.split()
+        if f and f[0] == name:
+            return int(f[1]), int(f[2]), int(f[3]), int(f[4]), int(f[5]), f[6], float(f[7])
+    pytest.skip(f"no stored oracle energy {name}")
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_residual_with_triples_mid_size(precision):
+    """o=9, v=70: several tiles and ragged tails in every T3' block."""
+    o, v, seed, hole, part = 9, 70, 3, 8, 2
+    s = synth.make_system(o, v, seed=seed)
+    idx = amp.t3p_index(o, v, hole, part)
+    t1, t2, t3 = _amplitudes(o, v, hole, part, len(idx), seed + 7)
+    ctx = _ctx(s, hole, part, linearize=1, precision=precision)
+    E, r1, r2, r3 = ctx.residual(t1, t2, t3)
+    Eo, r1o, r2o, r3o = _oracle(s, hole, part, t1, t2, t3, True, idx)
+    assert _rel(r1, r1o) <= REL_TOL
+    assert _rel(r2, r2o) <= REL_TOL
+    assert _rel(r3, r3o) <= REL_TOL
+    assert abs(E - Eo) <= E_TOL
+
+
+@pytest.mark.parametrize("name,precision,tol", [
+    ("c1_plascc_excited_t3", 0, E_TOL),
+    ("c1_ascc_excited_t3", 0, E_TOL),
+    ("c1_plascc_excited_t3", 1, 1e-6),
+    ("mid_plascc_excited_t3", 2, E_TOL),
+    ("mid_plascc_excited_t3", 1, 1e-6),
+])
+def test_solve_with_triples_matches_stored_oracle_energy(name, precision, tol):
+    """Converged ASCCSD / PLASCCSD energies with T3' against the oracle's
+    (tests/golden/make_reference_energies.py); FP64 and FP64-class paths at
+    1e-10 Eh, mixed precision at 1e-6 Eh."""
+    o, v, seed, hole, part, method, e_ref = _golden(name)
+    s = synth.make_system(o, v, seed=seed)
+    ctx = _ctx(s, hole, part, linearize=int(method.startswith("PL")), precision=precision,
+               max_iter=400)
+    res = ctx.solve()
+    assert res.status == 0
+    assert abs(res.energy - e_ref) <= tol, (res.energy, e_ref)

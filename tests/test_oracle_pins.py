@@ -186,7 +186,7 @@ def test_slice_oracle_matches_spinorbital(o, v, hole, part, linearize):
     idx = amp.t3p_index(o, v, hole, part)
     t1, t2, t3 = random_amplitudes(o, v, seed=12, scale=0.1, n_t3=len(idx))
     blk = sa.dressed_blocks(hb, Bb, o, t1)
-    r1, r2, r3 = t3slice.residual(blk.F, blk.B, o, t2, idx, t3, hole, part, linearize=linearize)
+    r1, r2, r3 = t3slice.residual(blk, t2, idx, t3, hole, part, linearize=linearize)
     _, r1s, r2s, R3s = so.residual(hb, ham.eri_from_df(Bb), t1, t2, amp.t3_dense(idx, t3, o, v),
                                    linearize=linearize, hole=hole, particle=part,
                                    triples_only=True)
