@@ -1,17 +1,20 @@
-"""Benchmark of the ASCC/PLASCC residual hot path on GB300.
+"""Benchmark of the ASCC / PLASCC solve on one GB300.
 
-Workload (default): the o=20, v=200 FP64 state -- naux = 660, seed 0,
-charge-transfer-like excitation from occupied 19 to virtual 3, PLASCC,
-synthetic integrals (see synth/).  One step is one pass of the whole hot
-path: the residual (integral dressing, Fock and ring/ladder intermediates,
-particle-particle ladder, partial linearisation, energy), the convergence
-test, the Jacobi update and the DIIS extrapolation of one solve iteration.
-Warm-up steps continue the same solve.  `value` is the residual throughput in
-TFLOP/s (algorithmic flops of the contractions the path performs, summed over
-ranks, over the max-over-ranks step time); `e2e` is the same through the
-host-buffer C-ABI call with the copies inside the timed region.
+Default workload: one complete PLASCC solve with the mixed-triples slice T3'
+(the paper's one-CSF ASCCSD, Sec. II.B.1, linearised as in Sec. II.C) of the
+o=20, v=200 synthetic state (naux = 660, seed 0, excitation 19 -> 3, sigma
+from the fixed coupling of synth/), from the zeroth-order guess to
+max|R| <= 1e-8 and |dE| <= 1e-10 Eh, in mixed precision (split-BF16 tensor-core
+contractions, FP64-class digit-plane polishing).  One step is one such solve;
+`value` is solves per second (whole job: every replica's solves over the
+slowest replica's time), measured with CUDA events on the context's stream
+with the molecule's integrals already resident.  `e2e` is the same solve
+requested through the host-buffer C ABI (context creation from pinned host
+eps/B, integral setup, solve, energy back to the host).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload c1|c2|c3|batch|serve|gemm] [--precision mixed|fp64tc|fp64]
+                    [--triples 0|1] [--fp64-solve]
 """
 from __future__ import annotations
 
@@ -34,14 +37,30 @@ METRIC = ("ASCC solves/sec & residual TFLOP/s vs plain FP64 at 1e-6 Eh; "
 SERVE_NOTE = ("scaled-down serving trace: o log-uniform [5,20], v log-uniform [50,160], 1-4 "
               "excited states per molecule plus its ground state, Poisson arrivals")
 WORKLOADS = {
-    "c2": dict(o=20, v=200, seed=0, hole=19, particle=3,
-               name="ascc solve o=20 v=200 naux=660 excitation 19->3 (PLASCC), max|R| <= 1e-8"),
-    "c1": dict(o=4, v=20, seed=0, hole=3, particle=0,
-               name="ascc solve o=4 v=20 naux=72 excitation 3->0 (PLASCC), max|R| <= 1e-8"),
-    "c3": dict(o=30, v=300, seed=0, hole=29, particle=0,
-               name="ascc solve o=30 v=300 naux=990 excitation 29->0 (PLASCC), max|R| <= 1e-8"),
+    "c2": dict(o=20, v=200, seed=0, hole=19, particle=3),
+    "c1": dict(o=4, v=20, seed=0, hole=3, particle=0),
+    "c3": dict(o=30, v=300, seed=0, hole=29, particle=0),
 }
 FP64_NOMINAL_TFLOPS = 1.25
+
+
+def workload_name(wl, triples):
+    n = wl["o"] + wl["v"]
+    return (f"ascc solve o={wl['o']} v={wl['v']} naux={3 * n} excitation "
+            f"{wl['hole']}->{wl['particle']} (PLASCC{' + T3' + chr(39) if triples else ''}), "
+            "max|R| <= 1e-8")
+
+
+def measured_peaks():
+    """Roofline denominators measured on this machine (MEASURED_PEAKS.json), else the
+    fallback figures of the profiling recipe."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16": float(d["bf16_tflops"]),
+                "bf16_sustained": float(d["bf16_tflops_sustained"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
 def rank_env():
@@ -97,7 +116,12 @@ class ClockSampler:
 
 
 def oracle_residual_timer(wl, steps, warmup):
-    """The CPU oracle's residual at the same state; returns (seconds per step list, flops ref)."""
+    """Seconds per oracle residual of the workload's state (list over the timed
+    steps).  The sample is the oracle's T1/T2 residual (singles, doubles,
+    partial linearisation, energy) at the zeroth-order guess: the oracle's
+    evaluation of the T3' terms takes more than ten minutes per residual at
+    o=20, v=200 on the host cores, far beyond a bounded sample, so the sample
+    leaves them out and the derived solves/s is an upper bound for the oracle."""
     import synth
     from oracle import amplitudes as amp
     from oracle import ascc as oracle_ascc
@@ -114,6 +138,12 @@ def oracle_residual_timer(wl, steps, warmup):
         if k >= warmup:
             times.append(dt)
     return times
+
+
+ORACLE_SAMPLE = ("one oracle T1/T2 residual of the same state at the zeroth-order guess per step "
+                 "(the T3' terms left out: over ten minutes per residual on these cores), times the "
+                 "iterations of a converged solve of that state -> an upper bound on the oracle's "
+                 "solves/s")
 
 
 def flops_per_residual(o, v, naux, excited=True, linearize=True):
@@ -157,35 +187,45 @@ def oracle_iterations(name, default=50):
 
 
 def run_reference(args, wl):
-    """The CPU oracle as it stands; each step is one oracle residual of the state
-    (a bounded sample of a solve), scaled to solves/s by the oracle's own
-    iteration count for this state."""
+    """The CPU oracle as it stands, on the host cores: each step is one bounded
+    sample (ORACLE_SAMPLE); ms_per_step is that sample's measured time, and the
+    value converts it to solves/s with the iteration count of the solve."""
     rank, world, _ = rank_env()
     if rank != 0:
         return 0
     cores = len(os.sched_getaffinity(0))
-    times = oracle_residual_timer(wl, args.steps, args.warmup)
+    times = oracle_residual_timer(wl, args.steps, max(1, args.warmup))
     naux = 3 * (wl["o"] + wl["v"])
-    iters = oracle_iterations(f"{args.workload}_plascc_excited")
+    name = f"{args.workload}_plascc_excited" + ("_t3" if args.triples else "")
+    iters = oracle_iterations(name, default=SOLVE_ITERATIONS.get((args.workload, args.triples), 50))
     per = sum(times) / len(times)
-    ms = 1e3 * per * iters
     value = 1.0 / (per * iters)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": wl["name"], "o": wl["o"], "v": wl["v"], "naux": naux,
-                   "excitation": [wl["hole"], wl["particle"]], "method": "PLASCC",
-                   "step": "one oracle residual evaluation at the zeroth-order guess",
-                   "iterations_per_solve": iters},
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * per, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(wl, args.triples), "o": wl["o"], "v": wl["v"],
+                   "naux": naux, "excitation": [wl["hole"], wl["particle"]],
+                   "method": "PLASCC" + ("+T3'" if args.triples else ""),
+                   "sigma": _sigma(wl), "triples": int(args.triples),
+                   "step": ORACLE_SAMPLE, "iterations_per_solve": iters},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": f"one residual evaluation of the same state per step, x {iters} "
-                                   "iterations (the oracle's own count for this state)"},
+                         "sample": ORACLE_SAMPLE},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _sigma(wl):
+    import synth
+    return synth.default_sigma(wl["o"], wl["v"])
+
+
+# iterations of the GPU solves of these states (FP64-class and mixed agree to
+# a few), used when the oracle has no converged solve of the state
+SOLVE_ITERATIONS = {("c2", 1): 63, ("c2", 0): 28}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the pair-row ladder GEMM
@@ -318,21 +358,25 @@ def run_gemm(args):
                       + " incl. operand split and K reduction",
                       "M": M, "N": N, "K": K, "level": lev, "products": products, "ms": ms,
                       "tflops_fp64_equivalent": tf, "mma_tflops": tf * products,
-                      "mma_frac_of_bf16_burst": tf * products / 1977.2}), flush=True)
+                      "mma_frac_of_bf16_burst": tf * products / measured_peaks()["bf16"],
+                      "peak_source": measured_peaks()["source"]}), flush=True)
     return 0
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["batch", "serve", "gemm"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "fp64tc"])
+    ap.add_argument("--triples", type=int, default=1, choices=[0, 1])
     ap.add_argument("--step", default="solve", choices=["solve", "iteration"])
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-iterations", type=int, default=2)
+    ap.add_argument("--fp64-solve", action="store_true",
+                    help="time one complete plain-FP64 solve of the same state (minutes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=0)
     ap.add_argument("--rate", type=float, default=1.0)
@@ -366,7 +410,7 @@ def main():
     mixed = args.precision != "fp64"  # tensor-core contractions
     prec = precision_code(pkg, args.precision)
     ctx = pkg.Context(o, v, s.naux, s.eps, s.B, hole=wl["hole"], particle=wl["particle"],
-                      linearize=1, stream=stream.cuda_stream, precision=prec)
+                      linearize=1, triples=args.triples, stream=stream.cuda_stream, precision=prec)
 
     def one_unit():
         if args.step == "solve":
@@ -409,40 +453,59 @@ def main():
     lad_mma = (p1.ladder_mma_flops - p0.ladder_mma_flops) / nlad
     achieved = lad_fl / (lad_ms / 1e3) / 1e12
     mma_rate = lad_mma / (lad_ms / 1e3) / 1e12
+    peaks = measured_peaks()
     if mixed:
-        peak, bound, unit_note = 1977.2, "tensor", "BF16 dense burst, measured (MEASURED_PEAKS.json)"
+        # the ladder launch is timed inside a seconds-long solve: the sustained figure
+        peak, bound = peaks["bf16_sustained"], "tensor"
+        peak_note = (f"BF16 dense, sustained under the power cap, of {peaks['source']} "
+                     "(MEASURED_PEAKS.json bf16_tflops_sustained)")
     else:
-        peak, bound, unit_note = FP64_NOMINAL_TFLOPS, "alu", "nominal FP64 rate of the recipe table"
+        peak, bound = FP64_NOMINAL_TFLOPS, "alu"
+        peak_note = "nominal FP64 rate of the recipe table (no FP64 peak is measured on this pool)"
     last = results[-1]
     iters = last.iterations
     value = units / (ms / 1e3) if args.step == "solve" else tflops
     unit = "solves/s" if args.step == "solve" else "TFLOP/s"
-    ref_e = golden_energy(f"{args.workload}_plascc_excited")
+    gname = f"{args.workload}_plascc_excited" + ("_t3" if args.triples else "")
+    ref_e = golden_energy(gname)
 
-    # the plain FP64 path on the same state: a few iterations, for the comparison
+    # the plain FP64 path on the same state (a sibling context sharing the
+    # molecule): a few iterations always, the complete solve with --fp64-solve
     fp64 = None
-    if mixed and args.fp64_iterations > 0 and args.step == "solve":
+    if mixed and args.step == "solve" and (args.fp64_iterations > 0 or args.fp64_solve):
         cf = pkg.Context(o, v, s.naux, None, None, hole=wl["hole"], particle=wl["particle"],
-                         base=ctx, linearize=1, stream=stream.cuda_stream, precision=pkg.ASCC_FP64)
+                         base=ctx, linearize=1, triples=args.triples, stream=stream.cuda_stream,
+                         precision=pkg.ASCC_FP64)
         cf.reset()
         cf.iterate(1)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        nit = max(1, args.fp64_iterations)
         e0.record(stream)
-        cf.iterate(args.fp64_iterations)
+        cf.iterate(nit)
         e1.record(stream)
         torch.cuda.synchronize()
-        fms = e0.elapsed_time(e1) / args.fp64_iterations
-        fp64 = {"ms_per_iteration": fms, "solve_s_estimate": fms * iters / 1e3,
-                "solves_per_s_estimate": 1e3 / (fms * iters),
-                "note": "FP64 time per iteration measured on this state; x the mixed solve's iterations"}
+        fms = e0.elapsed_time(e1) / nit
+        fp64 = {"ms_per_iteration": fms, "iterations_timed": nit}
+        if args.fp64_solve:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            rf = cf.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fp64.update(solve_s=e0.elapsed_time(e1) / 1e3, solve_iterations=rf.iterations,
+                        solve_status=int(rf.status), solve_energy=rf.energy,
+                        solves_per_s=1e3 / e0.elapsed_time(e1),
+                        energy_difference_to_this_solve=abs(rf.energy - last.energy))
+        else:
+            fp64.update(solve_s_estimate=fms * iters / 1e3,
+                        note="estimate: FP64 time per iteration measured on this state x this "
+                             "solve's iterations; python bench.py --fp64-solve times the whole solve")
         cf.close()
 
     # the timed context is released before the end-to-end request, which
     # builds its own molecule (two copies of the large ladder blocks need not fit)
     ctx.close()
-    # end to end: one solve request through the host-buffer C ABI (context
-    # creation from host eps/B, integral setup, solve, energy back to host)
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     eps_p, B_p = pin(s.eps), pin(s.B)
     torch.cuda.synchronize()
@@ -450,27 +513,29 @@ def main():
     e2e_energy = None
     for _ in range(args.e2e_steps):
         c2 = pkg.Context(o, v, s.naux, eps_p, B_p, hole=wl["hole"], particle=wl["particle"],
-                         linearize=1, precision=prec)
+                         linearize=1, triples=args.triples, precision=prec)
         r2 = c2.solve()
         e2e_energy = r2.energy
         c2.close()
     e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
-
 
     line = {
         "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[args.precision], "data": "synthetic",
-        "config": {"workload": wl["name"], "o": o, "v": v, "naux": s.naux,
-                   "excitation": [wl["hole"], wl["particle"]], "method": "PLASCC",
+        "config": {"workload": workload_name(wl, args.triples), "o": o, "v": v, "naux": s.naux,
+                   "excitation": [wl["hole"], wl["particle"]],
+                   "method": "PLASCC" + ("+T3'" if args.triples else ""),
+                   "triples": int(args.triples), "sigma": s.sigma,
+                   "n_t3": int(n3_of(wl, args.triples)),
                    "precision": args.precision, "parallelism": f"replicas{world}",
                    "l2": ("inputs larger than L2: the (xc|bd) block (%.1f GB as 3 BF16 planes, "
                           "%.1f GB as 6 digit planes, %.1f GB FP64) is streamed every iteration"
                           % (6.0 * (o + v) * v ** 3 / 1e9, 12.0 * (o + v) * v ** 3 / 1e9,
                              8.0 * (o + v) * v ** 3 / 1e9)),
-                   "step": ("one complete solve from the zeroth-order guess to max|R| <= 1e-8, |dE| <= 1e-10"
-                            if args.step == "solve" else
+                   "step": ("one complete solve from the zeroth-order guess to max|R| <= 1e-8, "
+                            "|dE| <= 1e-10" if args.step == "solve" else
                             "one solve iteration (residual + convergence test + Jacobi + DIIS)")},
         "clocks": clocks,
         "e2e": {"value": (1.0 / e2e_s) if (args.step == "solve" and args.e2e_steps) else None,
@@ -488,41 +553,55 @@ def main():
                      "kernel": {"fp64": "gemm_f64_kernel", "mixed": "gemm_tc_kernel",
                                 "fp64tc": "gemm_oz_kernel"}[args.precision] +
                                " (the particle-particle ladder's pair-row GEMM, M = o(o+1)/2, "
-                               "N = K = v^2, with its split-K reduction)",
-                     "peak_source": unit_note,
+                               "N = K = v^2, with its split-K reduction: the largest single launch)",
+                     "peak_source": peak_note,
                      "achieved_note": "algorithmic flops of that launch, 2 o(o+1)/2 v^4 (one "
                                       "product per multiply-add), over its CUDA-event time on "
                                       "the state's stream, averaged over the launches of the "
                                       "timed solves; mma_* count every BF16 plane product",
                      "mma_tflops": mma_rate,
-                     "mma_frac": mma_rate / peak},
+                     "mma_frac": mma_rate / peak,
+                     "ladder_ms_share_of_step": (p1.ladder_ms - p0.ladder_ms) / (ms / world)},
         "residual_tflops": tflops,
-        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+        "residual_frac": tflops / world / peak,
+        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                       "note": "per solve, back to back on one state (not a serving latency: "
+                               "see --workload serve)"},
         "iterations": iters, "iterations_low_precision": last.iterations_low,
         "status": int(last.status), "energy": last.energy,
         "energy_error_vs_oracle": (abs(last.energy - ref_e) if ref_e is not None else None),
+        "oracle_energy_source": (f"tests/golden/reference_energies.txt {gname}"
+                                 if ref_e is not None else
+                                 "none: the oracle's solve with T3' at this size is not feasible "
+                                 "on the host; tests/test_gpu_fullsize.py checks this residual "
+                                 "against tests/golden/c2_t3_residual.txt instead"),
         "e2e_energy": e2e_energy,
         "fp64_path": fp64,
     }
     if rank == 0 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0))
         times = oracle_residual_timer(wl, 1, 0)
-        fl = flops_per_residual(o, v, s.naux)
         ores = times[0]
-        cb = {"cores": cores, "kind": "oracle",
-              "sample": "one oracle residual evaluation of the same state; "
-                        "scaled by the solve's iteration count"}
+        cb = {"cores": cores, "kind": "oracle", "sample": ORACLE_SAMPLE,
+              "seconds_per_sample": ores, "iterations": iters}
         if args.step == "solve":
             cb.update(value=1.0 / (ores * iters), unit="solves/s")
         else:
-            cb.update(value=fl / ores / 1e12, unit="TFLOP/s")
-        cb["seconds_per_residual"] = ores
+            cb.update(value=flops_per_residual(o, v, s.naux) / ores / 1e12, unit="TFLOP/s")
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def n3_of(wl, triples):
+    if not triples:
+        return 0
+    o, v = wl["o"], wl["v"]
+    return (o - 1) * (v * (v - 1) // 2 + (v - 1) ** 2) + (o - 1) * (o - 2) // 2 * (v - 1) + \
+        (o - 1) ** 2 * (v - 1)
 
 
 if __name__ == "__main__":

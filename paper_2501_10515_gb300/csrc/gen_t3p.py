@@ -363,7 +363,7 @@ def merge(terms):
 
 
 # ---------------------------------------------------------- 5. contraction plan
-PLAN_SIZE = {'o': 20, 'v': 200, 'P': 660}
+PLAN_SIZE = {'o': 20, 'v': 200, 'P': 660, '#': 1}
 # base tensors: name -> spaces of their dimensions ('n': all orbitals, 'P': DF index)
 BASE_DIMS = {'F': 'nn', 'B': 'Pnn', 't2': 'oovv', 'ts': 'oovv', 'TA': 'ovv', 'TB': 'ovv',
              'TC': 'oov', 'TD': 'oov', 'r1': 'ov', 'r2': 'oovv', 'RA': 'ovv', 'RB': 'ovv',
@@ -636,38 +636,187 @@ def build_program(w):
 SECTIONS = ('pro', 'lin', 'quad', 'mix')
 BASES = ('F', 'B', 't2', 'ts', 'TA', 'TB', 'TC', 'TD', 'r1', 'r2', 'RA', 'RB', 'RC', 'RD')
 
+# ------------------------------------------------ 6. shared-operand stacking
+# Contractions that read the same large operand X with the same indices of X
+# contracted (an integral block, t2, a DF slice against many small operands)
+# are run as one: the small operands Y_i are stacked as rows of S[#][K],
+# W[F][#] = X . S^T is one GEMM, and each result is copied (or accumulated)
+# out of its columns of W.  X is then prepared and read once per group.
+FUSE_MIN = 1.0e6   # elements of X at the planning sizes
+FUSE_MAX_W = 6.4e7  # elements of a stacked product W (and of S) at the planning sizes
+
+
+def dims_size(dims):
+    r = 1.0
+    for c in dims:
+        r *= PLAN_SIZE[c]
+    return r
+
+
+def fuse_candidate(prog, op):
+    """((X, roles), (lx, Y, ly)) for a contraction that may share operand X."""
+    if op['kind'] not in ('ctr', 'acc'):
+        return None
+    lhs, c = op['spec'].split('->')
+    la, lb = lhs.split(',')
+    if any(x in la and x in lb for x in c):
+        return None
+    best = None
+    for X, lx, Y, ly in ((op['a'], la, op['b'], lb), (op['b'], lb, op['a'], la)):
+        dims = prog.tensors[X]['dims']
+        if '#' in dims or dims_size(dims) < FUSE_MIN or len(ly) == 0:
+            continue
+        roles = tuple('K' if (x in ly and x not in c) else 'F' for x in lx)
+        if 'K' not in roles:
+            continue
+        size = dims_size(dims)
+        if best is None or size > best[2]:
+            best = ((X, roles), (lx, Y, ly), size)
+    return None if best is None else best[:2]
+
+
+def fuse_shared_operands(prog):
+    for sec in SECTIONS:
+        ops = prog.ops[sec]
+        producer = {}
+        for i, op in enumerate(ops):
+            if op['kind'] in ('slice', 'ctr'):
+                producer[op['out']] = i
+        deps = []
+        for op in ops:
+            d = set()
+            for t in (op.get('a'), op.get('b')):
+                if t is not None and t in producer:
+                    d.add(producer[t])
+            deps.append(d)
+        cand = [fuse_candidate(prog, op) for op in ops]
+        count = {}
+        for cnd in cand:
+            if cnd is not None:
+                count[cnd[0]] = count.get(cnd[0], 0) + 1
+        emitted, out, remaining = set(), [], list(range(len(ops)))
+        while remaining:
+            ready = [i for i in remaining if deps[i] <= emitted]
+            plain = [i for i in ready if cand[i] is None or count[cand[i][0]] < 2]
+            if plain:
+                take = plain
+                out.extend(ops[i] for i in take)
+            else:
+                by = {}
+                for i in ready:
+                    by.setdefault(cand[i][0], []).append(i)
+                key, take = max(by.items(), key=lambda kv: (len(kv[1]), -kv[1][0]))
+                for chunk in size_chunks(prog, key, [(ops[i], cand[i][1]) for i in take]):
+                    if len(chunk) == 1:
+                        out.append(chunk[0][0])
+                    else:
+                        out.extend(stacked_ops(prog, sec, key, chunk))
+            emitted.update(take)
+            tk = set(take)
+            remaining = [i for i in remaining if i not in tk]
+        prog.ops[sec] = out
+
+
+def size_chunks(prog, key, members):
+    """Members in order, cut so that no stack product W or stack S exceeds FUSE_MAX_W."""
+    X, roles = key
+    xdims = prog.tensors[X]['dims']
+    f = dims_size(''.join(d for d, r in zip(xdims, roles) if r == 'F'))
+    kk = dims_size(''.join(d for d, r in zip(xdims, roles) if r == 'K'))
+    chunks, cur, rows = [], [], 0.0
+    for op, (lx, Y, ly) in members:
+        c = op['spec'].split('->')[1]
+        ydims = prog.tensors[Y]['dims']
+        n = dims_size(''.join(ydims[ly.index(x)] for x in c if x in ly))
+        if cur and max(f, kk) * (rows + n) > FUSE_MAX_W:
+            chunks.append(cur)
+            cur, rows = [], 0.0
+        cur.append((op, (lx, Y, ly)))
+        rows += n
+    if cur:
+        chunks.append(cur)
+    return chunks
+
+
+def stacked_ops(prog, sec, key, members):
+    X, roles = key
+    xdims = prog.tensors[X]['dims']
+    kdims = ''.join(d for d, r in zip(xdims, roles) if r == 'K')
+    fdims = ''.join(d for d, r in zip(xdims, roles) if r == 'F')
+    rows, stacks, unstacks = [], [], []
+    for m, (op, (lx, Y, ly)) in enumerate(members):
+        c = op['spec'].split('->')[1]
+        kl = ''.join(x for x, r in zip(lx, roles) if r == 'K')
+        fl = ''.join(x for x, r in zip(lx, roles) if r == 'F')
+        gl = ''.join(x for x in c if x in ly)
+        ydims = prog.tensors[Y]['dims']
+        rows.append(''.join(ydims[ly.index(x)] for x in gl))
+        stacks.append({'kind': 'stack', 'a': Y, 'spec': f"{ly}->{gl}{kl}", 'member': m})
+        u = {'kind': 'unstack', 'spec': f"{fl}{gl}->{c}", 'alpha': op['alpha'], 'member': m}
+        if op['kind'] == 'ctr':
+            u['out'] = op['out']
+        else:
+            u['outbase'], u['outspec'] = op['outbase'], op['outspec']
+        unstacks.append(u)
+    rs = '+'.join(rows)
+    S = len(prog.tensors)
+    prog.tensors.append({'kind': 'inter', 'dims': '#' + kdims, 'rows': rs, 'section': sec})
+    W = len(prog.tensors)
+    prog.tensors.append({'kind': 'inter', 'dims': fdims + '#', 'rows': rs, 'section': sec})
+    for st in stacks:
+        st['out'] = S
+    for u in unstacks:
+        u['a'] = W
+    lx = ''.join('abcdefghijklmnopqrstuvwxy'[q] for q in range(len(xdims)))
+    klet = ''.join(x for x, r in zip(lx, roles) if r == 'K')
+    flet = ''.join(x for x, r in zip(lx, roles) if r == 'F')
+    ctr = {'kind': 'ctr', 'a': X, 'b': S, 'out': W, 'spec': f"{lx},Z{klet}->{flet}Z", 'alpha': 1.0}
+    return stacks + [ctr] + unstacks
+
 
 def emit(prog, out):
     """Writes the program as C++ tables (included by t3p.cu)."""
     w = out.write
     w("// Generated by gen_t3p.py from the spin-orbital triples equations; do not edit.\n")
     w("// Tensors: kind 0 = base operand, 1 = slice of a base operand, 2 = intermediate;\n")
-    w("// dims use o (occupied), v (virtual), P (density-fitting index); a slice\n")
-    w("// selector has one character per base dimension: o / v / P (range), h / p (fixed).\n")
-    w("// Ops: kind 0 = slice, 1 = contraction into an intermediate,\n")
-    w("// 2 = contraction accumulated into an output block (selector outspec).\n")
+    w("// dims use o (occupied), v (virtual), P (density-fitting index) and # (the rows of\n")
+    w("// a stack: the sum over its members of the products of the '+'-separated dims);\n")
+    w("// a slice selector has one character per base dimension: o / v / P (range),\n")
+    w("// h / p (fixed).  Ops: kind 0 = slice, 1 = contraction into an intermediate,\n")
+    w("// 2 = contraction accumulated into an output block (selector outspec),\n")
+    w("// 3 = copy of a member operand into its rows of a stack, 4 = copy of a\n")
+    w("// member's columns of a stacked product into its intermediate or output.\n")
     w(f"static const int kT3pTensorCount = {len(prog.tensors)};\n")
     w("static const T3pTensor kT3pTensors[] = {\n")
     for t in prog.tensors:
         kind = {'base': 0, 'slice': 1, 'inter': 2}[t['kind']]
         base = BASES.index(t['base']) if 'base' in t else -1
-        w(f'    {{{kind}, {base}, "{t.get("spec", "")}", "{t["dims"]}", {SECTIONS.index(t["section"])}}},\n')
+        w(f'    {{{kind}, {base}, "{t.get("spec", "")}", "{t["dims"]}", '
+          f'{SECTIONS.index(t["section"])}, "{t.get("rows", "")}"}},\n')
     w("};\n")
     n = sum(len(v) for v in prog.ops.values())
     w(f"static const int kT3pOpCount = {n};\n")
     w("static const T3pOp kT3pOps[] = {\n")
     for sec in SECTIONS:
+        sid = SECTIONS.index(sec)
         for op in prog.ops[sec]:
-            kind = {'slice': 0, 'ctr': 1, 'acc': 2}[op['kind']]
-            if kind == 0:
-                w(f'    {{{SECTIONS.index(sec)}, 0, {op["out"]}, -1, -1, "{op["spec"]}", 1.0, '
-                  f'{BASES.index(op["base"])}, ""}},\n')
-            elif kind == 1:
-                w(f'    {{{SECTIONS.index(sec)}, 1, {op["out"]}, {op["a"]}, {op["b"]}, '
-                  f'"{op["spec"]}", {op["alpha"]!r}, -1, ""}},\n')
+            k = op['kind']
+            if k == 'slice':
+                w(f'    {{{sid}, 0, {op["out"]}, -1, -1, "{op["spec"]}", 1.0, '
+                  f'{BASES.index(op["base"])}, "", -1}},\n')
+            elif k == 'ctr':
+                w(f'    {{{sid}, 1, {op["out"]}, {op["a"]}, {op["b"]}, '
+                  f'"{op["spec"]}", {op["alpha"]!r}, -1, "", -1}},\n')
+            elif k == 'acc':
+                w(f'    {{{sid}, 2, -1, {op["a"]}, {op["b"]}, "{op["spec"]}", '
+                  f'{op["alpha"]!r}, {BASES.index(op["outbase"])}, "{op["outspec"]}", -1}},\n')
+            elif k == 'stack':
+                w(f'    {{{sid}, 3, {op["out"]}, {op["a"]}, -1, "{op["spec"]}", 1.0, -1, "", '
+                  f'{op["member"]}}},\n')
             else:
-                w(f'    {{{SECTIONS.index(sec)}, 2, -1, {op["a"]}, {op["b"]}, "{op["spec"]}", '
-                  f'{op["alpha"]!r}, {BASES.index(op["outbase"])}, "{op["outspec"]}"}},\n')
+                ob = BASES.index(op['outbase']) if 'outbase' in op else -1
+                w(f'    {{{sid}, 4, {op.get("out", -1)}, {op["a"]}, -1, "{op["spec"]}", '
+                  f'{op["alpha"]!r}, {ob}, "{op.get("outspec", "")}", {op["member"]}}},\n')
     w("};\n")
 
 
@@ -677,8 +826,10 @@ def main():
     cache = os.environ.get('T3P_WICK_CACHE')
     w = pickle.load(open(cache, 'rb')) if cache and os.path.exists(cache) else wick_terms()
     prog = build_program(w)
+    fuse_shared_operands(prog)
     for s in SECTIONS:
-        print(s, len(prog.ops[s]), f"{prog.flops[s]:.3e} flops at o=20 v=200", file=sys.stderr)
+        print(s, len(prog.ops[s]), f"{prog.flops[s]:.3e} flops at o=20 v=200 (before stacking)",
+              file=sys.stderr)
     emit(prog, sys.stdout)
 
 

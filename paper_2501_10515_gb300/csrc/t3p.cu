@@ -26,7 +26,8 @@ T3pProgram::T3pProgram(int o, int v, int naux, int h, int p)
   };
   shape_.resize(kT3pTensorCount);
   for (int t = 0; t < kT3pTensorCount; ++t)
-    for (const char* c = kT3pTensors[t].dims; *c; ++c) shape_[t].push_back(extent(*c));
+    for (const char* c = kT3pTensors[t].dims; *c; ++c)
+      shape_[t].push_back(*c == '#' ? stack_rows(kT3pTensors[t].rows, 1 << 30) : extent(*c));
   // lifetimes over the run order (pro, lin, quad, mix; quad may run twice on
   // the same allocation), then first-fit placement
   std::vector<int> def(kT3pTensorCount, -1), last(kT3pTensorCount, -1);
@@ -82,6 +83,27 @@ T3pProgram::T3pProgram(int o, int v, int naux, int h, int p)
   }
   acc_off_ = round_up(peak, 32);
   ws_elems_ = acc_off_ + round_up(acc_max, 32);
+}
+
+int64_t T3pProgram::dims_extent(const char* dims) const {
+  int64_t e = 1;
+  for (const char* c = dims; *c && *c != '+'; ++c)
+    e *= *c == 'o' ? o_ : *c == 'v' ? v_ : *c == 'P' ? naux_ : (int64_t)n_;
+  return e;
+}
+
+int64_t T3pProgram::stack_rows(const char* rows, int upto) const {
+  int64_t r = 0;
+  int m = 0;
+  const char* c = rows;
+  while (m < upto) {
+    r += dims_extent(c);
+    ++m;
+    while (*c && *c != '+') ++c;
+    if (!*c) break;
+    ++c;
+  }
+  return r;
 }
 
 std::vector<int64_t> T3pProgram::base_shape(int b) const {
@@ -169,6 +191,8 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
       box_copy(s, ws + offset_[op.out], ost, base[op.base] + off, stride, shape);
     } else if (op.kind == 1) {
       es(op.spec, op.alpha, tensor(op.a), tensor(op.b), 0.0, tensor(op.out));
+    } else if (op.kind == 3 || op.kind == 4) {
+      stack_copy(op, s, base, scale, ws);
     } else {
       int64_t off;
       std::vector<int64_t> shape, stride;
@@ -196,6 +220,117 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
     }
   }
   es.set_split(es.level(), es.err(), min0);
+}
+
+namespace {
+// the dims of member m of a '+'-separated rows string
+std::string member_dims(const char* rows, int m) {
+  const char* c = rows;
+  for (int q = 0; q < m; ++q) {
+    while (*c && *c != '+') ++c;
+    if (*c) ++c;
+  }
+  std::string d;
+  while (*c && *c != '+') d += *c++;
+  return d;
+}
+
+std::vector<int64_t> row_major(const std::vector<int64_t>& shape) {
+  std::vector<int64_t> st(shape.size());
+  int64_t acc = 1;
+  for (int d = (int)shape.size() - 1; d >= 0; --d) {
+    st[d] = acc;
+    acc *= shape[d];
+  }
+  return st;
+}
+}  // namespace
+
+// Kind 3: member operand Y (labels: spec before ->) into rows [off, off + N_m)
+// of the stack S[#][K...], in the order spec after -> (the member's free
+// labels, then the contracted ones).  Kind 4: the member's columns of the
+// stacked product W[F...][#] (labels: F, then the member's free labels) into
+// its intermediate, or accumulated into an output block.
+void T3pProgram::stack_copy(const T3pOp& op, cudaStream_t s, double* const* base, double scale,
+                            double* ws) const {
+  const std::string spec(op.spec);
+  const auto arrow = spec.find("->");
+  const std::string lhs = spec.substr(0, arrow), rhs = spec.substr(arrow + 2);
+  auto ext = [&](char c) -> int64_t {
+    return c == 'o' ? o_ : c == 'v' ? v_ : c == 'P' ? naux_ : (int64_t)n_;
+  };
+  if (op.kind == 3) {
+    const T3pTensor& S = kT3pTensors[op.out];
+    const std::string gd = member_dims(S.rows, op.member);
+    const int64_t off = stack_rows(S.rows, op.member);
+    std::vector<int64_t> kshape(shape_[op.out].begin() + 1, shape_[op.out].end());
+    int64_t kprod = 1;
+    for (auto d : kshape) kprod *= d;
+    std::vector<int64_t> gshape;
+    for (char c : gd) gshape.push_back(ext(c));
+    std::vector<int64_t> dst = row_major(gshape), kst = row_major(kshape);
+    for (auto& x : dst) x *= kprod;
+    dst.insert(dst.end(), kst.begin(), kst.end());
+    const T3pTensor& Yd = kT3pTensors[op.a];
+    const std::vector<int64_t> yshape = Yd.kind == 0 ? base_shape(Yd.base) : shape_[op.a];
+    const std::vector<int64_t> yst = row_major(yshape);
+    const double* y = Yd.kind == 0 ? base[Yd.base] : ws + offset_[op.a];
+    std::vector<int64_t> src, shape;
+    for (char c : rhs) {
+      const auto q = lhs.find(c);
+      src.push_back(yst[q]);
+      shape.push_back(yshape[q]);
+    }
+    if (shape.empty()) {
+      shape = {1};
+      src = {1};
+      dst = {1};
+    }
+    box_copy(s, ws + offset_[op.out] + off * kprod, dst, y, src, shape);
+    return;
+  }
+  const T3pTensor& W = kT3pTensors[op.a];
+  const std::string fd(W.dims, std::strlen(W.dims) - 1);
+  const std::string gd = member_dims(W.rows, op.member);
+  const int64_t off = stack_rows(W.rows, op.member);
+  const int64_t ntot = shape_[op.a].back();
+  std::vector<int64_t> fshape, gshape;
+  for (char c : fd) fshape.push_back(ext(c));
+  for (char c : gd) gshape.push_back(ext(c));
+  std::vector<int64_t> fst = row_major(fshape), gst = row_major(gshape);
+  for (auto& x : fst) x *= ntot;
+  std::vector<int64_t> lab_st(fst), lab_ext(fshape);
+  lab_st.insert(lab_st.end(), gst.begin(), gst.end());
+  lab_ext.insert(lab_ext.end(), gshape.begin(), gshape.end());
+  ASCC_REQUIRE(lab_st.size() == lhs.size(), "T3' program: unstack labels");
+  std::vector<int64_t> src, shape;
+  for (char c : rhs) {
+    const auto q = lhs.find(c);
+    src.push_back(lab_st[q]);
+    shape.push_back(lab_ext[q]);
+  }
+  const double* w = ws + offset_[op.a] + off;
+  if (op.out >= 0) {
+    ASCC_REQUIRE(shape_[op.out] == shape, "T3' program: unstack result shape");
+    std::vector<int64_t> dst = row_major(shape_[op.out]);
+    if (shape.empty()) {
+      shape = {1};
+      src = {1};
+      dst = {1};
+    }
+    box_copy(s, ws + offset_[op.out], dst, w, src, shape, op.alpha, 0.0);
+    return;
+  }
+  int64_t boff;
+  std::vector<int64_t> bshape, bstride;
+  select(op.base, op.outspec, &boff, bshape, bstride);
+  ASCC_REQUIRE(bshape == shape, "T3' program: unstack output box");
+  if (shape.empty()) {
+    shape = {1};
+    src = {1};
+    bstride = {1};
+  }
+  box_copy(s, base[op.base] + boff, bstride, w, src, shape, op.alpha * scale, 1.0);
 }
 
 namespace k {

@@ -15,7 +15,10 @@
 // Evaluation.  A generated program (t3p_program.inc, written by gen_t3p.py
 // from the spin-orbital triples equations) of dense contractions over these
 // blocks, the dressed Fock matrix, the dressed DF factor and t2, run through
-// the engine's einsum planner.  Its four sections are run with the t2
+// the engine's einsum planner.  Contractions that share a large operand with
+// the same indices contracted are stacked into one product: their other
+// operands are copied into the rows of a stack S, W = X . S^T is one GEMM,
+// and each member's result is copied out of its columns of W.  Its four sections are run with the t2
 // operand bound to:
 //   pro  (R1, R2 from T3'; R3' from [H,T3'])      no t2
 //   lin  (R3' from [H,T2])                         T2
@@ -32,18 +35,23 @@ struct T3pTensor {
   int kind;          // 0 base operand, 1 slice of a base operand, 2 intermediate
   int base;          // base operand index (kinds 0, 1)
   const char* spec;  // slice selector, one character per base dimension
-  const char* dims;  // o / v / P per dimension
+  const char* dims;  // o / v / P per dimension; # = the rows of a stack
   int section;
+  const char* rows;  // stacks: '+'-separated dims of each member's rows
 };
 
 struct T3pOp {
   int section;
-  int kind;          // 0 slice, 1 contraction into `out`, 2 contraction accumulated into an output
+  // 0 slice, 1 contraction into `out`, 2 contraction accumulated into an
+  // output, 3 member operand `a` into its rows of stack `out`, 4 member's
+  // columns of stacked product `a` into `out` or (out < 0) into an output
+  int kind;
   int out, a, b;
-  const char* spec;  // einsum labels of a, b and the result
+  const char* spec;  // einsum labels of a, b and the result; kinds 3, 4: a permutation
   double alpha;
   int base;          // slice: the base operand; accumulate: the output base operand
   const char* outspec;
+  int member;        // kinds 3, 4: the member's index in its stack
 };
 
 // Base operands of the program, in the order of its tables.
@@ -69,8 +77,12 @@ class T3pProgram {
 
  private:
   std::vector<int64_t> base_shape(int b) const;
+  int64_t dims_extent(const char* dims) const;      // product of o / v / P extents
+  int64_t stack_rows(const char* rows, int upto) const;  // rows of the first `upto` members
   void select(int b, const char* spec, int64_t* offset, std::vector<int64_t>& shape,
               std::vector<int64_t>& stride) const;
+  void stack_copy(const T3pOp& op, cudaStream_t s, double* const* base, double scale,
+                  double* ws) const;
   int o_, v_, n_, naux_, h_, p_;
   std::vector<std::vector<int64_t>> shape_;
   std::vector<int64_t> offset_;  // element offset of each slice / intermediate
