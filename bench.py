@@ -423,6 +423,9 @@ def main():
     for _ in range(args.warmup):
         one_unit()
     torch.cuda.synchronize()
+    # kernel launches so far (this process has launched no others): lets an ncu
+    # launch list skip to the timed region (-s)
+    print(f"launches before the timed region: {ctx.launches()}", file=sys.stderr, flush=True)
     ctx.set_profiling(True)
     p0 = ctx.profile()
     sampler = ClockSampler(local)
