@@ -222,6 +222,240 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent variant for narrow products (N <= 128): 128 x 64 tiles, one CTA
+// per SM looping over the (M tile, N tile, K chunk) work items.  Warps 0-3
+// move accumulators out of TMEM (warp w reads lanes [32 w, 32 w + 32)), warp 4
+// issues the TMA loads, warp 5 the MMAs.  The ring runs on across work items,
+// and two TMEM accumulator sets let the epilogue of one tile overlap the MMAs
+// of the next; the epilogue stages its tile in a shared-memory buffer of its
+// own.  Every wait is bounded; after a timeout all roles stop and the kernel
+// frees its TMEM and returns.
+constexpr int NB = 64, NWARPS_N = 6;
+
+template <int LEVEL>
+struct NarrowRing {
+  static constexpr int A_TILE = BM * TK * 2;     // 8 KB
+  static constexpr int B_TILE = NB * TK * 2;     // 4 KB
+  static constexpr int A_BYTES = LEVEL * A_TILE;
+  static constexpr int STAGE_BYTES = LEVEL * (A_TILE + B_TILE);
+  static constexpr int STAGES = LEVEL == 3 ? 4 : LEVEL == 2 ? 6 : 8;
+  static constexpr int RING_BYTES = STAGES * STAGE_BYTES;
+  static constexpr int EPI = BM * (NB + 1) * 4;
+  static constexpr int SMEM_BYTES = RING_BYTES + EPI + 1024 + 512;
+  static constexpr int NACC = Ring<LEVEL>::NACC;
+  static constexpr int ACC_COLS = NACC * NB;      // one accumulator set
+  static constexpr int TMEM_COLS = ACC_COLS <= 64 ? 128 : 256;  // two sets
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
+};
+
+template <int LEVEL>
+__global__ void __launch_bounds__(32 * NWARPS_N, 1)
+gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
+                      const __grid_constant__ CUtensorMap bmap, int M, int N, int num_kt,
+                      int kt_chunk, int splitk, double alpha, double beta,
+                      double* __restrict__ C, long long ldc, float* __restrict__ ws, int* err,
+                      int trans) {
+  using G = NarrowRing<LEVEL>;
+  using R = Ring<LEVEL>;
+  constexpr int STAGES = G::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* epi = reinterpret_cast<float*>(smem + G::RING_BYTES);
+  uint64_t* bars = (uint64_t*)(smem + G::RING_BYTES + G::EPI);
+  // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]
+  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 4);
+  __shared__ int abort_flag, epi_fail;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                 accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
+  const int mt = (M + BM - 1) / BM, nt = (N + NB - 1) / NB;
+  const int items = mt * nt * splitk;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    epi_fail = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 4 * 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_holder;
+
+  auto decode = [&](int w, int& m0, int& n0, int& kt0, int& nkt) {
+    const int mi = w % mt, rest = w / mt, ni = rest % nt, kz = rest / nt;
+    m0 = mi * BM;
+    n0 = ni * NB;
+    kt0 = kz * kt_chunk;
+    nkt = max(0, min(kt_chunk, num_kt - kt0));
+  };
+
+  if (warp == 4 && lane == 0) {
+    // TMA producer: the ring runs on across work items
+    int it = 0;
+    for (int w = blockIdx.x; w < items && !*(volatile int*)&abort_flag; w += gridDim.x) {
+      int m0, n0, kt0, nkt;
+      decode(w, m0, n0, kt0, nkt);
+      for (int j = 0; j < nkt; ++j, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err, 11) || *(volatile int*)&abort_flag) {
+          abort_flag = 1;
+          break;
+        }
+        const int kx = (kt0 + j) * TK;
+        const uint32_t sa = smem_u32(smem + s * G::STAGE_BYTES);
+        mbar_expect_tx(full0 + 8 * s, G::STAGE_BYTES);
+        tma_load_3d(sa, &amap, full0 + 8 * s, kx, m0, 0);
+        tma_load_3d(sa + G::A_BYTES, &bmap, full0 + 8 * s, kx, n0, 0);
+      }
+    }
+  } else if (warp == 5 && lane == 0) {
+    // MMA issuer: one accumulator set per work item, alternating
+    constexpr uint32_t idesc = idesc_bf16(BM, NB);
+    int it = 0, tc = 0;
+    for (int w = blockIdx.x; w < items && !*(volatile int*)&abort_flag; w += gridDim.x, ++tc) {
+      int m0, n0, kt0, nkt;
+      decode(w, m0, n0, kt0, nkt);
+      const int buf = tc & 1;
+      const uint32_t aph = (uint32_t)((tc >> 1) & 1);
+      if (!mbar_wait(acce0 + 8 * buf, aph ^ 1u, err, 12)) {
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tacc = tmem + (uint32_t)(buf * G::ACC_COLS);
+      bool stop = false;
+      for (int j = 0; j < nkt; ++j, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+        if (!mbar_wait(full0 + 8 * s, ph, err, 13)) {
+          abort_flag = 1;
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(smem + s * G::STAGE_BYTES), sb = sa + G::A_BYTES;
+#pragma unroll
+        for (int p = 0; p < R::NPROD; ++p) {
+          const bool lead = R::pa(p) == 0 && R::pb(p) == 0;
+          const uint32_t acc = (R::NACC == 2 && !lead) ? (uint32_t)NB : 0u;
+          const bool first = j == 0 && (lead || p == 0);
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk) {
+            const uint64_t ad = sw64_desc(sa + R::pa(p) * G::A_TILE + kk * 32);
+            const uint64_t bd = sw64_desc(sb + R::pb(p) * G::B_TILE + kk * 32);
+            mma_bf16(tacc + acc, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(empty0 + 8 * s);
+      }
+      if (stop) break;
+      mma_commit(accf0 + 8 * buf);
+    }
+  } else if (warp < 4) {
+    // epilogue: row lrow of each tile; TMEM -> registers -> staging tile ->
+    // coalesced global stores (FP64 C, or FP32 split-K partials)
+    const int lrow = warp * 32 + lane;
+    const int t = threadIdx.x;  // 0..127
+    int tc = 0;
+    for (int w = blockIdx.x; w < items; w += gridDim.x, ++tc) {
+      int m0, n0, kt0, nkt;
+      decode(w, m0, n0, kt0, nkt);
+      const int buf = tc & 1;
+      const uint32_t aph = (uint32_t)((tc >> 1) & 1);
+      const bool ok = mbar_wait(accf0 + 8 * buf, aph, err, 14);
+      // all 128 epilogue threads agree before they touch the staging tile
+      if (!ok) epi_fail = 1;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (*(volatile int*)&epi_fail || *(volatile int*)&abort_flag) {
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t taddr = tmem + (uint32_t)(buf * G::ACC_COLS) + ((uint32_t)(warp * 32) << 16);
+      constexpr int PITCH = NB + 1;
+      if (nkt > 0) {
+#pragma unroll
+        for (int c0 = 0; c0 < NB; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(taddr + c0, r);
+          if (R::NACC == 2) {
+            uint32_t q[16];
+            tmem_ld16(taddr + NB + c0, q);
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj)
+              epi[lrow * PITCH + c0 + jj] = __uint_as_float(r[jj]) + __uint_as_float(q[jj]);
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) epi[lrow * PITCH + c0 + jj] = __uint_as_float(r[jj]);
+          }
+        }
+      } else {
+        for (int c = 0; c < NB; ++c) epi[lrow * PITCH + c] = 0.f;
+      }
+      // the accumulator set is free for the MMA warp again
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acce0 + 8 * buf);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const int rows = min(BM, M - m0), cols = min(NB, N - n0);
+      const int kz = w / (mt * nt);
+      if (!trans) {
+        // 2 rows per pass, 64 columns each
+        for (int rr = t / NB; rr < rows; rr += 128 / NB) {
+          const int c = t % NB;
+          if (c >= cols) continue;
+          const long long row = m0 + rr;
+          const float a = epi[rr * PITCH + c];
+          if (ws)
+            ws[((long long)kz * M + row) * N + n0 + c] = a;
+          else if (beta == 0.0)
+            C[row * ldc + n0 + c] = alpha * (double)a;
+          else
+            C[row * ldc + n0 + c] = fma(alpha, (double)a, beta * C[row * ldc + n0 + c]);
+        }
+      } else if (t < rows) {
+        // the caller's product is the transpose of this one: tile row t is
+        // column m0 + t of the caller's C (row n0 + c); consecutive threads
+        // write consecutive columns
+        for (int c = 0; c < cols; ++c) {
+          const long long crow = n0 + c, ccol = m0 + t;
+          const float a = epi[t * PITCH + c];
+          if (ws)
+            ws[((long long)kz * N + crow) * M + ccol] = a;
+          else if (beta == 0.0)
+            C[crow * ldc + ccol] = alpha * (double)a;
+          else
+            C[crow * ldc + ccol] = fma(alpha, (double)a, beta * C[crow * ldc + ccol]);
+        }
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 5) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // One step of the compensated split-K sum: hi + x by Fast2Sum, its rounding
 // error into lo.
 __device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
@@ -371,10 +605,18 @@ void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t ro
 
 int products_for(int level) { return level == 1 ? 1 : level == 2 ? 3 : 6; }
 
+// Products with at most this many columns run on the persistent 128 x 64
+// kernel; those with at most NARROW_M rows (and more columns) run on it with
+// the operands exchanged and the tile stored transposed.
+constexpr int64_t NARROW_N = 128, NARROW_M = 64;
+
 int splitk_for(int64_t M, int64_t N, int64_t K) {
   // K chunks of at most 2048 (FP32 accumulation error ~ 2^-24 sqrt(K/16) per chunk),
-  // and enough CTAs to fill the GPU for small M x N
-  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  // and enough work items to fill the GPU for small M x N
+  const bool swap = M <= NARROW_M && N > NARROW_N;
+  if (swap) std::swap(M, N);
+  const int64_t bn = N <= NARROW_N ? NB : BN;
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + bn - 1) / bn);
   const int64_t num_kt = (K + BK - 1) / BK;
   int64_t z = (K + 2047) / 2048;
   while (tiles * z < 2 * 152 && z < num_kt) ++z;
@@ -403,16 +645,60 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   });
   ASCC_CUDA(attr_err);
   const int64_t Kp = padded_k(K);
-  const CUtensorMap am = make_planes_map(A, M, Kp, M * Kp, level, BM);
-  const CUtensorMap bm =
-      make_planes_map(B, N, Kp, b_plane_stride > 0 ? b_plane_stride : N * Kp, level, BN);
+  const bool swap = M <= NARROW_M && N > NARROW_N;
+  const bool narrow = N <= NARROW_N || swap;
+  const int64_t bstride = b_plane_stride > 0 ? b_plane_stride : N * Kp;
+  const CUtensorMap am = swap ? make_planes_map(B, N, Kp, bstride, level, BM)
+                              : make_planes_map(A, M, Kp, M * Kp, level, BM);
+  const CUtensorMap bm = swap ? make_planes_map(A, M, Kp, M * Kp, level, NB)
+                              : make_planes_map(B, N, Kp, bstride, level, narrow ? NB : BN);
   count_flops(2.0 * (double)M * N * K);
   const int num_kt = (int)(Kp / TK);
   const int kt_chunk = (num_kt + splitk - 1) / splitk;
+  float* wsp = splitk > 1 ? ws : nullptr;
+  if (narrow) {
+    static std::once_flag narrow_once;
+    cudaError_t e = cudaSuccess;
+    std::call_once(narrow_once, [&] {
+      e = cudaFuncSetAttribute(gemm_tc_narrow_kernel<1>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               NarrowRing<1>::SMEM_BYTES);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_tc_narrow_kernel<2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 NarrowRing<2>::SMEM_BYTES);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_tc_narrow_kernel<3>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 NarrowRing<3>::SMEM_BYTES);
+    });
+    ASCC_CUDA(e);
+    const int64_t Mk = swap ? N : M, Nk = swap ? M : N;  // the kernel's product
+    const int64_t items = ((Mk + BM - 1) / BM) * ((Nk + NB - 1) / NB) * splitk;
+    ASCC_REQUIRE(items < (1ll << 31), "gemm_split: too many tiles");
+    const unsigned grid = (unsigned)std::min<int64_t>(items, 152);
+    const int threads = 32 * NWARPS_N, tr = swap ? 1 : 0;
+    if (level == 1)
+      gemm_tc_narrow_kernel<1><<<grid, threads, NarrowRing<1>::SMEM_BYTES, s>>>(
+          am, bm, (int)Mk, (int)Nk, num_kt, kt_chunk, splitk, alpha, beta, C, (long long)ldc, wsp,
+          err, tr);
+    else if (level == 2)
+      gemm_tc_narrow_kernel<2><<<grid, threads, NarrowRing<2>::SMEM_BYTES, s>>>(
+          am, bm, (int)Mk, (int)Nk, num_kt, kt_chunk, splitk, alpha, beta, C, (long long)ldc, wsp,
+          err, tr);
+    else
+      gemm_tc_narrow_kernel<3><<<grid, threads, NarrowRing<3>::SMEM_BYTES, s>>>(
+          am, bm, (int)Mk, (int)Nk, num_kt, kt_chunk, splitk, alpha, beta, C, (long long)ldc, wsp,
+          err, tr);
+    count_launch();
+    check_launch("gemm_tc_narrow");
+  }
   dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splitk);
   ASCC_REQUIRE(grid.y <= 65535, "gemm_split: N too large");
-  float* w = splitk > 1 ? ws : nullptr;
-  if (level == 1)
+  float* w = wsp;
+  if (narrow) {
+    // launched above
+  } else if (level == 1)
     gemm_tc_kernel<1><<<grid, NTHREADS, Ring<1>::SMEM_BYTES, s>>>(
         am, bm, (int)M, (int)N, num_kt, kt_chunk, alpha, beta, C, (long long)ldc, w, err);
   else if (level == 2)
@@ -421,8 +707,10 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   else
     gemm_tc_kernel<3><<<grid, NTHREADS, Ring<3>::SMEM_BYTES, s>>>(
         am, bm, (int)M, (int)N, num_kt, kt_chunk, alpha, beta, C, (long long)ldc, w, err);
-  count_launch();
-  check_launch("gemm_tc");
+  if (!narrow) {
+    count_launch();
+    check_launch("gemm_tc");
+  }
   if (splitk > 1) {
     const unsigned gy = (unsigned)std::min<int64_t>(M, 65535);
     if (N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0) {

@@ -36,6 +36,29 @@ def test_split_gemm_matches_fp64(M, N, K, level):
     assert err / scale < LEVEL_TOL[level], (err, scale)
 
 
+@pytest.mark.parametrize("level", [1, 2, 3])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 16), (130, 17, 200), (1000, 64, 96), (777, 65, 40),
+                                   (20000, 128, 200), (300, 100, 5000), (5000, 3, 70),
+                                   (17, 300, 200), (64, 1000, 3000), (1, 500, 100), (40, 129, 64)])
+def test_narrow_split_gemm_matches_fp64(M, N, K, level):
+    """Products with N <= 128, or M <= 64 (operands exchanged, tile stored
+    transposed), run on the persistent 128 x 64 kernel: several tiles per CTA,
+    ragged M, N and K, split K for K > 2048."""
+    import torch
+    import paper_2501_10515_gb300 as pkg
+    g = torch.Generator(device="cuda").manual_seed(M * 5 + N * 11 + K + level)
+    A = torch.randn(M, K, device="cuda", dtype=torch.float64, generator=g)
+    B = torch.randn(N, K, device="cuda", dtype=torch.float64, generator=g)
+    C0 = torch.randn(M, N, device="cuda", dtype=torch.float64, generator=g)
+    for beta in (0.0, -1.0):
+        C = C0.clone()
+        pkg.gemm_split_bf16(A, B, C, level, alpha=0.5, beta=beta)
+        torch.cuda.synchronize()
+        ref = 0.5 * (A @ B.T) + beta * C0
+        scale = (0.5 * (A.abs() @ B.abs().T)).max().item() + 1.0
+        assert (C - ref).abs().max().item() / scale < LEVEL_TOL[level]
+
+
 def test_split_gemm_levels_improve():
     import torch
     import paper_2501_10515_gb300 as pkg
