@@ -340,6 +340,26 @@ __global__ void gemv_t_partial(int64_t M, int64_t K, const double* __restrict__ 
   }
 }
 
+// Row matrix-vector product for few, long rows, first pass: block (c, m)
+// sums chunk c of row m (256 threads, a fixed tree order) into part[c][m].
+__global__ void gemv_n_partial(int64_t M, int64_t K, const double* __restrict__ A, int64_t lda,
+                               const double* __restrict__ x, int64_t kchunk,
+                               double* __restrict__ part) {
+  __shared__ double sh[8];
+  const int64_t m = blockIdx.y, k0 = blockIdx.x * kchunk, k1 = min(K, k0 + kchunk);
+  const double* a = A + m * lda;
+  double acc = 0.0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) acc = fma(a[k], x[k], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    part[blockIdx.x * M + m] = t;
+  }
+}
+
 __global__ void gemv_t_reduce(int64_t M, int nchunk, const double* __restrict__ part,
                               double alpha, double beta, double* __restrict__ y) {
   for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
@@ -741,8 +761,8 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
   // GPU: K is cut into z equal chunks (z divides K), each chunk's product goes
   // to its own FP64 slice and the slices are summed in a fixed order
   const int64_t tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
-  if (batch == 1 && tiles < 152 && K >= 2048) {
-    int64_t zmax = std::min<int64_t>(2 * 152 / tiles, K / 256);
+  if (batch == 1 && tiles < 152 && K >= 256) {
+    int64_t zmax = std::min<int64_t>(2 * 152 / tiles, K / 64);
     int64_t z = 1;
     for (int64_t c = zmax; c >= 2; --c)
       if (K % c == 0) {
@@ -943,6 +963,23 @@ void gemv_f64(cudaStream_t s, bool ta, int64_t M, int64_t K, double alpha, const
     ASCC_CUDA(cudaFreeAsync(part, s));
     count_launch(2);
     check_launch("gemv_t");
+    return;
+  }
+  if (!ta && M < 152 * 16 && K >= 2048) {
+    // few long rows (down to a single dot product): chunks of each row over
+    // the grid, summed in a fixed order
+    const int64_t want = (152 * 8 + M - 1) / M;
+    int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>(want, K / 2048));
+    const int64_t kchunk = (K + nchunk - 1) / nchunk;
+    nchunk = (K + kchunk - 1) / kchunk;
+    double* part = nullptr;
+    ASCC_CUDA(cudaMallocAsync(&part, sizeof(double) * (size_t)(nchunk * M), s));
+    gemv_n_partial<<<dim3((unsigned)nchunk, (unsigned)M), 256, 0, s>>>(M, K, A, lda, x, kchunk,
+                                                                      part);
+    gemv_t_reduce<<<grid_for(M), 256, 0, s>>>(M, (int)nchunk, part, alpha, beta, y);
+    ASCC_CUDA(cudaFreeAsync(part, s));
+    count_launch(2);
+    check_launch("gemv_n");
     return;
   }
   if (ta)

@@ -1,6 +1,8 @@
 // Executor of the generated T3' program (see t3p.h) and the kernels that move
 // the packed slice into its dense blocks and back.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "kernels.h"
@@ -16,6 +18,7 @@ int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
 
 T3pProgram::T3pProgram(int o, int v, int naux, int h, int p)
     : o_(o), v_(v), n_(o + v), naux_(naux), h_(h), p_(p) {
+  profile_path_ = std::getenv("ASCC_T3P_PROFILE");
   blk_off_[0] = 0;
   blk_off_[1] = (int64_t)o * v * v;
   blk_off_[2] = blk_off_[1] + (int64_t)o * v * v;
@@ -170,9 +173,19 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
     if (d.kind == 0) return T(base[d.base], base_shape(d.base));
     return T(ws + offset_[t], shape_[t]);
   };
+  // optional per-op timing (ASCC_T3P_PROFILE=<file>): CUDA events around
+  // every op, summed per op and written to the file when the program is freed
+  const bool prof = profile_path_ != nullptr;
+  if (prof && prof_ev_.empty()) {
+    prof_ev_.resize(2 * kT3pOpCount);
+    for (auto& e : prof_ev_) ASCC_CUDA(cudaEventCreate(&e));
+    prof_ms_.assign(kT3pOpCount, 0.0);
+    prof_n_.assign(kT3pOpCount, 0);
+  }
   for (int q = 0; q < kT3pOpCount; ++q) {
     const T3pOp& op = kT3pOps[q];
     if (op.section != section) continue;
+    if (prof) ASCC_CUDA(cudaEventRecord(prof_ev_[2 * q], s));
     if (op.kind == 0) {
       int64_t off;
       std::vector<int64_t> shape, stride;
@@ -201,6 +214,7 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
       if (whole) {
         es(op.spec, op.alpha * scale, tensor(op.a), tensor(op.b), 1.0,
            T(base[op.base], shape));
+        if (prof) ASCC_CUDA(cudaEventRecord(prof_ev_[2 * q + 1], s));
         continue;
       }
       double* tmp = ws + acc_off_;
@@ -218,8 +232,36 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
       }
       box_copy(s, base[op.base] + off, stride, tmp, ost, shape, 1.0, 1.0);
     }
+    if (prof) ASCC_CUDA(cudaEventRecord(prof_ev_[2 * q + 1], s));
   }
   es.set_split(es.level(), es.err(), min0);
+  if (prof) {
+    ASCC_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < kT3pOpCount; ++q) {
+      if (kT3pOps[q].section != section) continue;
+      float ms = 0.f;
+      ASCC_CUDA(cudaEventElapsedTime(&ms, prof_ev_[2 * q], prof_ev_[2 * q + 1]));
+      prof_ms_[q] += ms;
+      prof_n_[q] += 1;
+    }
+  }
+}
+
+T3pProgram::~T3pProgram() {
+  if (profile_path_ && !prof_ms_.empty()) {
+    if (FILE* f = std::fopen(profile_path_, "w")) {
+      std::fprintf(f, "op,section,kind,a_dims,b_dims,out_dims,spec,calls,ms\n");
+      auto dims = [&](int t) { return t >= 0 ? kT3pTensors[t].dims : ""; };
+      for (int q = 0; q < kT3pOpCount; ++q) {
+        const T3pOp& op = kT3pOps[q];
+        std::fprintf(f, "%d,%d,%d,%s,%s,%s,%s,%d,%.6f\n", q, op.section, op.kind, dims(op.a),
+                     dims(op.b), op.out >= 0 ? dims(op.out) : op.outspec, op.spec, prof_n_[q],
+                     prof_ms_[q]);
+      }
+      std::fclose(f);
+    }
+  }
+  for (auto& e : prof_ev_) cudaEventDestroy(e);
 }
 
 namespace {

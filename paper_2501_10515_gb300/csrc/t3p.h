@@ -63,6 +63,9 @@ class T3pProgram {
  public:
   // o, v, naux: sizes; h, p: the primary hole and particle.
   T3pProgram(int o, int v, int naux, int h, int p);
+  ~T3pProgram();
+  T3pProgram(const T3pProgram&) = delete;
+  T3pProgram& operator=(const T3pProgram&) = delete;
   // Device workspace of the intermediates (elements of double), with
   // intermediates whose lifetimes do not overlap sharing memory.
   int64_t workspace_elements() const { return ws_elems_; }
@@ -88,6 +91,11 @@ class T3pProgram {
   std::vector<int64_t> offset_;  // element offset of each slice / intermediate
   int64_t ws_elems_ = 0, acc_off_ = 0;
   int64_t blk_off_[5];
+  // per-op timing when ASCC_T3P_PROFILE names an output file
+  const char* profile_path_ = nullptr;
+  mutable std::vector<cudaEvent_t> prof_ev_;
+  mutable std::vector<double> prof_ms_;
+  mutable std::vector<int> prof_n_;
 };
 
 namespace k {
