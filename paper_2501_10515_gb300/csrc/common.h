@@ -43,6 +43,9 @@ void count_launch(int64_t n = 1);
 int64_t launch_total();
 void count_flops(double f);
 double flop_total();
+// the same counts for the calling thread only (exact deltas around a capture)
+int64_t thread_launches();
+double thread_flops();
 void check_launch(const char* what);
 // Stores the message returned by ascc_last_error() on this thread.
 void record_error(const std::string& msg);

@@ -67,7 +67,10 @@ void box_copy(cudaStream_t s, double* out, std::vector<int64_t> ostride, const d
 
 void* Einsum::scratch(int which, size_t bytes) const {
   DevBuf& b = scratch_[which];
-  if (b.bytes() < bytes) b.alloc(bytes + bytes / 8, s_);
+  if (b.bytes() < bytes) {
+    ASCC_REQUIRE(!frozen_, "einsum scratch would grow during a graph capture");
+    b.alloc(bytes + bytes / 8, s_);
+  }
   return b.as<void>();
 }
 
@@ -419,6 +422,7 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
                "precision must be ASCC_FP64, ASCC_MIXED_BF16 or ASCC_FP64_TC");
   ASCC_REQUIRE(opt_.diis_dim >= 1 && opt_.diis_dim <= 32, "diis_dim in 1..32");
   if (opt_.triples && hole_ >= 0) t3idx_host_ = t3p_index(o_, v_, hole_, particle_);
+  if (const char* env = std::getenv("ASCC_NO_GRAPHS")) t3_use_graphs_ = env[0] == '0';
   nu_ = v_ + (hole_ >= 0 ? 1 : 0);
   const int64_t N = namp();
   t_.make({N}, s);
@@ -568,6 +572,68 @@ void State::setup_triples() {
   ASCC_CUDA(cudaStreamSynchronize(s_));
 }
 
+void State::run_t3(int section, double* const* base, double scale) {
+  const T3pProgram& P = *t3p_;
+  double* ws = t3ws_.p();
+  if (!t3_use_graphs_ || P.profiling()) {
+    P.run(es_, s_, section, base, scale, ws);
+    return;
+  }
+  std::vector<uint64_t> key = {(uint64_t)section, (uint64_t)es_.level()};
+  uint64_t sb;
+  std::memcpy(&sb, &scale, sizeof(sb));
+  key.push_back(sb);
+  for (int b = 0; b < T3P_NBASE; ++b) key.push_back((uint64_t)(uintptr_t)base[b]);
+  auto it = t3_graphs_.find(key);
+  if (it == t3_graphs_.end()) {
+    // first run of this form: direct, which also sizes the einsum scratch
+    // (callers that pass new buffers on every call do not grow the cache)
+    if (t3_graphs_.size() >= 64) {
+      for (auto& kv : t3_graphs_)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      t3_graphs_.clear();
+    }
+    t3_graphs_.emplace(key, T3Graph{});
+    P.run(es_, s_, section, base, scale, ws);
+    return;
+  }
+  T3Graph& g = it->second;
+  if (!g.exec && !g.failed) {
+    const int64_t l0 = thread_launches();
+    const double f0 = thread_flops();
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      es_.freeze(true);
+      try {
+        P.run(es_, s_, section, base, scale, ws);
+      } catch (const std::exception&) {
+        ok = false;
+      }
+      es_.freeze(false);
+      ok = cudaStreamEndCapture(s_, &graph) == cudaSuccess && ok && graph;
+    }
+    // the captured launches did not run
+    g.launches = thread_launches() - l0;
+    g.flops = thread_flops() - f0;
+    count_launch(-g.launches);
+    count_flops(-g.flops);
+    if (ok && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) g.exec = nullptr;
+    if (graph) cudaGraphDestroy(graph);
+    if (!g.exec) {
+      g.failed = true;
+      cudaGetLastError();
+    }
+  }
+  if (g.exec) {
+    ASCC_CUDA(cudaGraphLaunch(g.exec, s_));
+    count_launch(g.launches);
+    count_flops(g.flops);
+  } else {
+    P.run(es_, s_, section, base, scale, ws);
+  }
+}
+
 // R3' and the T3' terms of R1 and R2 by the generated program (t3p.h); the
 // partially linearised state drops the T2^M T2^M and T2^M T3' parts of R3'
 // (Sec. II.C).
@@ -594,18 +660,18 @@ void State::triples(const T& t2, const double* t3, const T& r1, const T& r2, dou
     base[T3P_T2] = t;
     base[T3P_TS] = t3ts_.p();
   };
-  P.run(es_, s_, T3P_PRO, base, 1.0, ws);
+  run_t3(T3P_PRO, base, 1.0);
   bind(t2.p);
-  P.run(es_, s_, T3P_LIN, base, 1.0, ws);
-  P.run(es_, s_, T3P_QUAD, base, 1.0, ws);
+  run_t3(T3P_LIN, base, 1.0);
+  run_t3(T3P_QUAD, base, 1.0);
   if (opt_.linearize) {
     bind(m_.p());
-    P.run(es_, s_, T3P_QUAD, base, -1.0, ws);
+    run_t3(T3P_QUAD, base, -1.0);
     k::axpby(s_, t3nm_.p(), t2.p, 1.0, 0.0, n2());
     k::axpby(s_, t3nm_.p(), m_.p(), -1.0, 1.0, n2());
     bind(t3nm_.p());
   }
-  P.run(es_, s_, T3P_MIX, base, 1.0, ws);
+  run_t3(T3P_MIX, base, 1.0);
   k::t3p_gather(s_, r3, r3blk_.p(), t3dst_.as<int64_t>(), t3sgn_.as<signed char>(), N3);
 }
 
@@ -621,6 +687,8 @@ int State::level_for_phase() const {
 }
 
 State::~State() {
+  for (auto& kv : t3_graphs_)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   for (auto& ev : events_) {
     cudaEventDestroy(ev.first);
     cudaEventDestroy(ev.second);

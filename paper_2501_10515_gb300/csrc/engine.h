@@ -2,6 +2,7 @@
 // integrals, the per-state amplitude iteration.
 #pragma once
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -37,9 +38,13 @@ class Einsum {
   // Scratch of the tensor-core path, grown on demand and reused by every call
   // on this stream (calls on one stream never overlap).
   void* scratch(int which, size_t bytes) const;
+  // While frozen (a CUDA graph capture), the scratch must not be reallocated:
+  // a request beyond its size is an error instead.
+  void freeze(bool on) const { frozen_ = on; }
 
  private:
   cudaStream_t s_;
+  mutable bool frozen_ = false;
   int level_ = 0;
   int* err_ = nullptr;
   double min_flops_ = 4e7;
@@ -151,6 +156,17 @@ class State {
   // T3' slice: its residual R3' and its contributions to R1 and R2
   void triples(const T& t2, const double* t3, const T& r1, const T& r2, double* r3);
   void setup_triples();
+  // one section of the T3' program, replayed from a CUDA graph captured on its
+  // second run with the same level, operands and weight
+  void run_t3(int section, double* const* base, double scale);
+  struct T3Graph {
+    cudaGraphExec_t exec = nullptr;
+    bool failed = false;
+    int64_t launches = 0;
+    double flops = 0.0;
+  };
+  std::map<std::vector<uint64_t>, T3Graph> t3_graphs_;
+  bool t3_use_graphs_ = true;
   void foo_term(const T& t, const double* W, double alpha, const T& Z);
 
   std::shared_ptr<Molecule> mol_;

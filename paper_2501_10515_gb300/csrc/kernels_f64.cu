@@ -9,14 +9,24 @@ namespace ascc {
 
 static std::atomic<int64_t> g_launches{0};
 static std::atomic<double> g_flops{0.0};
-void count_launch(int64_t n) { g_launches += n; }
+namespace {
+thread_local int64_t tl_launches = 0;
+thread_local double tl_flops = 0.0;
+}  // namespace
+void count_launch(int64_t n) {
+  g_launches += n;
+  tl_launches += n;
+}
 int64_t launch_total() { return g_launches.load(); }
+int64_t thread_launches() { return tl_launches; }
 void count_flops(double f) {
+  tl_flops += f;
   double cur = g_flops.load();
   while (!g_flops.compare_exchange_weak(cur, cur + f)) {
   }
 }
 double flop_total() { return g_flops.load(); }
+double thread_flops() { return tl_flops; }
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)

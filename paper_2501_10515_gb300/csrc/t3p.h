@@ -76,6 +76,7 @@ class T3pProgram {
   // Sizes of the four blocks (elements) and the offsets of TA..TD (RA..RD)
   // in one concatenated buffer.
   int64_t block_elements() const { return blk_off_[4]; }
+  bool profiling() const { return profile_path_ != nullptr; }
   int64_t block_offset(int b) const { return blk_off_[b]; }
 
  private:
