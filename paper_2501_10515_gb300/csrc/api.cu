@@ -502,8 +502,10 @@ size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux, const ascc_optio
     // T3' blocks of t3 and R3', their workspace (intermediates of the
     // generated program, sized for the worst primary pair) and the t2 - t2^T
     // operands
-    T3pProgram prog(o, v, naux, 0, 0);
-    state += 8.0 * (2.0 * prog.block_elements() + prog.workspace_elements() + 2.0 * o2v2);
+    const int ns = t3p_streams();
+    T3pProgram prog(o, v, naux, 0, 0, ns);
+    state += 8.0 * ((2.0 + (ns > 1 ? ns : 0)) * prog.block_elements() +
+                    prog.workspace_elements() + 2.0 * o2v2);
   }
   return (size_t)((mol + state) * 1.1);
 }

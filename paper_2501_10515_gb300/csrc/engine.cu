@@ -520,7 +520,8 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
 // TC also receive the antisymmetric partner (c, b) / (k, j).
 void State::setup_triples() {
   const int o = o_, v = v_, h = hole_, p = particle_;
-  t3p_ = std::make_unique<T3pProgram>(o, v, naux_, h, p);
+  const int ns = t3p_streams();
+  t3p_ = std::make_unique<T3pProgram>(o, v, naux_, h, p, ns);
   const int64_t N3 = n3();
   std::vector<int64_t> dst(N3), dst2(N3);
   std::vector<signed char> sgn(N3);
@@ -567,6 +568,24 @@ void State::setup_triples() {
   t3blk_.make({t3p_->block_elements()}, s_);
   r3blk_.make({t3p_->block_elements()}, s_);
   t3ws_.make({t3p_->workspace_elements()}, s_);
+  if (ns > 1) {
+    t3x_ = std::make_unique<T3pStreams>();
+    T3pStreams& x = *t3x_;
+    x.streams.push_back(s_);
+    for (int k = 1; k < ns; ++k) {
+      cudaStream_t st;
+      ASCC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      x.streams.push_back(st);
+    }
+    for (int k = 0; k < ns; ++k) x.es.push_back(std::make_unique<Einsum>(x.streams[k]));
+    x.op_events.resize(t3p_->op_count());
+    for (auto& e : x.op_events) ASCC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ASCC_CUDA(cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming));
+    x.join.resize(ns);
+    for (auto& e : x.join) ASCC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    t3priv_.make({(int64_t)ns * t3p_->block_elements()}, s_);
+    x.priv = t3priv_.p();
+  }
   t3ts_.make({o, o, v, v}, s_);
   if (opt_.linearize) t3nm_.make({o, o, v, v}, s_);
   ASCC_CUDA(cudaStreamSynchronize(s_));
@@ -575,8 +594,22 @@ void State::setup_triples() {
 void State::run_t3(int section, double* const* base, double scale) {
   const T3pProgram& P = *t3p_;
   double* ws = t3ws_.p();
+  const bool conc = t3x_ && !P.profiling();
+  if (conc)
+    for (auto& e : t3x_->es) e->set_split(es_.level(), es_.err(), es_.min_flops());
+  auto direct = [&] {
+    if (conc)
+      P.run_streams(*t3x_, section, base, scale, ws);
+    else
+      P.run(es_, s_, section, base, scale, ws);
+  };
+  auto freeze = [&](bool on) {
+    es_.freeze(on);
+    if (t3x_)
+      for (auto& e : t3x_->es) e->freeze(on);
+  };
   if (!t3_use_graphs_ || P.profiling()) {
-    P.run(es_, s_, section, base, scale, ws);
+    direct();
     return;
   }
   std::vector<uint64_t> key = {(uint64_t)section, (uint64_t)es_.level()};
@@ -594,7 +627,7 @@ void State::run_t3(int section, double* const* base, double scale) {
       t3_graphs_.clear();
     }
     t3_graphs_.emplace(key, T3Graph{});
-    P.run(es_, s_, section, base, scale, ws);
+    direct();
     return;
   }
   T3Graph& g = it->second;
@@ -604,13 +637,13 @@ void State::run_t3(int section, double* const* base, double scale) {
     cudaGraph_t graph = nullptr;
     bool ok = cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      es_.freeze(true);
+      freeze(true);
       try {
-        P.run(es_, s_, section, base, scale, ws);
+        direct();
       } catch (const std::exception&) {
         ok = false;
       }
-      es_.freeze(false);
+      freeze(false);
       ok = cudaStreamEndCapture(s_, &graph) == cudaSuccess && ok && graph;
     }
     // the captured launches did not run
@@ -630,7 +663,7 @@ void State::run_t3(int section, double* const* base, double scale) {
     count_launch(g.launches);
     count_flops(g.flops);
   } else {
-    P.run(es_, s_, section, base, scale, ws);
+    direct();
   }
 }
 
@@ -689,6 +722,15 @@ int State::level_for_phase() const {
 State::~State() {
   for (auto& kv : t3_graphs_)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (t3x_) {
+    T3pStreams& x = *t3x_;
+    cudaStreamSynchronize(s_);
+    x.es.clear();
+    for (auto& e : x.op_events) cudaEventDestroy(e);
+    for (auto& e : x.join) cudaEventDestroy(e);
+    if (x.fork) cudaEventDestroy(x.fork);
+    for (size_t k = 1; k < x.streams.size(); ++k) cudaStreamDestroy(x.streams[k]);
+  }
   for (auto& ev : events_) {
     cudaEventDestroy(ev.first);
     cudaEventDestroy(ev.second);

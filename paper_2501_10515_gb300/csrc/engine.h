@@ -85,6 +85,7 @@ struct Molecule {
 };
 
 class T3pProgram;
+struct T3pStreams;
 
 struct Options {
   int precision = ASCC_FP64;
@@ -167,6 +168,10 @@ class State {
   };
   std::map<std::vector<uint64_t>, T3Graph> t3_graphs_;
   bool t3_use_graphs_ = true;
+  // streams of the concurrent T3' run (empty: one stream) and the private
+  // copies of the R3' blocks it accumulates into
+  std::unique_ptr<T3pStreams> t3x_;
+  OT t3priv_;
   void foo_term(const T& t, const double* W, double alpha, const T& Z);
 
   std::shared_ptr<Molecule> mol_;

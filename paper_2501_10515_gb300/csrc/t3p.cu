@@ -14,10 +14,20 @@ namespace {
 #include "t3p_program.inc"
 
 int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+std::vector<int64_t> rm_strides(const std::vector<int64_t>& shape) {
+  std::vector<int64_t> st(shape.size());
+  int64_t acc = 1;
+  for (int d = (int)shape.size() - 1; d >= 0; --d) {
+    st[d] = acc;
+    acc *= shape[d];
+  }
+  return st;
+}
 }  // namespace
 
-T3pProgram::T3pProgram(int o, int v, int naux, int h, int p)
-    : o_(o), v_(v), n_(o + v), naux_(naux), h_(h), p_(p) {
+T3pProgram::T3pProgram(int o, int v, int naux, int h, int p, int nstreams)
+    : o_(o), v_(v), n_(o + v), naux_(naux), h_(h), p_(p), nstreams_(std::max(1, nstreams)) {
   profile_path_ = std::getenv("ASCC_T3P_PROFILE");
   blk_off_[0] = 0;
   blk_off_[1] = (int64_t)o * v * v;
@@ -58,6 +68,10 @@ T3pProgram::T3pProgram(int o, int v, int naux, int h, int p)
     for (int t : {op.a, op.b})
       if (t >= 0 && kT3pTensors[t].section != T3P_QUAD) last[t] = std::max(last[t], quad_end);
   }
+  // on several streams an op may run while ops before it still do: memory is
+  // not handed on before a window of later ops has been issued (the stream
+  // plan then adds the waits for what is still shared)
+  const int window = nstreams_ > 1 ? 48 : 0;
   struct Slot { int64_t off, size; int s, e; };
   std::vector<Slot> placed;
   std::vector<int> order;
@@ -70,7 +84,7 @@ T3pProgram::T3pProgram(int o, int v, int naux, int h, int p)
     int64_t sz = 1;
     for (auto d : shape_[t]) sz *= d;
     sz = round_up(std::max<int64_t>(sz, 1), 32);
-    const int s = def[t], e = std::max(last[t], def[t]);
+    const int s = def[t], e = std::max(last[t], def[t]) + window;
     std::vector<std::pair<int64_t, int64_t>> live;
     for (const Slot& sl : placed)
       if (!(sl.e < s || sl.s > e)) live.push_back({sl.off, sl.size});
@@ -85,7 +99,134 @@ T3pProgram::T3pProgram(int o, int v, int naux, int h, int p)
     peak = std::max(peak, off + sz);
   }
   acc_off_ = round_up(peak, 32);
-  ws_elems_ = acc_off_ + round_up(acc_max, 32);
+  acc_len_ = round_up(acc_max, 32);
+  ws_elems_ = acc_off_ + acc_len_ * nstreams_;
+  if (nstreams_ > 1) plan_streams();
+}
+
+int T3pProgram::op_count() const { return kT3pOpCount; }
+
+int t3p_streams() {
+  if (const char* env = std::getenv("ASCC_T3P_STREAMS")) {
+    const int n = std::atoi(env);
+    return std::min(std::max(n, 1), 16);
+  }
+  return 6;
+}
+
+// Stream plan: dependencies of every op (writers of what it reads; earlier
+// users of any workspace range it writes), then a list schedule in program
+// order on estimated op times, each op on the stream where it can start
+// first; accumulations into R1 / R2 stay on stream 0.
+void T3pProgram::plan_streams() {
+  const int T = kT3pTensorCount, Q = kT3pOpCount;
+  std::vector<int64_t> size(T, 0);
+  for (int t = 0; t < T; ++t) {
+    int64_t e = 1;
+    for (auto d : shape_[t]) e *= d;
+    size[t] = e;
+  }
+  std::vector<std::vector<int>> writers(T), users(T);
+  for (int q = 0; q < Q; ++q) {
+    const T3pOp& op = kT3pOps[q];
+    if (op.out >= 0) {
+      writers[op.out].push_back(q);
+      users[op.out].push_back(q);
+    }
+    if (op.a >= 0) users[op.a].push_back(q);
+    if (op.b >= 0) users[op.b].push_back(q);
+  }
+  // tensors whose workspace ranges overlap
+  std::vector<std::vector<int>> overlap(T);
+  for (int t = 0; t < T; ++t) {
+    if (offset_[t] < 0) continue;
+    const int64_t a0 = offset_[t], a1 = offset_[t] + std::max<int64_t>(size[t], 1);
+    for (int u = 0; u < T; ++u) {
+      if (u == t || offset_[u] < 0) continue;
+      const int64_t b0 = offset_[u], b1 = offset_[u] + std::max<int64_t>(size[u], 1);
+      if (a0 < b1 && b0 < a1) overlap[t].push_back(u);
+    }
+  }
+  std::vector<std::vector<int>> full(Q);
+  for (int q = 0; q < Q; ++q) {
+    const T3pOp& op = kT3pOps[q];
+    auto add = [&](int d) {
+      if (d < q && kT3pOps[d].section == op.section) full[q].push_back(d);
+    };
+    for (int t : {op.a, op.b})
+      if (t >= 0)
+        for (int w : writers[t]) add(w);
+    if (op.out >= 0) {
+      for (int u : users[op.out])
+        if (u < q && kT3pOps[u].kind == 3) add(u);  // earlier rows of a stack
+      for (int y : overlap[op.out])
+        for (int u : users[y]) add(u);
+    }
+  }
+  // estimated time of an op (s): launch gaps plus data movement plus flops
+  auto cost = [&](int q) {
+    const T3pOp& op = kT3pOps[q];
+    double bytes = 0.0, flops = 0.0;
+    for (int t : {op.a, op.b, op.out})
+      if (t >= 0) bytes += 8.0 * (double)size[t];
+    if (op.kind == 1 || op.kind == 2) {
+      double f = 2.0;
+      const std::string sp(op.spec);
+      std::string seen;
+      const auto arrow = sp.find("->");
+      const auto comma = sp.find(',');
+      const std::string la = sp.substr(0, comma), lb = sp.substr(comma + 1, arrow - comma - 1);
+      for (int side = 0; side < 2; ++side) {
+        const std::string& l = side ? lb : la;
+        const int t = side ? op.b : op.a;
+        const std::vector<int64_t> sh = kT3pTensors[t].kind == 0
+                                            ? base_shape(kT3pTensors[t].base)
+                                            : shape_[t];
+        for (size_t d = 0; d < l.size() && d < sh.size(); ++d)
+          if (seen.find(l[d]) == std::string::npos) {
+            seen += l[d];
+            f *= (double)sh[d];
+          }
+      }
+      flops = f;
+    }
+    return 6e-6 + bytes / 3e12 + flops / 2e14;
+  };
+  op_stream_.assign(Q, 0);
+  deps_.assign(Q, {});
+  std::vector<double> finish(Q, 0.0), ready(nstreams_, 0.0);
+  int section = -1;
+  for (int q = 0; q < Q; ++q) {
+    const T3pOp& op = kT3pOps[q];
+    if (op.section != section) {
+      section = op.section;
+      std::fill(ready.begin(), ready.end(), 0.0);
+    }
+    double est = 0.0;
+    for (int d : full[q]) est = std::max(est, finish[d]);
+    const bool to_r12 = (op.kind == 2 || (op.kind == 4 && op.out < 0)) &&
+                        (op.base == T3P_R1 || op.base == T3P_R2);
+    int best = 0;
+    if (!to_r12) {
+      double bt = 1e300;
+      for (int k = 0; k < nstreams_; ++k) {
+        const double t0 = std::max(est, ready[k]);
+        if (t0 < bt - 1e-12) {
+          bt = t0;
+          best = k;
+        }
+      }
+    }
+    op_stream_[q] = best;
+    finish[q] = std::max(est, ready[best]) + cost(q);
+    ready[best] = finish[q];
+    // keep the latest dependency on each other stream
+    std::vector<int> latest(nstreams_, -1);
+    for (int d : full[q])
+      if (op_stream_[d] != best) latest[op_stream_[d]] = std::max(latest[op_stream_[d]], d);
+    for (int k = 0; k < nstreams_; ++k)
+      if (latest[k] >= 0) deps_[q].push_back(latest[k]);
+  }
 }
 
 int64_t T3pProgram::dims_extent(const char* dims) const {
@@ -164,15 +305,54 @@ void T3pProgram::select(int b, const char* spec, int64_t* offset, std::vector<in
 // block against a v x v one), and the FP64 units would serialise them.
 constexpr double kTcMinFlops = 1e6;
 
-void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* base,
-                     double scale, double* ws) const {
-  const double min0 = es.min_flops();
-  if (es.level() > 0) es.set_split(es.level(), es.err(), std::min(min0, kTcMinFlops));
+// One op.  base: the operands; outb: where accumulations into the output
+// blocks go (the outputs themselves, or a stream's private copies); tmp: room
+// for a product that lands in a slice of an output.
+void T3pProgram::exec_op(int q, Einsum& es, cudaStream_t s, double* const* base,
+                         double* const* outb, double scale, double* ws, double* tmp) const {
+  const T3pOp& op = kT3pOps[q];
   auto tensor = [&](int t) -> T {
     const T3pTensor& d = kT3pTensors[t];
     if (d.kind == 0) return T(base[d.base], base_shape(d.base));
     return T(ws + offset_[t], shape_[t]);
   };
+  auto pack = [](std::vector<int64_t>& shape, std::vector<int64_t>& a, std::vector<int64_t>& b) {
+    if (shape.empty()) {
+      shape = {1};
+      a = {1};
+      b = {1};
+    }
+  };
+  if (op.kind == 0) {
+    int64_t off;
+    std::vector<int64_t> shape, stride;
+    select(op.base, kT3pTensors[op.out].spec, &off, shape, stride);
+    std::vector<int64_t> ost = rm_strides(shape);
+    pack(shape, stride, ost);
+    box_copy(s, ws + offset_[op.out], ost, base[op.base] + off, stride, shape);
+  } else if (op.kind == 1) {
+    es(op.spec, op.alpha, tensor(op.a), tensor(op.b), 0.0, tensor(op.out));
+  } else if (op.kind == 3 || op.kind == 4) {
+    stack_copy(op, s, base, outb, scale, ws);
+  } else {
+    int64_t off;
+    std::vector<int64_t> shape, stride;
+    select(op.base, op.outspec, &off, shape, stride);
+    if (off == 0 && shape == base_shape(op.base)) {
+      es(op.spec, op.alpha * scale, tensor(op.a), tensor(op.b), 1.0, T(outb[op.base], shape));
+      return;
+    }
+    es(op.spec, op.alpha * scale, tensor(op.a), tensor(op.b), 0.0, T(tmp, shape));
+    std::vector<int64_t> ost = rm_strides(shape);
+    pack(shape, stride, ost);
+    box_copy(s, outb[op.base] + off, stride, tmp, ost, shape, 1.0, 1.0);
+  }
+}
+
+void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* base,
+                     double scale, double* ws) const {
+  const double min0 = es.min_flops();
+  if (es.level() > 0) es.set_split(es.level(), es.err(), std::min(min0, kTcMinFlops));
   // optional per-op timing (ASCC_T3P_PROFILE=<file>): CUDA events around
   // every op, summed per op and written to the file when the program is freed
   const bool prof = profile_path_ != nullptr;
@@ -183,55 +363,9 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
     prof_n_.assign(kT3pOpCount, 0);
   }
   for (int q = 0; q < kT3pOpCount; ++q) {
-    const T3pOp& op = kT3pOps[q];
-    if (op.section != section) continue;
+    if (kT3pOps[q].section != section) continue;
     if (prof) ASCC_CUDA(cudaEventRecord(prof_ev_[2 * q], s));
-    if (op.kind == 0) {
-      int64_t off;
-      std::vector<int64_t> shape, stride;
-      select(op.base, kT3pTensors[op.out].spec, &off, shape, stride);
-      std::vector<int64_t> ost(shape.size());
-      int64_t acc = 1;
-      for (int d = (int)shape.size() - 1; d >= 0; --d) {
-        ost[d] = acc;
-        acc *= shape[d];
-      }
-      if (shape.empty()) {
-        shape = {1};
-        stride = {1};
-        ost = {1};
-      }
-      box_copy(s, ws + offset_[op.out], ost, base[op.base] + off, stride, shape);
-    } else if (op.kind == 1) {
-      es(op.spec, op.alpha, tensor(op.a), tensor(op.b), 0.0, tensor(op.out));
-    } else if (op.kind == 3 || op.kind == 4) {
-      stack_copy(op, s, base, scale, ws);
-    } else {
-      int64_t off;
-      std::vector<int64_t> shape, stride;
-      select(op.base, op.outspec, &off, shape, stride);
-      const bool whole = off == 0 && shape == base_shape(op.base);
-      if (whole) {
-        es(op.spec, op.alpha * scale, tensor(op.a), tensor(op.b), 1.0,
-           T(base[op.base], shape));
-        if (prof) ASCC_CUDA(cudaEventRecord(prof_ev_[2 * q + 1], s));
-        continue;
-      }
-      double* tmp = ws + acc_off_;
-      es(op.spec, op.alpha * scale, tensor(op.a), tensor(op.b), 0.0, T(tmp, shape));
-      std::vector<int64_t> ost(shape.size());
-      int64_t acc = 1;
-      for (int d = (int)shape.size() - 1; d >= 0; --d) {
-        ost[d] = acc;
-        acc *= shape[d];
-      }
-      if (shape.empty()) {
-        shape = {1};
-        stride = {1};
-        ost = {1};
-      }
-      box_copy(s, base[op.base] + off, stride, tmp, ost, shape, 1.0, 1.0);
-    }
+    exec_op(q, es, s, base, base, scale, ws, ws + acc_off_);
     if (prof) ASCC_CUDA(cudaEventRecord(prof_ev_[2 * q + 1], s));
   }
   es.set_split(es.level(), es.err(), min0);
@@ -245,6 +379,52 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
       prof_n_[q] += 1;
     }
   }
+}
+
+// The same section spread over the streams of `ex` (ex.streams[0] is the
+// caller's stream): each op on its planned stream after the ops it depends
+// on (producers of its operands, earlier users of the memory it writes);
+// accumulations into RA..RD go to the stream's private copies, summed into
+// the outputs in stream order at the end; R1 / R2 accumulate on stream 0.
+void T3pProgram::run_streams(T3pStreams& ex, int section, double* const* base, double scale,
+                             double* ws) const {
+  const int ns = (int)ex.streams.size();
+  cudaStream_t s0 = ex.streams[0];
+  const int64_t nb = block_elements();
+  k::fill(s0, ex.priv, 0.0, nb * ns);
+  ASCC_CUDA(cudaEventRecord(ex.fork, s0));
+  for (int k = 1; k < ns; ++k) ASCC_CUDA(cudaStreamWaitEvent(ex.streams[k], ex.fork, 0));
+  std::vector<double> min0(ns);
+  for (int k = 0; k < ns; ++k) {
+    Einsum& e = *ex.es[k];
+    min0[k] = e.min_flops();
+    if (e.level() > 0) e.set_split(e.level(), e.err(), std::min(min0[k], kTcMinFlops));
+  }
+  std::vector<double*> outb(T3P_NBASE * ns);
+  for (int k = 0; k < ns; ++k) {
+    for (int b = 0; b < T3P_NBASE; ++b) outb[k * T3P_NBASE + b] = base[b];
+    for (int b = 0; b < 4; ++b) outb[k * T3P_NBASE + T3P_RA + b] = ex.priv + k * nb + blk_off_[b];
+  }
+  for (int q = 0; q < kT3pOpCount; ++q) {
+    if (kT3pOps[q].section != section) continue;
+    const int st = op_stream_[q] % ns;
+    cudaStream_t s = ex.streams[st];
+    for (int d : deps_[q])
+      if (kT3pOps[d].section == section && op_stream_[d] % ns != st)
+        ASCC_CUDA(cudaStreamWaitEvent(s, ex.op_events[d], 0));
+    exec_op(q, *ex.es[st], s, base, outb.data() + st * T3P_NBASE, scale, ws,
+            ws + acc_off_ + st * acc_len_);
+    ASCC_CUDA(cudaEventRecord(ex.op_events[q], s));
+  }
+  for (int k = 0; k < ns; ++k) {
+    Einsum& e = *ex.es[k];
+    e.set_split(e.level(), e.err(), min0[k]);
+  }
+  for (int k = 1; k < ns; ++k) {
+    ASCC_CUDA(cudaEventRecord(ex.join[k], ex.streams[k]));
+    ASCC_CUDA(cudaStreamWaitEvent(s0, ex.join[k], 0));
+  }
+  k::sum_rows(s0, base[T3P_RA], ex.priv, nb, ns);
 }
 
 T3pProgram::~T3pProgram() {
@@ -277,15 +457,6 @@ std::string member_dims(const char* rows, int m) {
   return d;
 }
 
-std::vector<int64_t> row_major(const std::vector<int64_t>& shape) {
-  std::vector<int64_t> st(shape.size());
-  int64_t acc = 1;
-  for (int d = (int)shape.size() - 1; d >= 0; --d) {
-    st[d] = acc;
-    acc *= shape[d];
-  }
-  return st;
-}
 }  // namespace
 
 // Kind 3: member operand Y (labels: spec before ->) into rows [off, off + N_m)
@@ -293,8 +464,8 @@ std::vector<int64_t> row_major(const std::vector<int64_t>& shape) {
 // labels, then the contracted ones).  Kind 4: the member's columns of the
 // stacked product W[F...][#] (labels: F, then the member's free labels) into
 // its intermediate, or accumulated into an output block.
-void T3pProgram::stack_copy(const T3pOp& op, cudaStream_t s, double* const* base, double scale,
-                            double* ws) const {
+void T3pProgram::stack_copy(const T3pOp& op, cudaStream_t s, double* const* base,
+                            double* const* outb, double scale, double* ws) const {
   const std::string spec(op.spec);
   const auto arrow = spec.find("->");
   const std::string lhs = spec.substr(0, arrow), rhs = spec.substr(arrow + 2);
@@ -310,12 +481,12 @@ void T3pProgram::stack_copy(const T3pOp& op, cudaStream_t s, double* const* base
     for (auto d : kshape) kprod *= d;
     std::vector<int64_t> gshape;
     for (char c : gd) gshape.push_back(ext(c));
-    std::vector<int64_t> dst = row_major(gshape), kst = row_major(kshape);
+    std::vector<int64_t> dst = rm_strides(gshape), kst = rm_strides(kshape);
     for (auto& x : dst) x *= kprod;
     dst.insert(dst.end(), kst.begin(), kst.end());
     const T3pTensor& Yd = kT3pTensors[op.a];
     const std::vector<int64_t> yshape = Yd.kind == 0 ? base_shape(Yd.base) : shape_[op.a];
-    const std::vector<int64_t> yst = row_major(yshape);
+    const std::vector<int64_t> yst = rm_strides(yshape);
     const double* y = Yd.kind == 0 ? base[Yd.base] : ws + offset_[op.a];
     std::vector<int64_t> src, shape;
     for (char c : rhs) {
@@ -339,7 +510,7 @@ void T3pProgram::stack_copy(const T3pOp& op, cudaStream_t s, double* const* base
   std::vector<int64_t> fshape, gshape;
   for (char c : fd) fshape.push_back(ext(c));
   for (char c : gd) gshape.push_back(ext(c));
-  std::vector<int64_t> fst = row_major(fshape), gst = row_major(gshape);
+  std::vector<int64_t> fst = rm_strides(fshape), gst = rm_strides(gshape);
   for (auto& x : fst) x *= ntot;
   std::vector<int64_t> lab_st(fst), lab_ext(fshape);
   lab_st.insert(lab_st.end(), gst.begin(), gst.end());
@@ -354,7 +525,7 @@ void T3pProgram::stack_copy(const T3pOp& op, cudaStream_t s, double* const* base
   const double* w = ws + offset_[op.a] + off;
   if (op.out >= 0) {
     ASCC_REQUIRE(shape_[op.out] == shape, "T3' program: unstack result shape");
-    std::vector<int64_t> dst = row_major(shape_[op.out]);
+    std::vector<int64_t> dst = rm_strides(shape_[op.out]);
     if (shape.empty()) {
       shape = {1};
       src = {1};
@@ -372,7 +543,7 @@ void T3pProgram::stack_copy(const T3pOp& op, cudaStream_t s, double* const* base
     src = {1};
     bstride = {1};
   }
-  box_copy(s, base[op.base] + boff, bstride, w, src, shape, op.alpha * scale, 1.0);
+  box_copy(s, outb[op.base] + boff, bstride, w, src, shape, op.alpha * scale, 1.0);
 }
 
 namespace k {
@@ -409,6 +580,25 @@ void t3p_unpack(cudaStream_t s, double* blocks, int64_t nblk, const double* t3,
   t3p_unpack_kernel<<<blocks_for(n3), 256, 0, s>>>(blocks, t3, dst, dst2, sgn, n3);
   count_launch();
   check_launch("t3p_unpack");
+}
+
+namespace {
+__global__ void sum_rows_kernel(double* __restrict__ out, const double* __restrict__ part,
+                                int64_t n, int nparts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double t = out[i];
+    for (int k = 0; k < nparts; ++k) t += part[k * n + i];
+    out[i] = t;
+  }
+}
+}  // namespace
+
+void sum_rows(cudaStream_t s, double* out, const double* part, int64_t n, int nparts) {
+  if (n <= 0) return;
+  sum_rows_kernel<<<blocks_for(n), 256, 0, s>>>(out, part, n, nparts);
+  count_launch();
+  check_launch("sum_rows");
 }
 
 void t3p_gather(cudaStream_t s, double* r3, const double* blocks, const int64_t* dst,

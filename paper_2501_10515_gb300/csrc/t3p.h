@@ -59,10 +59,26 @@ enum T3pBase { T3P_F = 0, T3P_B, T3P_T2, T3P_TS, T3P_TA, T3P_TB, T3P_TC, T3P_TD,
                T3P_R2, T3P_RA, T3P_RB, T3P_RC, T3P_RD, T3P_NBASE };
 enum T3pSection { T3P_PRO = 0, T3P_LIN, T3P_QUAD, T3P_MIX };
 
+// Streams, per-stream planners, events and private output copies of a
+// concurrent run (T3pProgram::run_streams); owned by the caller.
+struct T3pStreams {
+  std::vector<cudaStream_t> streams;          // [0] is the caller's stream
+  std::vector<std::unique_ptr<Einsum>> es;    // one planner per stream
+  std::vector<cudaEvent_t> op_events;         // one per op
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;              // one per stream
+  double* priv = nullptr;                     // [streams][block_elements]
+};
+
+// Streams of a concurrent T3' run: ASCC_T3P_STREAMS if set (1 = one
+// stream), else the default.
+int t3p_streams();
+
 class T3pProgram {
  public:
-  // o, v, naux: sizes; h, p: the primary hole and particle.
-  T3pProgram(int o, int v, int naux, int h, int p);
+  // o, v, naux: sizes; h, p: the primary hole and particle; nstreams: the
+  // streams a concurrent run may use (the workspace and the plan depend on it).
+  T3pProgram(int o, int v, int naux, int h, int p, int nstreams = 1);
   ~T3pProgram();
   T3pProgram(const T3pProgram&) = delete;
   T3pProgram& operator=(const T3pProgram&) = delete;
@@ -73,6 +89,11 @@ class T3pProgram {
   // the binding of that section); scale multiplies every accumulation.
   void run(Einsum& es, cudaStream_t s, int section, double* const* base, double scale,
            double* ws) const;
+  // The same on several streams (dependencies by events, deterministic sums).
+  void run_streams(T3pStreams& ex, int section, double* const* base, double scale,
+                   double* ws) const;
+  int nstreams() const { return nstreams_; }
+  int op_count() const;
   // Sizes of the four blocks (elements) and the offsets of TA..TD (RA..RD)
   // in one concatenated buffer.
   int64_t block_elements() const { return blk_off_[4]; }
@@ -85,12 +106,18 @@ class T3pProgram {
   int64_t stack_rows(const char* rows, int upto) const;  // rows of the first `upto` members
   void select(int b, const char* spec, int64_t* offset, std::vector<int64_t>& shape,
               std::vector<int64_t>& stride) const;
-  void stack_copy(const T3pOp& op, cudaStream_t s, double* const* base, double scale,
-                  double* ws) const;
+  void stack_copy(const T3pOp& op, cudaStream_t s, double* const* base, double* const* outb,
+                  double scale, double* ws) const;
+  void exec_op(int q, Einsum& es, cudaStream_t s, double* const* base, double* const* outb,
+               double scale, double* ws, double* tmp) const;
+  void plan_streams();
   int o_, v_, n_, naux_, h_, p_;
   std::vector<std::vector<int64_t>> shape_;
   std::vector<int64_t> offset_;  // element offset of each slice / intermediate
-  int64_t ws_elems_ = 0, acc_off_ = 0;
+  int64_t ws_elems_ = 0, acc_off_ = 0, acc_len_ = 0;
+  int nstreams_ = 1;
+  std::vector<int> op_stream_;            // planned stream of each op
+  std::vector<std::vector<int>> deps_;    // ops each op waits for (latest per stream)
   int64_t blk_off_[5];
   // per-op timing when ASCC_T3P_PROFILE names an output file
   const char* profile_path_ = nullptr;
@@ -107,6 +134,8 @@ void t3p_unpack(cudaStream_t s, double* blocks, int64_t nblk, const double* t3,
                 const int64_t* dst, const int64_t* dst2, const signed char* sgn, int64_t n3);
 void t3p_gather(cudaStream_t s, double* r3, const double* blocks, const int64_t* dst,
                 const signed char* sgn, int64_t n3);
+// out[i] += sum_k part[k * n + i], k = 0..nparts-1 in order
+void sum_rows(cudaStream_t s, double* out, const double* part, int64_t n, int nparts);
 }  // namespace k
 
 }  // namespace ascc
