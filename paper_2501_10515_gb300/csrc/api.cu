@@ -505,7 +505,8 @@ size_t ascc_footprint_bytes(int32_t o, int32_t v, int32_t naux, const ascc_optio
     const int ns = t3p_streams();
     T3pProgram prog(o, v, naux, 0, 0, ns);
     state += 8.0 * ((2.0 + (ns > 1 ? ns : 0)) * prog.block_elements() +
-                    prog.workspace_elements() + 2.0 * o2v2);
+                    prog.workspace_elements() + 2.0 * o2v2) +
+             (double)ns * prog.cache_bytes();
   }
   return (size_t)((mol + state) * 1.1);
 }

@@ -123,4 +123,22 @@ struct OT {
   operator const T&() const { return t; }
 };
 
+// A strided tensor read as a matrix: row r = (r_0, .., r_{nm-1}) and column
+// k = (k_0, .., k_{nk-1}) in row-major digit order over mext / kext; the
+// element is at sum_d r_d mstr[d] + sum_d k_d kstr[d] (in elements).
+struct MatView {
+  int nm = 0, nk = 0;
+  int64_t mext[4] = {}, mstr[4] = {}, kext[4] = {}, kstr[4] = {};
+  int64_t rows() const {
+    int64_t n = 1;
+    for (int d = 0; d < nm; ++d) n *= mext[d];
+    return n;
+  }
+  int64_t cols() const {
+    int64_t n = 1;
+    for (int d = 0; d < nk; ++d) n *= kext[d];
+    return n;
+  }
+};
+
 }  // namespace ascc

@@ -65,6 +65,12 @@ void box_copy(cudaStream_t s, double* out, std::vector<int64_t> ostride, const d
                   alpha, beta);
 }
 
+void Einsum::cache_reset(size_t bytes) const {
+  cache_.clear();
+  cache_used_ = 0;
+  if (cache_buf_.bytes() < bytes && !frozen_) cache_buf_.alloc(bytes, s_);
+}
+
 void* Einsum::scratch(int which, size_t bytes) const {
   DevBuf& b = scratch_[which];
   if (b.bytes() < bytes) {
@@ -89,8 +95,48 @@ void Einsum::perm(const char* spec, double alpha, const T& A, double beta, const
   box_copy(s_, C.p, row_major_strides(C.shape), A.p, istride, shape, alpha, beta);
 }
 
+namespace {
+// X (labels xl, row-major) as the matrix [rows ml][cols kl]: each side's
+// dimensions in label order, unit dimensions dropped and neighbours that are
+// contiguous in X merged.  False when a side needs more than 4 dimensions or
+// neither side's last dimension is contiguous (its reads would not coalesce;
+// a contiguous row side is read by the transposing split kernels).
+bool matrix_view(const T& X, const std::string& xl, const std::string& ml, const std::string& kl,
+                 MatView& v, bool any_layout = false) {
+  const auto st = row_major_strides(X.shape);
+  auto side = [&](const std::string& l, int64_t* ext, int64_t* str, int& n) {
+    n = 0;
+    for (char ch : l) {
+      const auto pos = xl.find(ch);
+      const int64_t e = X.shape[pos], s = st[pos];
+      if (e == 1) continue;
+      if (n > 0 && str[n - 1] == s * e) {
+        ext[n - 1] *= e;
+        str[n - 1] = s;
+        continue;
+      }
+      if (n == 4) return false;
+      ext[n] = e;
+      str[n] = s;
+      ++n;
+    }
+    if (n == 0) {
+      ext[0] = 1;
+      str[0] = 0;
+      n = 1;
+    }
+    return true;
+  };
+  if (!side(ml, v.mext, v.mstr, v.nm) || !side(kl, v.kext, v.kstr, v.nk)) return false;
+  return any_layout || v.kstr[v.nk - 1] == 1 || v.mstr[v.nm - 1] == 1;
+}
+}  // namespace
+
 void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, double beta,
                         const T& C) const {
+  // the operand keys hold for this call only
+  const int64_t key_a = key_a_, key_b = key_b_;
+  key_a_ = key_b_ = -1;
   Spec sp = parse(spec, true);
   ASCC_REQUIRE((int)sp.a.size() == A.nd() && (int)sp.b.size() == B.nd() &&
                    (int)sp.c.size() == C.nd(),
@@ -123,6 +169,15 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
     for (char ch : l) p *= size[ch];
     return p;
   };
+  // an output laid out [batch][N][M]: the same product with the operands
+  // exchanged writes it directly
+  if (sp.c != bat + Ml + Nl && sp.c == bat + Nl + Ml) {
+    const std::string sw = sp.b + "," + sp.a + "->" + sp.c;
+    key_a_ = key_b;
+    key_b_ = key_a;
+    (*this)(sw.c_str(), alpha, B, A, beta, C);
+    return;
+  }
   const int64_t nb = prod(bat), Ms = prod(Ml), Ns = prod(Nl), Ks = prod(Kl);
   auto shape_of = [&](const std::string& l) {
     std::vector<int64_t> sh;
@@ -131,52 +186,110 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
   };
 
   const std::string cl = bat + Ml + Nl;
+  if (Ks == 1 && C.nd() <= 8) {
+    // no contraction (an outer product or a scaled copy): written in place
+    const auto ast = row_major_strides(A.shape), bst = row_major_strides(B.shape);
+    const auto cst = row_major_strides(C.shape);
+    std::vector<int64_t> as(C.nd(), 0), bs(C.nd(), 0);
+    for (int d = 0; d < C.nd(); ++d) {
+      const auto pa = sp.a.find(sp.c[d]), pb = sp.b.find(sp.c[d]);
+      if (pa != std::string::npos) as[d] = ast[pa];
+      if (pb != std::string::npos) bs[d] = bst[pb];
+    }
+    k::outer(s_, C.p, cst.data(), A.p, as.data(), B.p, bs.data(), C.nd(), C.shape.data(), alpha,
+             beta);
+    return;
+  }
   if (level_ > 0 && nb == 1 && Ms > 1 && Ns > 1 && 2.0 * Ms * Ns * Ks >= min_flops_) {
-    // tensor-core path: A as [M][K], B as [N][K] (K contiguous), split into BF16 planes
-    const double* Am = A.p;
-    OT Am_t, Bn_t;
-    if (sp.a != Ml + Kl) {
-      Am_t.make(shape_of(Ml + Kl), s_);
-      perm((sp.a + "->" + Ml + Kl).c_str(), 1.0, A, 0.0, Am_t.t);
-      Am = Am_t.p();
-    }
-    const double* Bn = B.p;
-    if (sp.b != Nl + Kl) {
-      Bn_t.make(shape_of(Nl + Kl), s_);
-      perm((sp.b + "->" + Nl + Kl).c_str(), 1.0, B, 0.0, Bn_t.t);
-      Bn = Bn_t.p();
-    }
-    if (level_ == 4) {
+    // tensor-core path: A as [M][K], B as [N][K] (K contiguous), split into
+    // BF16 planes (or digit planes at level 4).  An operand in another layout
+    // is split through a strided view when one of its sides is contiguous,
+    // else permuted first; planes of a keyed operand come from the cache when
+    // the same arrangement was split before.
+    const bool oz_level = level_ == 4;
+    const int64_t Kp = oz_level ? oz::padded_k(Ks) : tc::padded_k(Ks);
+    const int nplanes = oz_level ? oz::NSLICE : level_;
+    struct Planes {
+      __nv_bfloat16* p = nullptr;
+      int32_t* e = nullptr;
+    };
+    auto planes = [&](const T& X, const std::string& xl, const std::string& ml, int64_t key,
+                      int which) {
+      const int64_t rows = prod(ml);
+      const size_t pbytes = sizeof(__nv_bfloat16) * (size_t)(nplanes * rows * Kp);
+      const size_t ebytes = oz_level ? sizeof(int32_t) * (size_t)rows : 0;
+      std::string sig;
+      if (key >= 0) {
+        sig = std::to_string(level_) + ":";
+        for (char ch : ml) sig += std::to_string(xl.find(ch)) + ",";
+        sig += "|";
+        for (char ch : Kl) sig += std::to_string(xl.find(ch)) + ",";
+        for (const auto& c : cache_)
+          if (c.key == key && c.sig == sig) {
+            Planes r;
+            r.p = reinterpret_cast<__nv_bfloat16*>(cache_buf_.as<char>() + c.off);
+            if (oz_level) r.e = reinterpret_cast<int32_t*>(cache_buf_.as<char>() + c.off + pbytes);
+            return r;
+          }
+      }
+      Planes r;
+      const size_t need = (pbytes + ebytes + 255) / 256 * 256;
+      if (key >= 0 && cache_buf_.bytes() > 0 && cache_used_ + need <= cache_buf_.bytes()) {
+        r.p = reinterpret_cast<__nv_bfloat16*>(cache_buf_.as<char>() + cache_used_);
+        if (oz_level) r.e = reinterpret_cast<int32_t*>(cache_buf_.as<char>() + cache_used_ + pbytes);
+        cache_.push_back({key, sig, cache_used_});
+        cache_used_ += need;
+      } else {
+        r.p = static_cast<__nv_bfloat16*>(scratch(which, pbytes));
+        if (oz_level) r.e = static_cast<int32_t*>(scratch(3 + which, ebytes));
+      }
+      MatView vx;
+      if (xl == ml + Kl) {
+        if (oz_level)
+          oz::split(s_, r.p, r.e, X.p, rows, Ks, Ks);
+        else
+          tc::split_bf16(s_, r.p, X.p, rows, Ks, Ks, level_);
+      } else if (matrix_view(X, xl, ml, Kl, vx)) {
+        if (oz_level)
+          oz::split_view(s_, r.p, r.e, X.p, vx);
+        else
+          tc::split_bf16_view(s_, r.p, X.p, vx, level_);
+      } else {
+        OT Xt(shape_of(ml + Kl), s_);
+        perm((xl + "->" + ml + Kl).c_str(), 1.0, X, 0.0, Xt.t);
+        if (oz_level)
+          oz::split(s_, r.p, r.e, Xt.p(), rows, Ks, Ks);
+        else
+          tc::split_bf16(s_, r.p, Xt.p(), rows, Ks, Ks, level_);
+      }
+      return r;
+    };
+    const Planes qa = planes(A, sp.a, Ml, key_a, 0), qb = planes(B, sp.b, Nl, key_b, 1);
+    if (oz_level) {
       // exact digit-plane products (FP64-class)
-      const int64_t Kq = oz::padded_k(Ks);
-      auto* pa = static_cast<__nv_bfloat16*>(
-          scratch(0, sizeof(__nv_bfloat16) * (size_t)(oz::NSLICE * Ms * Kq)));
-      auto* pb = static_cast<__nv_bfloat16*>(
-          scratch(1, sizeof(__nv_bfloat16) * (size_t)(oz::NSLICE * Ns * Kq)));
-      auto* ea = static_cast<int32_t*>(scratch(3, sizeof(int32_t) * (size_t)Ms));
-      auto* eb = static_cast<int32_t*>(scratch(4, sizeof(int32_t) * (size_t)Ns));
-      oz::split(s_, pa, ea, Am, Ms, Ks, Ks);
-      oz::split(s_, pb, eb, Bn, Ns, Ks, Ks);
       auto* ws = static_cast<long long*>(scratch(2, oz::ws_bytes(Ms, Ns)));
       const int z = oz::splitk_for(Ms, Ns, Ks);
       if (sp.c == cl) {
-        oz::gemm(s_, Ms, Ns, Ks, alpha, pa, ea, 0, pb, eb, 0, beta, C.p, Ns, ws, err_, z);
+        oz::gemm(s_, Ms, Ns, Ks, alpha, qa.p, qa.e, 0, qb.p, qb.e, 0, beta, C.p, Ns, ws, err_, z);
       } else {
         OT Ct(shape_of(cl), s_);
-        oz::gemm(s_, Ms, Ns, Ks, 1.0, pa, ea, 0, pb, eb, 0, 0.0, Ct.p(), Ns, ws, err_, z);
+        oz::gemm(s_, Ms, Ns, Ks, 1.0, qa.p, qa.e, 0, qb.p, qb.e, 0, 0.0, Ct.p(), Ns, ws, err_, z);
         perm((cl + "->" + sp.c).c_str(), alpha, Ct.t, beta, C);
       }
       return;
     }
-    const int64_t Kp = tc::padded_k(Ks);
-    auto* pa = static_cast<__nv_bfloat16*>(scratch(0, sizeof(__nv_bfloat16) * (size_t)(level_ * Ms * Kp)));
-    auto* pb = static_cast<__nv_bfloat16*>(scratch(1, sizeof(__nv_bfloat16) * (size_t)(level_ * Ns * Kp)));
-    tc::split_bf16(s_, pa, Am, Ms, Ks, Ks, level_);
-    tc::split_bf16(s_, pb, Bn, Ns, Ks, Ks, level_);
+    const __nv_bfloat16 *pa = qa.p, *pb = qb.p;
     const int z = tc::splitk_for(Ms, Ns, Ks);
-    float* ws = z > 1 ? static_cast<float*>(scratch(2, sizeof(float) * (size_t)(z * Ms * Ns))) : nullptr;
+    // an output in another layout is written through a view by the reduction
+    MatView vc;
+    const bool view_c = sp.c != cl && matrix_view(C, sp.c, Ml, Nl, vc, true);
+    float* ws = (z > 1 || view_c)
+                    ? static_cast<float*>(scratch(2, sizeof(float) * (size_t)(z * Ms * Ns)))
+                    : nullptr;
     if (sp.c == cl) {
       tc::gemm_split(s_, Ms, Ns, Ks, level_, alpha, pa, pb, beta, C.p, Ns, err_, z, ws);
+    } else if (view_c) {
+      tc::gemm_split(s_, Ms, Ns, Ks, level_, alpha, pa, pb, beta, C.p, 0, err_, z, ws, 0, &vc);
     } else {
       OT Ct(shape_of(cl), s_);
       tc::gemm_split(s_, Ms, Ns, Ks, level_, 1.0, pa, pb, 0.0, Ct.p(), Ns, err_, z, ws);

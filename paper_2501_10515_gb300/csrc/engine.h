@@ -41,8 +41,27 @@ class Einsum {
   // While frozen (a CUDA graph capture), the scratch must not be reallocated:
   // a request beyond its size is an error instead.
   void freeze(bool on) const { frozen_ = on; }
+  // Plane cache of the tensor-core path.  set_keys names the operands of the
+  // next call (-1: none): a key promises that the operand's values stay the
+  // same until the next cache_reset, so that planes split from it with the
+  // same arrangement and level are reused.  cache_reset empties the cache and
+  // gives it `bytes` of room (kept when it already has that much).
+  void set_keys(int64_t a, int64_t b) const {
+    key_a_ = a;
+    key_b_ = b;
+  }
+  void cache_reset(size_t bytes) const;
 
  private:
+  struct CacheEntry {
+    int64_t key;
+    std::string sig;
+    size_t off;
+  };
+  mutable std::vector<CacheEntry> cache_;
+  mutable DevBuf cache_buf_;
+  mutable size_t cache_used_ = 0;
+  mutable int64_t key_a_ = -1, key_b_ = -1;
   cudaStream_t s_;
   mutable bool frozen_ = false;
   int level_ = 0;

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "gemm_oz.h"
+#include "matview.cuh"
 #include "tc_ptx.cuh"
 
 namespace ascc {
@@ -403,6 +404,121 @@ __global__ void oz_digits_kernel(__nv_bfloat16* __restrict__ out, const int32_t*
   }
 }
 
+// The first and third steps reading a strided tensor through a MatView.
+__global__ void oz_rowmax_view_kernel(unsigned* __restrict__ hmax, const double* __restrict__ in,
+                                      MatView v, long long rows, long long K, long long Kp,
+                                      bool fast) {
+  const long long runs = Kp / 8, total = rows * runs;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+    double x[8];
+    matview_run8(v, in + matview_row(v, r), k0, K, fast, x);
+    unsigned m = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m = max(m, (unsigned)(abs_bits(x[j]) >> 32));
+    const unsigned active = __activemask();
+    const long long r0 = __shfl_sync(active, r, __ffs(active) - 1);
+    if (active == 0xffffffffu && __all_sync(active, r == r0)) {
+      for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(active, m, off));
+      if ((threadIdx.x & 31) == 0 && m) atomicMax(hmax + r, m);
+    } else if (m) {
+      atomicMax(hmax + r, m);
+    }
+  }
+}
+
+__global__ void oz_digits_view_kernel(__nv_bfloat16* __restrict__ out,
+                                      const int32_t* __restrict__ exps,
+                                      const double* __restrict__ in, MatView v, long long rows,
+                                      long long K, long long Kp, long long plane_stride,
+                                      bool fast) {
+  const long long runs = Kp / 8, total = rows * runs;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+    const int e = exps[r];
+    double x[8];
+    matview_run8(v, in + matview_row(v, r), k0, K, fast, x);
+    __align__(16) __nv_bfloat16 dig[NSLICE][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      long long q = 0;
+      if (e != kNonFinite && k0 + j < K) q = scaled_int(x[j], L - e);
+#pragma unroll
+      for (int s = NSLICE - 1; s >= 1; --s) {
+        const long long d = ((q + 64) & 127) - 64;
+        q = (q - d) >> BETA;
+        dig[s][j] = __float2bfloat16_rn(ldexpf((float)d, -BETA * s));
+      }
+      dig[0][j] = __float2bfloat16_rn((float)q);
+    }
+#pragma unroll
+    for (int s = 0; s < NSLICE; ++s)
+      *reinterpret_cast<uint4*>(out + (long long)s * plane_stride + r * Kp + k0) =
+          *reinterpret_cast<const uint4*>(dig[s]);
+  }
+}
+
+// The first and third steps for a view whose contiguous dimension is on the
+// row side: 64 x 32 tiles transposed through shared memory; thread (row mi,
+// run kr) holds eight values of one row.
+__global__ void __launch_bounds__(256) oz_rowmax_view_t_kernel(
+    unsigned* __restrict__ hmax, const double* __restrict__ in, MatView v, long long rows,
+    long long K, long long Kp) {
+  __shared__ double tile[kViewTileK][kViewTileM + 1];
+  __shared__ long long roff[kViewTileM], coff[kViewTileK];
+  const long long ntm = (rows + kViewTileM - 1) / kViewTileM, ntk = Kp / kViewTileK;
+  for (long long tix = blockIdx.x; tix < ntm * ntk; tix += gridDim.x) {
+    const long long m0 = (tix / ntk) * kViewTileM, k0 = (tix % ntk) * kViewTileK;
+    matview_load_tile_t(v, in, rows, K, m0, k0, tile, roff, coff);
+    const int mi = threadIdx.x >> 2, kr = (threadIdx.x & 3) * 8;
+    unsigned m = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m = max(m, (unsigned)(abs_bits(tile[kr + j][mi]) >> 32));
+    // the four runs of a row are neighbouring lanes
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    if ((threadIdx.x & 3) == 0 && m0 + mi < rows && m) atomicMax(hmax + m0 + mi, m);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) oz_digits_view_t_kernel(
+    __nv_bfloat16* __restrict__ out, const int32_t* __restrict__ exps,
+    const double* __restrict__ in, MatView v, long long rows, long long K, long long Kp,
+    long long plane_stride) {
+  __shared__ double tile[kViewTileK][kViewTileM + 1];
+  __shared__ long long roff[kViewTileM], coff[kViewTileK];
+  const long long ntm = (rows + kViewTileM - 1) / kViewTileM, ntk = Kp / kViewTileK;
+  for (long long tix = blockIdx.x; tix < ntm * ntk; tix += gridDim.x) {
+    const long long m0 = (tix / ntk) * kViewTileM, k0 = (tix % ntk) * kViewTileK;
+    matview_load_tile_t(v, in, rows, K, m0, k0, tile, roff, coff);
+    const int mi = threadIdx.x >> 2, kr = (threadIdx.x & 3) * 8;
+    if (m0 + mi < rows) {
+      const int e = exps[m0 + mi];
+      __align__(16) __nv_bfloat16 dig[NSLICE][8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        long long q = 0;
+        if (e != kNonFinite) q = scaled_int(tile[kr + j][mi], L - e);
+#pragma unroll
+        for (int s = NSLICE - 1; s >= 1; --s) {
+          const long long d = ((q + 64) & 127) - 64;
+          q = (q - d) >> BETA;
+          dig[s][j] = __float2bfloat16_rn(ldexpf((float)d, -BETA * s));
+        }
+        dig[0][j] = __float2bfloat16_rn((float)q);
+      }
+#pragma unroll
+      for (int s = 0; s < NSLICE; ++s)
+        *reinterpret_cast<uint4*>(out + (long long)s * plane_stride + (m0 + mi) * Kp + k0 + kr) =
+            *reinterpret_cast<const uint4*>(dig[s]);
+    }
+    __syncthreads();
+  }
+}
+
 CUtensorMap make_map3(const __nv_bfloat16* base, int64_t rows, int64_t Kp, int64_t plane_stride,
                       int box_rows) {
   CUtensorMap m;
@@ -441,6 +557,36 @@ void split(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const double* i
   oz_digits_kernel<<<g, 256, 0, s>>>(planes, exps, in, rows, K, ld, Kp, plane_stride);
   count_launch(3);
   check_launch("oz_split");
+}
+
+void split_view(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const double* in,
+                const MatView& v, int64_t plane_stride) {
+  ASCC_REQUIRE(v.nm >= 1 && v.nm <= 4 && v.nk >= 1 && v.nk <= 4, "oz split_view: 1..4 dims");
+  const int64_t rows = v.rows(), K = v.cols();
+  if (rows <= 0) return;
+  const int64_t Kp = padded_k(K);
+  if (plane_stride <= 0) plane_stride = rows * Kp;
+  ASCC_CUDA(cudaMemsetAsync(exps, 0, sizeof(int32_t) * (size_t)rows, s));
+  if (v.kstr[v.nk - 1] != 1) {
+    const int64_t tiles = (rows + kViewTileM - 1) / kViewTileM * (Kp / kViewTileK);
+    const int gt = (int)std::min<int64_t>(tiles, 152 * 8);
+    oz_rowmax_view_t_kernel<<<gt, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, v, rows, K,
+                                               Kp);
+    oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
+    oz_digits_view_t_kernel<<<gt, 256, 0, s>>>(planes, exps, in, v, rows, K, Kp, plane_stride);
+    count_launch(3);
+    check_launch("oz_split_view_t");
+    return;
+  }
+  const bool fast = v.kext[v.nk - 1] % 8 == 0;
+  const int64_t runs = rows * (Kp / 8);
+  const int g = (int)std::min<int64_t>((runs + 255) / 256, 152 * 16);
+  oz_rowmax_view_kernel<<<g, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, v, rows, K, Kp,
+                                          fast);
+  oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
+  oz_digits_view_kernel<<<g, 256, 0, s>>>(planes, exps, in, v, rows, K, Kp, plane_stride, fast);
+  count_launch(3);
+  check_launch("oz_split_view");
 }
 
 int splitk_for(int64_t M, int64_t N, int64_t K) {

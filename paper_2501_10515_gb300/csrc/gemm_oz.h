@@ -47,6 +47,11 @@ int64_t padded_k(int64_t K);
 void split(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const double* in, int64_t rows,
            int64_t K, int64_t ld, int64_t plane_stride = 0);
 
+// The same from a strided tensor read as the matrix v (rows v.rows(), K =
+// v.cols()), without a permuted copy.
+void split_view(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const double* in,
+                const MatView& v, int64_t plane_stride = 0);
+
 // Workspace of gemm(): one 64-bit integer per element of C.
 inline size_t ws_bytes(int64_t M, int64_t N) { return sizeof(long long) * (size_t)(M * N); }
 

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "gemm_tc.h"
+#include "matview.cuh"
 #include "tc_ptx.cuh"
 
 namespace ascc {
@@ -231,32 +232,37 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
 // of the next; the epilogue stages its tile in a shared-memory buffer of its
 // own.  Every wait is bounded; after a timeout all roles stop and the kernel
 // frees its TMEM and returns.
-constexpr int NB = 64, NWARPS_N = 6;
+// The tile is 128 x NB with NB = 64 (thin products) or 128 (products whose
+// K chunk is short, where the epilogue of a tile would otherwise not overlap
+// any MMA work).
+constexpr int NWARPS_N = 6;
 
-template <int LEVEL>
+template <int LEVEL, int NB>
 struct NarrowRing {
   static constexpr int A_TILE = BM * TK * 2;     // 8 KB
-  static constexpr int B_TILE = NB * TK * 2;     // 4 KB
+  static constexpr int B_TILE = NB * TK * 2;     // 4 or 8 KB
   static constexpr int A_BYTES = LEVEL * A_TILE;
   static constexpr int STAGE_BYTES = LEVEL * (A_TILE + B_TILE);
-  static constexpr int STAGES = LEVEL == 3 ? 4 : LEVEL == 2 ? 6 : 8;
+  static constexpr int STAGES = NB == 64 ? (LEVEL == 3 ? 4 : LEVEL == 2 ? 6 : 8)
+                                         : (LEVEL == 3 ? 3 : LEVEL == 2 ? 4 : 6);
   static constexpr int RING_BYTES = STAGES * STAGE_BYTES;
   static constexpr int EPI = BM * (NB + 1) * 4;
   static constexpr int SMEM_BYTES = RING_BYTES + EPI + 1024 + 512;
   static constexpr int NACC = Ring<LEVEL>::NACC;
   static constexpr int ACC_COLS = NACC * NB;      // one accumulator set
-  static constexpr int TMEM_COLS = ACC_COLS <= 64 ? 128 : 256;  // two sets
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two sets (a power of 2)
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
+  static_assert(TMEM_COLS <= 512, "TMEM columns");
 };
 
-template <int LEVEL>
+template <int LEVEL, int NB>
 __global__ void __launch_bounds__(32 * NWARPS_N, 1)
 gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
                       const __grid_constant__ CUtensorMap bmap, int M, int N, int num_kt,
                       int kt_chunk, int splitk, double alpha, double beta,
                       double* __restrict__ C, long long ldc, float* __restrict__ ws, int* err,
                       int trans) {
-  using G = NarrowRing<LEVEL>;
+  using G = NarrowRing<LEVEL, NB>;
   using R = Ring<LEVEL>;
   constexpr int STAGES = G::STAGES;
   extern __shared__ uint8_t smem_raw[];
@@ -416,7 +422,7 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
       const int rows = min(BM, M - m0), cols = min(NB, N - n0);
       const int kz = w / (mt * nt);
       if (!trans) {
-        // 2 rows per pass, 64 columns each
+        // 128 / NB rows per pass, NB columns each
         for (int rr = t / NB; rr < rows; rr += 128 / NB) {
           const int c = t % NB;
           if (c >= cols) continue;
@@ -529,6 +535,35 @@ __global__ void splitk_reduce4_kernel(double* __restrict__ C, long long ldc,
   }
 }
 
+// The same sums written through an output view: element (m, n) of the
+// product goes to C + matview_row(v, m) + (offset of n over the view's
+// column dimensions).  by_rows: consecutive threads take consecutive rows
+// (when the view's rows, not its columns, are the contiguous side).
+__global__ void splitk_reduce_view_kernel(double* __restrict__ C, MatView v,
+                                          const float* __restrict__ ws, long long M, long long N,
+                                          int nz, double alpha, double beta, bool by_rows) {
+  const long long total = M * N;
+  const long long outer = by_rows ? N : M, inner = by_rows ? M : N;
+  for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < inner;
+         i += (long long)gridDim.x * blockDim.x) {
+      const long long m = by_rows ? i : o, n = by_rows ? o : i;
+      const long long idx = m * N + n;
+      float hi = 0.f, lo = 0.f;
+      for (int z = 0; z < nz; ++z) comp_add(hi, lo, ws[(long long)z * total + idx]);
+      const double acc = (double)hi + (double)lo;
+      long long off = matview_row(v, m), r = n;
+      for (int d = v.nk - 1; d >= 0; --d) {
+        const long long q = r / v.kext[d];
+        off += (r - q * v.kext[d]) * v.kstr[d];
+        r = q;
+      }
+      double* c = C + off;
+      *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *c);
+    }
+  }
+}
+
 // FP64 [rows][K] (row stride ld) -> nsplit BF16 planes [nsplit][rows][Kp], zero padded.
 // The value is rounded to FP32 once (24 significant bits, as many as three
 // planes hold) and split with exact FP32 subtractions.  Each thread converts a
@@ -554,6 +589,64 @@ __global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double*
       *reinterpret_cast<uint4*>(out + (long long)s * plane_stride + r * Kp + k0) =
           *reinterpret_cast<const uint4*>(h);
     }
+  }
+}
+
+// The same from a strided tensor read through a MatView (no permuted copy).
+__global__ void split_bf16_view_kernel(__nv_bfloat16* __restrict__ out,
+                                       const double* __restrict__ in, MatView v, long long rows,
+                                       long long K, long long Kp, int nsplit,
+                                       long long plane_stride, bool fast) {
+  const long long runs = Kp / 8, total = rows * runs;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+    double x[8];
+    matview_run8(v, in + matview_row(v, r), k0, K, fast, x);
+    float f[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = (float)x[j];
+    for (int s = 0; s < nsplit; ++s) {
+      __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        h[j] = __float2bfloat16_rn(f[j]);
+        f[j] -= __bfloat162float(h[j]);
+      }
+      *reinterpret_cast<uint4*>(out + (long long)s * plane_stride + r * Kp + k0) =
+          *reinterpret_cast<const uint4*>(h);
+    }
+  }
+}
+
+// The same for a view whose contiguous dimension is on the row side: one
+// 64 x 32 tile per block pass, transposed through shared memory.
+__global__ void __launch_bounds__(256) split_bf16_view_t_kernel(
+    __nv_bfloat16* __restrict__ out, const double* __restrict__ in, MatView v, long long rows,
+    long long K, long long Kp, int nsplit, long long plane_stride) {
+  __shared__ double tile[kViewTileK][kViewTileM + 1];
+  __shared__ long long roff[kViewTileM], coff[kViewTileK];
+  const long long ntm = (rows + kViewTileM - 1) / kViewTileM, ntk = Kp / kViewTileK;
+  for (long long tix = blockIdx.x; tix < ntm * ntk; tix += gridDim.x) {
+    const long long m0 = (tix / ntk) * kViewTileM, k0 = (tix % ntk) * kViewTileK;
+    matview_load_tile_t(v, in, rows, K, m0, k0, tile, roff, coff);
+    const int mi = threadIdx.x >> 2, kr = (threadIdx.x & 3) * 8;
+    float f[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = (float)tile[kr + j][mi];
+    if (m0 + mi < rows) {
+      for (int s = 0; s < nsplit; ++s) {
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          h[j] = __float2bfloat16_rn(f[j]);
+          f[j] -= __bfloat162float(h[j]);
+        }
+        *reinterpret_cast<uint4*>(out + (long long)s * plane_stride + (m0 + mi) * Kp + k0 + kr) =
+            *reinterpret_cast<const uint4*>(h);
+      }
+    }
+    __syncthreads();  // the tile is rewritten by the next pass
   }
 }
 
@@ -603,19 +696,43 @@ void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t ro
   check_launch("split_bf16");
 }
 
+void split_bf16_view(cudaStream_t s, __nv_bfloat16* out, const double* in, const MatView& v,
+                     int nsplit, int64_t plane_stride) {
+  ASCC_REQUIRE(v.nm >= 1 && v.nm <= 4 && v.nk >= 1 && v.nk <= 4, "split_bf16_view: 1..4 dims");
+  const int64_t rows = v.rows(), K = v.cols(), Kp = padded_k(K), total = rows * Kp;
+  if (total == 0) return;
+  if (plane_stride <= 0) plane_stride = total;
+  if (v.kstr[v.nk - 1] != 1) {
+    const int64_t tiles = (rows + kViewTileM - 1) / kViewTileM * (Kp / kViewTileK);
+    const int g = (int)std::min<int64_t>(tiles, 152 * 8);
+    split_bf16_view_t_kernel<<<g, 256, 0, s>>>(out, in, v, rows, K, Kp, nsplit, plane_stride);
+    count_launch();
+    check_launch("split_bf16_view_t");
+    return;
+  }
+  const bool fast = v.kext[v.nk - 1] % 8 == 0;
+  const int g = (int)std::min<int64_t>((rows * (Kp / 8) + 255) / 256, 152 * 16);
+  split_bf16_view_kernel<<<g, 256, 0, s>>>(out, in, v, rows, K, Kp, nsplit, plane_stride, fast);
+  count_launch();
+  check_launch("split_bf16_view");
+}
+
 int products_for(int level) { return level == 1 ? 1 : level == 2 ? 3 : 6; }
 
 // Products with at most this many columns run on the persistent 128 x 64
 // kernel; those with at most NARROW_M rows (and more columns) run on it with
 // the operands exchanged and the tile stored transposed.
-constexpr int64_t NARROW_N = 128, NARROW_M = 64;
+// Other products whose K (chunk) is at most SHORT_K run on the persistent
+// kernel with 128 x 128 tiles: there the epilogue of a tile takes as long as
+// its MMAs, and the persistent kernel overlaps the two.
+constexpr int64_t NARROW_N = 128, NARROW_M = 64, SHORT_K = 1024;
 
 int splitk_for(int64_t M, int64_t N, int64_t K) {
   // K chunks of at most 2048 (FP32 accumulation error ~ 2^-24 sqrt(K/16) per chunk),
   // and enough work items to fill the GPU for small M x N
   const bool swap = M <= NARROW_M && N > NARROW_N;
   if (swap) std::swap(M, N);
-  const int64_t bn = N <= NARROW_N ? NB : BN;
+  const int64_t bn = N <= NARROW_N ? 64 : padded_k(K) <= SHORT_K ? 128 : BN;
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + bn - 1) / bn);
   const int64_t num_kt = (K + BK - 1) / BK;
   int64_t z = (K + 2047) / 2048;
@@ -625,8 +742,9 @@ int splitk_for(int64_t M, int64_t N, int64_t K) {
 
 void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
                 const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C, int64_t ldc,
-                int* err, int splitk, float* ws, int64_t b_plane_stride) {
+                int* err, int splitk, float* ws, int64_t b_plane_stride, const MatView* cview) {
   ASCC_REQUIRE(level >= 1 && level <= 3, "split level 1..3");
+  ASCC_REQUIRE(!cview || ws, "gemm_split: an output view needs a workspace");
   ASCC_REQUIRE(M > 0 && N > 0 && K > 0, "gemm_split: empty");
   ASCC_REQUIRE(splitk >= 1 && (splitk == 1 || ws), "gemm_split: split-K needs a workspace");
   static std::once_flag attr_once;
@@ -645,51 +763,61 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   });
   ASCC_CUDA(attr_err);
   const int64_t Kp = padded_k(K);
+  const int num_kt = (int)(Kp / TK);
+  const int kt_chunk = (num_kt + splitk - 1) / splitk;
   const bool swap = M <= NARROW_M && N > NARROW_N;
-  const bool narrow = N <= NARROW_N || swap;
+  const bool thin = N <= NARROW_N || swap;
+  const bool shortk = !thin && (int64_t)kt_chunk * TK <= SHORT_K;
+  const bool narrow = thin || shortk;   // the persistent kernel
+  const int nbt = thin ? 64 : 128;      // its tile width
   const int64_t bstride = b_plane_stride > 0 ? b_plane_stride : N * Kp;
   const CUtensorMap am = swap ? make_planes_map(B, N, Kp, bstride, level, BM)
                               : make_planes_map(A, M, Kp, M * Kp, level, BM);
-  const CUtensorMap bm = swap ? make_planes_map(A, M, Kp, M * Kp, level, NB)
-                              : make_planes_map(B, N, Kp, bstride, level, narrow ? NB : BN);
+  const CUtensorMap bm = swap ? make_planes_map(A, M, Kp, M * Kp, level, nbt)
+                              : make_planes_map(B, N, Kp, bstride, level, narrow ? nbt : BN);
   count_flops(2.0 * (double)M * N * K);
-  const int num_kt = (int)(Kp / TK);
-  const int kt_chunk = (num_kt + splitk - 1) / splitk;
-  float* wsp = splitk > 1 ? ws : nullptr;
+  float* wsp = (splitk > 1 || cview) ? ws : nullptr;
   if (narrow) {
     static std::once_flag narrow_once;
     cudaError_t e = cudaSuccess;
     std::call_once(narrow_once, [&] {
-      e = cudaFuncSetAttribute(gemm_tc_narrow_kernel<1>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               NarrowRing<1>::SMEM_BYTES);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gemm_tc_narrow_kernel<2>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 NarrowRing<2>::SMEM_BYTES);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gemm_tc_narrow_kernel<3>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 NarrowRing<3>::SMEM_BYTES);
+      auto set = [&](const void* f, int bytes) {
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      };
+      set((const void*)gemm_tc_narrow_kernel<1, 64>, NarrowRing<1, 64>::SMEM_BYTES);
+      set((const void*)gemm_tc_narrow_kernel<2, 64>, NarrowRing<2, 64>::SMEM_BYTES);
+      set((const void*)gemm_tc_narrow_kernel<3, 64>, NarrowRing<3, 64>::SMEM_BYTES);
+      set((const void*)gemm_tc_narrow_kernel<1, 128>, NarrowRing<1, 128>::SMEM_BYTES);
+      set((const void*)gemm_tc_narrow_kernel<2, 128>, NarrowRing<2, 128>::SMEM_BYTES);
+      set((const void*)gemm_tc_narrow_kernel<3, 128>, NarrowRing<3, 128>::SMEM_BYTES);
     });
     ASCC_CUDA(e);
     const int64_t Mk = swap ? N : M, Nk = swap ? M : N;  // the kernel's product
-    const int64_t items = ((Mk + BM - 1) / BM) * ((Nk + NB - 1) / NB) * splitk;
+    const int64_t items = ((Mk + BM - 1) / BM) * ((Nk + nbt - 1) / nbt) * splitk;
     ASCC_REQUIRE(items < (1ll << 31), "gemm_split: too many tiles");
     const unsigned grid = (unsigned)std::min<int64_t>(items, 152);
     const int threads = 32 * NWARPS_N, tr = swap ? 1 : 0;
-    if (level == 1)
-      gemm_tc_narrow_kernel<1><<<grid, threads, NarrowRing<1>::SMEM_BYTES, s>>>(
-          am, bm, (int)Mk, (int)Nk, num_kt, kt_chunk, splitk, alpha, beta, C, (long long)ldc, wsp,
-          err, tr);
-    else if (level == 2)
-      gemm_tc_narrow_kernel<2><<<grid, threads, NarrowRing<2>::SMEM_BYTES, s>>>(
-          am, bm, (int)Mk, (int)Nk, num_kt, kt_chunk, splitk, alpha, beta, C, (long long)ldc, wsp,
-          err, tr);
-    else
-      gemm_tc_narrow_kernel<3><<<grid, threads, NarrowRing<3>::SMEM_BYTES, s>>>(
-          am, bm, (int)Mk, (int)Nk, num_kt, kt_chunk, splitk, alpha, beta, C, (long long)ldc, wsp,
-          err, tr);
+#define ASCC_NARROW(LV, NBV)                                                                  \
+  gemm_tc_narrow_kernel<LV, NBV><<<grid, threads, NarrowRing<LV, NBV>::SMEM_BYTES, s>>>(       \
+      am, bm, (int)Mk, (int)Nk, num_kt, kt_chunk, splitk, alpha, beta, C, (long long)ldc, wsp, \
+      err, tr)
+    if (nbt == 64) {
+      if (level == 1)
+        ASCC_NARROW(1, 64);
+      else if (level == 2)
+        ASCC_NARROW(2, 64);
+      else
+        ASCC_NARROW(3, 64);
+    } else {
+      if (level == 1)
+        ASCC_NARROW(1, 128);
+      else if (level == 2)
+        ASCC_NARROW(2, 128);
+      else
+        ASCC_NARROW(3, 128);
+    }
+#undef ASCC_NARROW
     count_launch();
     check_launch("gemm_tc_narrow");
   }
@@ -711,7 +839,17 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
     count_launch();
     check_launch("gemm_tc");
   }
-  if (splitk > 1) {
+  if (cview) {
+    const MatView& v = *cview;
+    const bool by_rows = v.kstr[v.nk - 1] != 1 && v.mstr[v.nm - 1] == 1;
+    const int64_t outer = by_rows ? N : M, inner = by_rows ? M : N;
+    const unsigned gy = (unsigned)std::min<int64_t>(outer, 65535);
+    const unsigned gx = (unsigned)std::min<int64_t>((inner + 255) / 256, 64);
+    splitk_reduce_view_kernel<<<dim3(gx, gy), 256, 0, s>>>(C, v, ws, M, N, splitk, alpha, beta,
+                                                           by_rows);
+    count_launch();
+    check_launch("splitk_reduce_view");
+  } else if (splitk > 1) {
     const unsigned gy = (unsigned)std::min<int64_t>(M, 65535);
     if (N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0) {
       const unsigned gx = (unsigned)std::min<int64_t>((N / 4 + 255) / 256, 64);

@@ -20,6 +20,11 @@ int products_for(int level);
 void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t rows, int64_t K,
                 int64_t ld, int nsplit, int64_t plane_stride = 0);
 
+// The same planes of a strided tensor read as the matrix v (rows v.rows(),
+// K = v.cols()), without a permuted copy.
+void split_bf16_view(cudaStream_t s, __nv_bfloat16* out, const double* in, const MatView& v,
+                     int nsplit, int64_t plane_stride = 0);
+
 // C[M][N] (FP64, row stride ldc) = alpha * A B^T + beta * C with A [level][M][Kp] and
 // B [level][N][Kp] BF16 planes from split_bf16 (K-major).  err: device int that
 // receives a nonzero code if a bounded wait inside the kernel gives up.
@@ -28,10 +33,12 @@ void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t ro
 // bounds the FP32 accumulation error by the chunk length.
 // b_plane_stride: elements between B's planes (<= 0: N * Kp, i.e. packed planes),
 // so that a row block of a larger plane set can serve as B.
+// cview: C written through a view (rows over its M dimensions, columns over
+// its column dimensions; ldc unused), the partials always going through ws.
 void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
                 const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C,
                 int64_t ldc, int* err, int splitk = 1, float* ws = nullptr,
-                int64_t b_plane_stride = 0);
+                int64_t b_plane_stride = 0, const MatView* cview = nullptr);
 
 // Number of K chunks the residual engine uses for an M x N x K product.
 int splitk_for(int64_t M, int64_t N, int64_t K);

@@ -24,6 +24,12 @@ void axis_matrix(cudaStream_t s, bool fp32, double* C, const double* A, const do
 void gemv_f64(cudaStream_t s, bool ta, int64_t M, int64_t K, double alpha, const double* A,
               int64_t lda, const double* x, double beta, double* y);
 
+// out[strided] = alpha * a[strided] * b[strided] + beta * out over an
+// nd-dimensional box (an outer product, or a scaled copy when b's strides are 0).
+void outer(cudaStream_t s, double* out, const int64_t* out_stride, const double* a,
+           const int64_t* a_stride, const double* b, const int64_t* b_stride, int nd,
+           const int64_t* shape, double alpha, double beta);
+
 // out[strided] = alpha * in[strided] + beta * out over an nd-dimensional
 // index box `shape` (strides in elements, one per dimension).
 void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride,

@@ -317,6 +317,43 @@ __global__ void gemv_rows_kernel(int64_t M, int64_t K, double alpha, const doubl
   }
 }
 
+// Short rows (K <= 8): one thread per row.
+__global__ void gemv_short_kernel(int64_t M, int64_t K, double alpha, const double* __restrict__ A,
+                                  int64_t lda, const double* __restrict__ x, double beta,
+                                  double* __restrict__ y) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t k = 0; k < K; ++k) acc = fma(A[m * lda + k], x[k], acc);
+    y[m] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * y[m]);
+  }
+}
+
+// out = alpha * a * b + beta * out over an nd-dimensional box walked in the
+// output's row-major order (astride / bstride 0 where a label is absent).
+struct OuterStrides {
+  int nd;
+  int64_t shape[8], astride[8], bstride[8], ostride[8];
+};
+
+__global__ void outer_kernel(double* __restrict__ out, const double* __restrict__ a,
+                             const double* __restrict__ b, int64_t total, OuterStrides st,
+                             double alpha, double beta) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = idx, ao = 0, bo = 0, oo = 0;
+    for (int d = st.nd - 1; d >= 0; --d) {
+      const int64_t c = rem % st.shape[d];
+      rem /= st.shape[d];
+      ao += c * st.astride[d];
+      bo += c * st.bstride[d];
+      oo += c * st.ostride[d];
+    }
+    const double val = alpha * a[ao] * b[bo];
+    out[oo] = (beta == 0.0) ? val : val + beta * out[oo];
+  }
+}
+
 __global__ void gemv_cols_kernel(int64_t M, int64_t K, double alpha, const double* __restrict__ A,
                                  int64_t lda, const double* __restrict__ x, double beta,
                                  double* __restrict__ y) {
@@ -813,6 +850,28 @@ void gemm_f64(cudaStream_t s, bool ta, bool tb, int64_t M, int64_t N, int64_t K,
   check_launch("gemm_f64");
 }
 
+void outer(cudaStream_t s, double* out, const int64_t* out_stride, const double* a,
+           const int64_t* a_stride, const double* b, const int64_t* b_stride, int nd,
+           const int64_t* shape, double alpha, double beta) {
+  ASCC_REQUIRE(nd >= 0 && nd <= 8, "outer: 0..8 dimensions");
+  OuterStrides st;
+  st.nd = 0;
+  int64_t total = 1;
+  for (int d = 0; d < nd; ++d) {
+    total *= shape[d];
+    if (shape[d] == 1) continue;
+    st.shape[st.nd] = shape[d];
+    st.astride[st.nd] = a_stride[d];
+    st.bstride[st.nd] = b_stride[d];
+    st.ostride[st.nd] = out_stride[d];
+    ++st.nd;
+  }
+  if (total == 0) return;
+  outer_kernel<<<grid_for(total), 256, 0, s>>>(out, a, b, total, st, alpha, beta);
+  count_launch();
+  check_launch("outer");
+}
+
 void strided_copy(cudaStream_t s, double* out, const int64_t* out_stride, const double* in,
                   const int64_t* in_stride, int nd, const int64_t* shape, double alpha,
                   double beta) {
@@ -994,6 +1053,8 @@ void gemv_f64(cudaStream_t s, bool ta, int64_t M, int64_t K, double alpha, const
   }
   if (ta)
     gemv_cols_kernel<<<grid_for(M), 256, 0, s>>>(M, K, alpha, A, lda, x, beta, y);
+  else if (K <= 8)
+    gemv_short_kernel<<<grid_for(M), 256, 0, s>>>(M, K, alpha, A, lda, x, beta, y);
   else
     gemv_rows_kernel<<<(int)std::min<int64_t>((M * 32 + 255) / 256, 152 * 16), 256, 0, s>>>(
         M, K, alpha, A, lda, x, beta, y);

@@ -331,6 +331,7 @@ void T3pProgram::exec_op(int q, Einsum& es, cudaStream_t s, double* const* base,
     pack(shape, stride, ost);
     box_copy(s, ws + offset_[op.out], ost, base[op.base] + off, stride, shape);
   } else if (op.kind == 1) {
+    es.set_keys(op.a, op.b);
     es(op.spec, op.alpha, tensor(op.a), tensor(op.b), 0.0, tensor(op.out));
   } else if (op.kind == 3 || op.kind == 4) {
     stack_copy(op, s, base, outb, scale, ws);
@@ -338,6 +339,7 @@ void T3pProgram::exec_op(int q, Einsum& es, cudaStream_t s, double* const* base,
     int64_t off;
     std::vector<int64_t> shape, stride;
     select(op.base, op.outspec, &off, shape, stride);
+    es.set_keys(op.a, op.b);
     if (off == 0 && shape == base_shape(op.base)) {
       es(op.spec, op.alpha * scale, tensor(op.a), tensor(op.b), 1.0, T(outb[op.base], shape));
       return;
@@ -353,6 +355,9 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
                      double scale, double* ws) const {
   const double min0 = es.min_flops();
   if (es.level() > 0) es.set_split(es.level(), es.err(), std::min(min0, kTcMinFlops));
+  // every tensor of a section is written once before it is read, so its
+  // planes stay valid for the rest of the section
+  es.cache_reset(cache_bytes());
   // optional per-op timing (ASCC_T3P_PROFILE=<file>): CUDA events around
   // every op, summed per op and written to the file when the program is freed
   const bool prof = profile_path_ != nullptr;
@@ -399,6 +404,7 @@ void T3pProgram::run_streams(T3pStreams& ex, int section, double* const* base, d
     Einsum& e = *ex.es[k];
     min0[k] = e.min_flops();
     if (e.level() > 0) e.set_split(e.level(), e.err(), std::min(min0[k], kTcMinFlops));
+    e.cache_reset(cache_bytes());
   }
   std::vector<double*> outb(T3P_NBASE * ns);
   for (int k = 0; k < ns; ++k) {

@@ -93,6 +93,10 @@ class T3pProgram {
   void run_streams(T3pStreams& ex, int section, double* const* base, double scale,
                    double* ws) const;
   int nstreams() const { return nstreams_; }
+  // room of each planner's plane cache during a run
+  size_t cache_bytes() const {
+    return (size_t)std::min<int64_t>(int64_t(1) << 30, ws_elems_ / 2) / 256 * 256;
+  }
   int op_count() const;
   // Sizes of the four blocks (elements) and the offsets of TA..TD (RA..RD)
   // in one concatenated buffer.

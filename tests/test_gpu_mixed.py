@@ -59,6 +59,28 @@ def test_narrow_split_gemm_matches_fp64(M, N, K, level):
         assert (C - ref).abs().max().item() / scale < LEVEL_TOL[level]
 
 
+@pytest.mark.parametrize("level", [1, 2, 3])
+@pytest.mark.parametrize("M,N,K", [(3000, 1000, 200), (129, 257, 1024), (5000, 300, 640),
+                                   (65, 4000, 96), (1000, 999, 33)])
+def test_short_k_split_gemm_matches_fp64(M, N, K, level):
+    """Products with a short K (at most 1024) and neither side thin run on the
+    persistent kernel with 128 x 128 tiles: several tiles per CTA, ragged
+    edges, both beta branches."""
+    import torch
+    import paper_2501_10515_gb300 as pkg
+    g = torch.Generator(device="cuda").manual_seed(M * 3 + N * 13 + K + level)
+    A = torch.randn(M, K, device="cuda", dtype=torch.float64, generator=g)
+    B = torch.randn(N, K, device="cuda", dtype=torch.float64, generator=g)
+    C0 = torch.randn(M, N, device="cuda", dtype=torch.float64, generator=g)
+    for beta in (0.0, 0.75):
+        C = C0.clone()
+        pkg.gemm_split_bf16(A, B, C, level, alpha=-1.5, beta=beta)
+        torch.cuda.synchronize()
+        ref = -1.5 * (A @ B.T) + beta * C0
+        scale = (1.5 * (A.abs() @ B.abs().T)).max().item() + 1.0
+        assert (C - ref).abs().max().item() / scale < LEVEL_TOL[level]
+
+
 def test_split_gemm_levels_improve():
     import torch
     import paper_2501_10515_gb300 as pkg
