@@ -19,6 +19,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "fpconv.cuh"
 #include "gemm_oz.h"
 #include "matview.cuh"
 #include "tc_ptx.cuh"
@@ -67,11 +68,29 @@ __device__ __forceinline__ long long fold_low(uint32_t a3, uint32_t a4) {
   return i3 * (1ll << 7) + it;
 }
 
+// One output of the digit products: the exact integer sum v scaled by
+// 2^(a + b - 2 BETA - UNIT) (the row and column exponents), times alpha, plus
+// beta times the old value.  The conversion, and for beta = 0 a power-of-two
+// alpha, run in integer arithmetic with the FP64 expression's result.
+__device__ __forceinline__ double digit_out(long long v, int32_t a, int32_t b, const Pow2& p2,
+                                            double alpha, double beta, double old) {
+  if (a == kNonFinite || b == kNonFinite) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    return beta == 0.0 ? alpha * nan : fma(alpha, nan, beta * old);
+  }
+  const int sh = a + b - (2 * BETA + UNIT);
+  double val;
+  if (beta == 0.0 && p2.ok && i64_to_f64_scaled(v, sh + p2.e, p2.neg, val)) return val;
+  if (!i64_to_f64_scaled(v, sh, 0u, val)) val = i64_scaled_fp64(v, sh);
+  return beta == 0.0 ? alpha * val : fma(alpha, val, beta * old);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
                int M, int N, int num_kt, int kt_chunk, unsigned long long* __restrict__ ws,
                const int32_t* __restrict__ ea, const int32_t* __restrict__ eb, double alpha,
                double beta, double* __restrict__ C, long long ldc, int* err) {
+  const Pow2 p2 = pow2_of(alpha);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -251,11 +270,8 @@ gemm_oz_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
             const int rr = r0 + u * RPP;
             if (rr < rows) {
               const long long v = tile[rr * PITCH + c];
-              const double val = (a[u] == kNonFinite || b == kNonFinite)
-                                     ? __longlong_as_double(0x7ff8000000000000ll)
-                                     : ldexp((double)v, a[u] + b - (2 * BETA + UNIT));
               C[(long long)(m0 + rr) * ldc + col] =
-                  (beta == 0.0) ? alpha * val : fma(alpha, val, beta * old[u]);
+                  digit_out(v, a[u], b, p2, alpha, beta, old[u]);
             }
           }
         }
@@ -282,18 +298,14 @@ __global__ void oz_finish_kernel(double* __restrict__ C, long long ldc,
                                  const long long* __restrict__ ws, const int32_t* __restrict__ ea,
                                  const int32_t* __restrict__ eb, long long M, long long N,
                                  double alpha, double beta) {
+  const Pow2 p2 = pow2_of(alpha);
   const long long total = M * N;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long m = idx / N, n = idx % N;
     const int32_t a = ea[m], b = eb[n];
-    double val;
-    if (a == kNonFinite || b == kNonFinite)
-      val = __longlong_as_double(0x7ff8000000000000ll);
-    else
-      val = ldexp((double)ws[idx], a + b - (2 * BETA + UNIT));
     double* c = C + m * ldc + n;
-    *c = (beta == 0.0) ? alpha * val : fma(alpha, val, beta * *c);
+    *c = digit_out(ws[idx], a, b, p2, alpha, beta, beta != 0.0 ? *c : 0.0);
   }
 }
 
@@ -336,12 +348,14 @@ __device__ __forceinline__ long long scaled_int(double x, int sh) {
 //     16-byte stores per plane.
 // A row whose largest |x| is below 2^-1054 (a subnormal with no bit in the
 // high word) counts as zero.
+template <typename I>
 __global__ void oz_rowmax_kernel(unsigned* __restrict__ hmax, const double* __restrict__ in,
                                  long long rows, long long K, long long ld, long long Kp) {
-  const long long runs = Kp / 8, total = rows * runs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+  const I runs = (I)(Kp / 8), total = (I)rows * runs;
+  for (I idx = blockIdx.x * (I)blockDim.x + threadIdx.x; idx < total;
+       idx += (I)gridDim.x * blockDim.x) {
+    const I rq = idx / runs;
+    const long long r = rq, k0 = (long long)(idx - rq * runs) * 8;
     const double* x = in + r * ld + k0;
     unsigned m = 0;
 #pragma unroll
@@ -375,13 +389,15 @@ __global__ void oz_exponent_kernel(int32_t* __restrict__ exps, long long rows) {
   }
 }
 
+template <typename I>
 __global__ void oz_digits_kernel(__nv_bfloat16* __restrict__ out, const int32_t* __restrict__ exps,
                                  const double* __restrict__ in, long long rows, long long K,
                                  long long ld, long long Kp, long long plane_stride) {
-  const long long runs = Kp / 8, total = rows * runs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+  const I runs = (I)(Kp / 8), total = (I)rows * runs;
+  for (I idx = blockIdx.x * (I)blockDim.x + threadIdx.x; idx < total;
+       idx += (I)gridDim.x * blockDim.x) {
+    const I rq = idx / runs;
+    const long long r = rq, k0 = (long long)(idx - rq * runs) * 8;
     const int e = exps[r];
     const double* x = in + r * ld + k0;
     __align__(16) __nv_bfloat16 dig[NSLICE][8];
@@ -405,15 +421,17 @@ __global__ void oz_digits_kernel(__nv_bfloat16* __restrict__ out, const int32_t*
 }
 
 // The first and third steps reading a strided tensor through a MatView.
+template <typename I>
 __global__ void oz_rowmax_view_kernel(unsigned* __restrict__ hmax, const double* __restrict__ in,
                                       MatView v, long long rows, long long K, long long Kp,
                                       bool fast) {
-  const long long runs = Kp / 8, total = rows * runs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+  const I runs = (I)(Kp / 8), total = (I)rows * runs;
+  for (I idx = blockIdx.x * (I)blockDim.x + threadIdx.x; idx < total;
+       idx += (I)gridDim.x * blockDim.x) {
+    const I rq = idx / runs;
+    const long long r = rq, k0 = (long long)(idx - rq * runs) * 8;
     double x[8];
-    matview_run8(v, in + matview_row(v, r), k0, K, fast, x);
+    matview_run8<I>(v, in + matview_row<I>(v, rq), k0, K, fast, x);
     unsigned m = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) m = max(m, (unsigned)(abs_bits(x[j]) >> 32));
@@ -428,18 +446,20 @@ __global__ void oz_rowmax_view_kernel(unsigned* __restrict__ hmax, const double*
   }
 }
 
+template <typename I>
 __global__ void oz_digits_view_kernel(__nv_bfloat16* __restrict__ out,
                                       const int32_t* __restrict__ exps,
                                       const double* __restrict__ in, MatView v, long long rows,
                                       long long K, long long Kp, long long plane_stride,
                                       bool fast) {
-  const long long runs = Kp / 8, total = rows * runs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+  const I runs = (I)(Kp / 8), total = (I)rows * runs;
+  for (I idx = blockIdx.x * (I)blockDim.x + threadIdx.x; idx < total;
+       idx += (I)gridDim.x * blockDim.x) {
+    const I rq = idx / runs;
+    const long long r = rq, k0 = (long long)(idx - rq * runs) * 8;
     const int e = exps[r];
     double x[8];
-    matview_run8(v, in + matview_row(v, r), k0, K, fast, x);
+    matview_run8<I>(v, in + matview_row<I>(v, rq), k0, K, fast, x);
     __align__(16) __nv_bfloat16 dig[NSLICE][8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -552,9 +572,18 @@ void split(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const double* i
   const int64_t runs = rows * (Kp / 8);
   const int g = (int)std::min<int64_t>((runs + 255) / 256, 152 * 16);
   ASCC_CUDA(cudaMemsetAsync(exps, 0, sizeof(int32_t) * (size_t)rows, s));
-  oz_rowmax_kernel<<<g, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, rows, K, ld, Kp);
-  oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
-  oz_digits_kernel<<<g, 256, 0, s>>>(planes, exps, in, rows, K, ld, Kp, plane_stride);
+  if (runs + 256ll * g < (1ll << 32)) {
+    oz_rowmax_kernel<uint32_t><<<g, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, rows, K,
+                                                 ld, Kp);
+    oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
+    oz_digits_kernel<uint32_t><<<g, 256, 0, s>>>(planes, exps, in, rows, K, ld, Kp, plane_stride);
+  } else {
+    oz_rowmax_kernel<long long><<<g, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, rows, K,
+                                                  ld, Kp);
+    oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
+    oz_digits_kernel<long long><<<g, 256, 0, s>>>(planes, exps, in, rows, K, ld, Kp,
+                                                  plane_stride);
+  }
   count_launch(3);
   check_launch("oz_split");
 }
@@ -581,10 +610,19 @@ void split_view(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const doub
   const bool fast = v.kext[v.nk - 1] % 8 == 0;
   const int64_t runs = rows * (Kp / 8);
   const int g = (int)std::min<int64_t>((runs + 255) / 256, 152 * 16);
-  oz_rowmax_view_kernel<<<g, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, v, rows, K, Kp,
-                                          fast);
-  oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
-  oz_digits_view_kernel<<<g, 256, 0, s>>>(planes, exps, in, v, rows, K, Kp, plane_stride, fast);
+  if (runs + 256ll * g < (1ll << 32)) {
+    oz_rowmax_view_kernel<uint32_t><<<g, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, v,
+                                                      rows, K, Kp, fast);
+    oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
+    oz_digits_view_kernel<uint32_t><<<g, 256, 0, s>>>(planes, exps, in, v, rows, K, Kp,
+                                                      plane_stride, fast);
+  } else {
+    oz_rowmax_view_kernel<long long><<<g, 256, 0, s>>>(reinterpret_cast<unsigned*>(exps), in, v,
+                                                       rows, K, Kp, fast);
+    oz_exponent_kernel<<<grid_for(rows), 256, 0, s>>>(exps, rows);
+    oz_digits_view_kernel<long long><<<g, 256, 0, s>>>(planes, exps, in, v, rows, K, Kp,
+                                                       plane_stride, fast);
+  }
   count_launch(3);
   check_launch("oz_split_view");
 }

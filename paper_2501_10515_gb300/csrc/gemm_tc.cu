@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "fpconv.cuh"
 #include "gemm_tc.h"
 #include "matview.cuh"
 #include "tc_ptx.cuh"
@@ -180,18 +181,28 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     __syncthreads();
     const int rows = min(BM, M - m0), cols = min(BN, N - n0);
     if (ws || beta == 0.0) {
-      // store-only: split-K partials (summed later) or alpha * tile
-      for (int rr = 0; rr < rows; ++rr) {
-        const long long row = m0 + rr;
-        for (int c = threadIdx.x; c < cols; c += NTHREADS) {
-          const int col = n0 + c;
-          const float a = total > 0 ? tile[rr * PITCH + c] : 0.f;
-          if (ws)
-            ws[((long long)blockIdx.z * M + row) * N + col] = a;
-          else
-            C[row * ldc + col] = alpha * (double)a;
+      // store-only: split-K partials (summed later) or alpha * tile, one loop
+      // per kind of store
+      const Pow2 p2 = pow2_of(alpha);
+      auto rows_loop = [&](auto put) {
+        for (int rr = 0; rr < rows; ++rr) {
+          const long long row = m0 + rr;
+          for (int c = threadIdx.x; c < cols; c += NTHREADS)
+            put(total > 0 ? tile[rr * PITCH + c] : 0.f, row, n0 + c);
         }
-      }
+      };
+      if (ws)
+        rows_loop([&](float a, long long row, int col) {
+          ws[((long long)blockIdx.z * M + row) * N + col] = a;
+        });
+      else if (p2.ok)
+        rows_loop([&](float a, long long row, int col) {
+          C[row * ldc + col] = f32_to_f64_pow2(a, p2, alpha);
+        });
+      else
+        rows_loop([&](float a, long long row, int col) {
+          C[row * ldc + col] = alpha * f32_to_f64(a);
+        });
     } else {
       // C = alpha * tile + beta * C: the old values of RB rows are loaded
       // before the first store, so that each thread has RB loads in flight
@@ -379,6 +390,8 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
     // coalesced global stores (FP64 C, or FP32 split-K partials)
     const int lrow = warp * 32 + lane;
     const int t = threadIdx.x;  // 0..127
+    const Pow2 p2 = pow2_of(alpha);
+    const int smode = ws ? 0 : beta != 0.0 ? kStoreBeta : p2.ok ? kStorePow2 : kStoreScaled;
     int tc = 0;
     for (int w = blockIdx.x; w < items; w += gridDim.x, ++tc) {
       int m0, n0, kt0, nkt;
@@ -400,14 +413,17 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
 #pragma unroll
         for (int c0 = 0; c0 < NB; c0 += 16) {
           uint32_t r[16];
-          tmem_ld16(taddr + c0, r);
           if (R::NACC == 2) {
+            // both accumulators' columns in flight before one wait
             uint32_t q[16];
-            tmem_ld16(taddr + NB + c0, q);
+            tmem_ld16_nowait(taddr + c0, r);
+            tmem_ld16_nowait(taddr + NB + c0, q);
+            tmem_wait_ld();
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj)
               epi[lrow * PITCH + c0 + jj] = __uint_as_float(r[jj]) + __uint_as_float(q[jj]);
           } else {
+            tmem_ld16(taddr + c0, r);
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) epi[lrow * PITCH + c0 + jj] = __uint_as_float(r[jj]);
           }
@@ -421,35 +437,34 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
       asm volatile("bar.sync 1, 128;" ::: "memory");
       const int rows = min(BM, M - m0), cols = min(NB, N - n0);
       const int kz = w / (mt * nt);
-      if (!trans) {
-        // 128 / NB rows per pass, NB columns each
-        for (int rr = t / NB; rr < rows; rr += 128 / NB) {
-          const int c = t % NB;
-          if (c >= cols) continue;
-          const long long row = m0 + rr;
-          const float a = epi[rr * PITCH + c];
-          if (ws)
-            ws[((long long)kz * M + row) * N + n0 + c] = a;
-          else if (beta == 0.0)
-            C[row * ldc + n0 + c] = alpha * (double)a;
-          else
-            C[row * ldc + n0 + c] = fma(alpha, (double)a, beta * C[row * ldc + n0 + c]);
+      // (r, c) of the caller's C: tile row rr, column c; or, for the
+      // exchanged product, tile row t is column m0 + t of the caller's C
+      // (row n0 + c) and consecutive threads write consecutive columns
+      auto tile_loop = [&](auto put) {
+        if (!trans) {
+          // 128 / NB rows per pass, NB columns each
+          for (int rr = t / NB; rr < rows; rr += 128 / NB) {
+            const int c = t % NB;
+            if (c < cols) put(epi[rr * PITCH + c], (long long)(m0 + rr), (long long)(n0 + c));
+          }
+        } else if (t < rows) {
+          for (int c = 0; c < cols; ++c)
+            put(epi[t * PITCH + c], (long long)(n0 + c), (long long)(m0 + t));
         }
-      } else if (t < rows) {
-        // the caller's product is the transpose of this one: tile row t is
-        // column m0 + t of the caller's C (row n0 + c); consecutive threads
-        // write consecutive columns
-        for (int c = 0; c < cols; ++c) {
-          const long long crow = n0 + c, ccol = m0 + t;
-          const float a = epi[t * PITCH + c];
-          if (ws)
-            ws[((long long)kz * N + crow) * M + ccol] = a;
-          else if (beta == 0.0)
-            C[crow * ldc + ccol] = alpha * (double)a;
-          else
-            C[crow * ldc + ccol] = fma(alpha, (double)a, beta * C[crow * ldc + ccol]);
-        }
-      }
+      };
+      const long long Mo = trans ? N : M, No = trans ? M : N;
+      if (smode == 0)
+        tile_loop([&](float a, long long r, long long c) { ws[((long long)kz * Mo + r) * No + c] = a; });
+      else if (smode == kStorePow2)
+        tile_loop([&](float a, long long r, long long c) {
+          C[r * ldc + c] = f32_to_f64_pow2(a, p2, alpha);
+        });
+      else if (smode == kStoreScaled)
+        tile_loop([&](float a, long long r, long long c) { C[r * ldc + c] = alpha * f32_to_f64(a); });
+      else
+        tile_loop([&](float a, long long r, long long c) {
+          C[r * ldc + c] = fma(alpha, (double)a, beta * C[r * ldc + c]);
+        });
       asm volatile("bar.sync 1, 128;" ::: "memory");
     }
   }
@@ -470,13 +485,31 @@ __device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
   hi = t;
 }
 
+// The output of a compensated sum hi + lo, alpha (hi + lo) (+ beta c), with
+// the FP32 -> FP64 conversions in integer arithmetic: no FP64 operation for a
+// power-of-two alpha and lo = 0, one addition when lo != 0; another alpha
+// multiplies in FP64 (equal to the plain FP64 expression, signed zeros aside).
+template <int MODE>
+__device__ __forceinline__ double reduce_out(float hi, float lo, const Pow2& p2, double alpha,
+                                             double beta, const double* c) {
+  if (MODE == kStorePow2) {
+    const double h = f32_to_f64_pow2(hi, p2, alpha);
+    return lo == 0.f ? h : h + f32_to_f64_pow2(lo, p2, alpha);
+  }
+  const double acc = f32_to_f64(hi) + f32_to_f64(lo);
+  if (MODE == kStoreScaled) return alpha * acc;
+  return fma(alpha, acc, beta * *c);
+}
+
 // C = alpha * sum_z ws[z] + beta * C.  The FP32 partials are summed in FP32
 // with a compensation term (Fast2Sum), i.e. to about 2^-48 relative, in a
 // fixed order, and converted to FP64 once: the FP64 units are the scarce
 // ones on this part.
+template <int MODE>
 __global__ void splitk_reduce_kernel(double* __restrict__ C, long long ldc,
                                      const float* __restrict__ ws, long long M, long long N,
                                      int nz, double alpha, double beta) {
+  const Pow2 p2 = pow2_of(alpha);
   const long long total = M * N;
   for (long long m = blockIdx.y; m < M; m += gridDim.y) {
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
@@ -484,9 +517,8 @@ __global__ void splitk_reduce_kernel(double* __restrict__ C, long long ldc,
       const long long idx = m * N + n;
       float hi = 0.f, lo = 0.f;
       for (int z = 0; z < nz; ++z) comp_add(hi, lo, ws[(long long)z * total + idx]);
-      const double acc = (double)hi + (double)lo;
       double* c = C + m * ldc + n;
-      *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *c);
+      *c = reduce_out<MODE>(hi, lo, p2, alpha, beta, c);
     }
   }
 }
@@ -495,9 +527,11 @@ __global__ void splitk_reduce_kernel(double* __restrict__ C, long long ldc,
 // aligned: each thread takes four neighbouring columns with 16-byte loads and
 // keeps four K-chunks in flight.  Every element is summed in the same order as
 // above, so the results are identical.
+template <int MODE>
 __global__ void splitk_reduce4_kernel(double* __restrict__ C, long long ldc,
                                       const float* __restrict__ ws, long long M, long long N,
                                       int nz, double alpha, double beta) {
+  const Pow2 p2 = pow2_of(alpha);
   const long long n4 = N / 4, total4 = M * n4;
   const float4* __restrict__ w4 = reinterpret_cast<const float4*>(ws);
   for (long long m = blockIdx.y; m < M; m += gridDim.y) {
@@ -527,10 +561,7 @@ __global__ void splitk_reduce4_kernel(double* __restrict__ C, long long ldc,
       }
       double* c = C + m * ldc + 4 * q;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const double acc = (double)hi[e] + (double)lo[e];
-        c[e] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * c[e]);
-      }
+      for (int e = 0; e < 4; ++e) c[e] = reduce_out<MODE>(hi[e], lo[e], p2, alpha, beta, c + e);
     }
   }
 }
@@ -539,9 +570,11 @@ __global__ void splitk_reduce4_kernel(double* __restrict__ C, long long ldc,
 // product goes to C + matview_row(v, m) + (offset of n over the view's
 // column dimensions).  by_rows: consecutive threads take consecutive rows
 // (when the view's rows, not its columns, are the contiguous side).
+template <int MODE>
 __global__ void splitk_reduce_view_kernel(double* __restrict__ C, MatView v,
                                           const float* __restrict__ ws, long long M, long long N,
                                           int nz, double alpha, double beta, bool by_rows) {
+  const Pow2 p2 = pow2_of(alpha);
   const long long total = M * N;
   const long long outer = by_rows ? N : M, inner = by_rows ? M : N;
   for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
@@ -551,15 +584,15 @@ __global__ void splitk_reduce_view_kernel(double* __restrict__ C, MatView v,
       const long long idx = m * N + n;
       float hi = 0.f, lo = 0.f;
       for (int z = 0; z < nz; ++z) comp_add(hi, lo, ws[(long long)z * total + idx]);
-      const double acc = (double)hi + (double)lo;
-      long long off = matview_row(v, m), r = n;
+      long long off = matview_row<uint32_t>(v, (uint32_t)m);
+      uint32_t r = (uint32_t)n;
       for (int d = v.nk - 1; d >= 0; --d) {
-        const long long q = r / v.kext[d];
-        off += (r - q * v.kext[d]) * v.kstr[d];
+        const uint32_t e = (uint32_t)v.kext[d], q = r / e;
+        off += (long long)(r - q * e) * v.kstr[d];
         r = q;
       }
       double* c = C + off;
-      *c = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * *c);
+      *c = reduce_out<MODE>(hi, lo, p2, alpha, beta, c);
     }
   }
 }
@@ -568,17 +601,19 @@ __global__ void splitk_reduce_view_kernel(double* __restrict__ C, MatView v,
 // The value is rounded to FP32 once (24 significant bits, as many as three
 // planes hold) and split with exact FP32 subtractions.  Each thread converts a
 // run of 8 consecutive values of one row and writes 16 bytes per plane.
+template <typename I>
 __global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double* __restrict__ in,
                                   long long rows, long long K, long long ld, long long Kp,
                                   int nsplit, long long plane_stride) {
-  const long long runs = Kp / 8, total = rows * runs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+  const I runs = (I)(Kp / 8), total = (I)rows * runs;
+  for (I idx = blockIdx.x * (I)blockDim.x + threadIdx.x; idx < total;
+       idx += (I)gridDim.x * blockDim.x) {
+    const I rq = idx / runs;
+    const long long r = rq, k0 = (long long)(idx - rq * runs) * 8;
     const double* x = in + r * ld + k0;
     float f[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) f[j] = (k0 + j < K) ? (float)x[j] : 0.f;
+    for (int j = 0; j < 8; ++j) f[j] = (k0 + j < K) ? f64_to_f32_rn(x[j]) : 0.f;
     for (int s = 0; s < nsplit; ++s) {
       __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
@@ -593,19 +628,21 @@ __global__ void split_bf16_kernel(__nv_bfloat16* __restrict__ out, const double*
 }
 
 // The same from a strided tensor read through a MatView (no permuted copy).
+template <typename I>
 __global__ void split_bf16_view_kernel(__nv_bfloat16* __restrict__ out,
                                        const double* __restrict__ in, MatView v, long long rows,
                                        long long K, long long Kp, int nsplit,
                                        long long plane_stride, bool fast) {
-  const long long runs = Kp / 8, total = rows * runs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / runs, k0 = (idx - r * runs) * 8;
+  const I runs = (I)(Kp / 8), total = (I)rows * runs;
+  for (I idx = blockIdx.x * (I)blockDim.x + threadIdx.x; idx < total;
+       idx += (I)gridDim.x * blockDim.x) {
+    const I rq = idx / runs;
+    const long long r = rq, k0 = (long long)(idx - rq * runs) * 8;
     double x[8];
-    matview_run8(v, in + matview_row(v, r), k0, K, fast, x);
+    matview_run8<I>(v, in + matview_row<I>(v, rq), k0, K, fast, x);
     float f[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) f[j] = (float)x[j];
+    for (int j = 0; j < 8; ++j) f[j] = f64_to_f32_rn(x[j]);
     for (int s = 0; s < nsplit; ++s) {
       __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
@@ -633,7 +670,7 @@ __global__ void __launch_bounds__(256) split_bf16_view_t_kernel(
     const int mi = threadIdx.x >> 2, kr = (threadIdx.x & 3) * 8;
     float f[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) f[j] = (float)tile[kr + j][mi];
+    for (int j = 0; j < 8; ++j) f[j] = f64_to_f32_rn(tile[kr + j][mi]);
     if (m0 + mi < rows) {
       for (int s = 0; s < nsplit; ++s) {
         __align__(16) __nv_bfloat16 h[8];
@@ -691,7 +728,10 @@ void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t ro
   if (total == 0) return;
   if (plane_stride <= 0) plane_stride = total;
   const int g = (int)std::min<int64_t>((rows * (Kp / 8) + 255) / 256, 152 * 16);
-  split_bf16_kernel<<<g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit, plane_stride);
+  if (rows * (Kp / 8) + 256ll * g < (1ll << 32))
+    split_bf16_kernel<uint32_t><<<g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit, plane_stride);
+  else
+    split_bf16_kernel<long long><<<g, 256, 0, s>>>(out, in, rows, K, ld, Kp, nsplit, plane_stride);
   count_launch();
   check_launch("split_bf16");
 }
@@ -712,7 +752,12 @@ void split_bf16_view(cudaStream_t s, __nv_bfloat16* out, const double* in, const
   }
   const bool fast = v.kext[v.nk - 1] % 8 == 0;
   const int g = (int)std::min<int64_t>((rows * (Kp / 8) + 255) / 256, 152 * 16);
-  split_bf16_view_kernel<<<g, 256, 0, s>>>(out, in, v, rows, K, Kp, nsplit, plane_stride, fast);
+  if (rows * (Kp / 8) + 256ll * g < (1ll << 32))
+    split_bf16_view_kernel<uint32_t><<<g, 256, 0, s>>>(out, in, v, rows, K, Kp, nsplit,
+                                                       plane_stride, fast);
+  else
+    split_bf16_view_kernel<long long><<<g, 256, 0, s>>>(out, in, v, rows, K, Kp, nsplit,
+                                                        plane_stride, fast);
   count_launch();
   check_launch("split_bf16_view");
 }
@@ -841,24 +886,52 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   }
   if (cview) {
     const MatView& v = *cview;
+    ASCC_REQUIRE(M < (1ll << 32) && N < (1ll << 32), "gemm_split: output view too large");
     const bool by_rows = v.kstr[v.nk - 1] != 1 && v.mstr[v.nm - 1] == 1;
     const int64_t outer = by_rows ? N : M, inner = by_rows ? M : N;
     const unsigned gy = (unsigned)std::min<int64_t>(outer, 65535);
     const unsigned gx = (unsigned)std::min<int64_t>((inner + 255) / 256, 64);
-    splitk_reduce_view_kernel<<<dim3(gx, gy), 256, 0, s>>>(C, v, ws, M, N, splitk, alpha, beta,
-                                                           by_rows);
+    const int mode = host_store_mode(alpha, beta);
+#define ASCC_RV(MD)                                                                        \
+  splitk_reduce_view_kernel<MD><<<dim3(gx, gy), 256, 0, s>>>(C, v, ws, M, N, splitk, alpha, \
+                                                             beta, by_rows)
+    if (mode == kStorePow2)
+      ASCC_RV(kStorePow2);
+    else if (mode == kStoreScaled)
+      ASCC_RV(kStoreScaled);
+    else
+      ASCC_RV(kStoreBeta);
+#undef ASCC_RV
     count_launch();
     check_launch("splitk_reduce_view");
   } else if (splitk > 1) {
     const unsigned gy = (unsigned)std::min<int64_t>(M, 65535);
     if (N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0) {
       const unsigned gx = (unsigned)std::min<int64_t>((N / 4 + 255) / 256, 64);
-      splitk_reduce4_kernel<<<dim3(gx, gy), 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk,
-                                                          alpha, beta);
+      const int mode = host_store_mode(alpha, beta);
+#define ASCC_R4(MD)                                                                          \
+  splitk_reduce4_kernel<MD><<<dim3(gx, gy), 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk, \
+                                                         alpha, beta)
+      if (mode == kStorePow2)
+        ASCC_R4(kStorePow2);
+      else if (mode == kStoreScaled)
+        ASCC_R4(kStoreScaled);
+      else
+        ASCC_R4(kStoreBeta);
+#undef ASCC_R4
     } else {
       const unsigned gx = (unsigned)std::min<int64_t>((N + 255) / 256, 64);
-      splitk_reduce_kernel<<<dim3(gx, gy), 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk,
-                                                       alpha, beta);
+      const int mode = host_store_mode(alpha, beta);
+#define ASCC_R1(MD)                                                                        \
+  splitk_reduce_kernel<MD><<<dim3(gx, gy), 256, 0, s>>>(C, (long long)ldc, ws, M, N, splitk, \
+                                                        alpha, beta)
+      if (mode == kStorePow2)
+        ASCC_R1(kStorePow2);
+      else if (mode == kStoreScaled)
+        ASCC_R1(kStoreScaled);
+      else
+        ASCC_R1(kStoreBeta);
+#undef ASCC_R1
     }
     count_launch();
     check_launch("splitk_reduce");

@@ -336,15 +336,18 @@ struct OuterStrides {
   int64_t shape[8], astride[8], bstride[8], ostride[8];
 };
 
+template <typename I>
 __global__ void outer_kernel(double* __restrict__ out, const double* __restrict__ a,
                              const double* __restrict__ b, int64_t total, OuterStrides st,
                              double alpha, double beta) {
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t rem = idx, ao = 0, bo = 0, oo = 0;
+  for (I idx = blockIdx.x * (I)blockDim.x + threadIdx.x; idx < (I)total;
+       idx += (I)gridDim.x * blockDim.x) {
+    I rem = idx;
+    int64_t ao = 0, bo = 0, oo = 0;
     for (int d = st.nd - 1; d >= 0; --d) {
-      const int64_t c = rem % st.shape[d];
-      rem /= st.shape[d];
+      const I e = (I)st.shape[d], q = rem / e;
+      const int64_t c = (int64_t)(rem - q * e);
+      rem = q;
       ao += c * st.astride[d];
       bo += c * st.bstride[d];
       oo += c * st.ostride[d];
@@ -867,7 +870,11 @@ void outer(cudaStream_t s, double* out, const int64_t* out_stride, const double*
     ++st.nd;
   }
   if (total == 0) return;
-  outer_kernel<<<grid_for(total), 256, 0, s>>>(out, a, b, total, st, alpha, beta);
+  const int g = grid_for(total);
+  if (total + 256ll * g < (1ll << 32))
+    outer_kernel<uint32_t><<<g, 256, 0, s>>>(out, a, b, total, st, alpha, beta);
+  else
+    outer_kernel<int64_t><<<g, 256, 0, s>>>(out, a, b, total, st, alpha, beta);
   count_launch();
   check_launch("outer");
 }

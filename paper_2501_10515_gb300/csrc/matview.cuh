@@ -7,11 +7,15 @@
 
 namespace ascc {
 
-__device__ __forceinline__ long long matview_row(const MatView& v, long long r) {
+// I: the type of the index arithmetic (32-bit whenever the extents allow:
+// a 64-bit division is a long instruction sequence).
+template <typename I = long long>
+__device__ __forceinline__ long long matview_row(const MatView& v, I r) {
   long long off = 0;
   for (int d = v.nm - 1; d >= 0; --d) {
-    const long long q = r / v.mext[d];
-    off += (r - q * v.mext[d]) * v.mstr[d];
+    const I e = (I)v.mext[d];
+    const I q = r / e;
+    off += (long long)(r - q * e) * v.mstr[d];
     r = q;
   }
   return off;
@@ -20,13 +24,16 @@ __device__ __forceinline__ long long matview_row(const MatView& v, long long r) 
 // x[j] = element (row, k0 + j) for k0 + j < K, else 0; row points at the
 // row's first element.  When the last column dimension is contiguous and a
 // multiple of 8 long (fast), a run that starts at a multiple of 8 stays in it.
+template <typename I = long long>
 __device__ __forceinline__ void matview_run8(const MatView& v, const double* __restrict__ row,
                                              long long k0, long long K, bool fast, double* x) {
   long long idx[4] = {0, 0, 0, 0};
-  long long off = 0, rem = k0;
+  long long off = 0;
+  I rem = (I)k0;
   for (int d = v.nk - 1; d >= 0; --d) {
-    const long long q = rem / v.kext[d];
-    idx[d] = rem - q * v.kext[d];
+    const I e = (I)v.kext[d];
+    const I q = rem / e;
+    idx[d] = (long long)(rem - q * e);
     off += idx[d] * v.kstr[d];
     rem = q;
   }

@@ -303,7 +303,14 @@ void T3pProgram::select(int b, const char* spec, int64_t* offset, std::vector<in
 // Contractions of at least this many flops run on the tensor cores when the
 // state uses them: most of the program's products are small (an o x v x v
 // block against a v x v one), and the FP64 units would serialise them.
-constexpr double kTcMinFlops = 1e6;
+// (ASCC_T3P_TC_MIN_FLOPS overrides it.)
+double tc_min_flops() {
+  static const double v = [] {
+    const char* env = std::getenv("ASCC_T3P_TC_MIN_FLOPS");
+    return env ? std::atof(env) : 1e6;
+  }();
+  return v;
+}
 
 // One op.  base: the operands; outb: where accumulations into the output
 // blocks go (the outputs themselves, or a stream's private copies); tmp: room
@@ -354,7 +361,7 @@ void T3pProgram::exec_op(int q, Einsum& es, cudaStream_t s, double* const* base,
 void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* base,
                      double scale, double* ws) const {
   const double min0 = es.min_flops();
-  if (es.level() > 0) es.set_split(es.level(), es.err(), std::min(min0, kTcMinFlops));
+  if (es.level() > 0) es.set_split(es.level(), es.err(), std::min(min0, tc_min_flops()));
   // every tensor of a section is written once before it is read, so its
   // planes stay valid for the rest of the section
   es.cache_reset(cache_bytes());
@@ -403,7 +410,7 @@ void T3pProgram::run_streams(T3pStreams& ex, int section, double* const* base, d
   for (int k = 0; k < ns; ++k) {
     Einsum& e = *ex.es[k];
     min0[k] = e.min_flops();
-    if (e.level() > 0) e.set_split(e.level(), e.err(), std::min(min0[k], kTcMinFlops));
+    if (e.level() > 0) e.set_split(e.level(), e.err(), std::min(min0[k], tc_min_flops()));
     e.cache_reset(cache_bytes());
   }
   std::vector<double*> outb(T3P_NBASE * ns);

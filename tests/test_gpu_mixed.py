@@ -81,6 +81,54 @@ def test_short_k_split_gemm_matches_fp64(M, N, K, level):
         assert (C - ref).abs().max().item() / scale < LEVEL_TOL[level]
 
 
+def _rounding_cases(M, K, seed):
+    """FP64 values whose FP32 rounding is decided by every kind of dropped
+    tail: ties to even (both parities), just above and below a tie, carries
+    into the exponent, signed zeros; exponents within 2^+-60, so that no
+    plane of the split underflows."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sig = rng.integers(0, 1 << 52, size=(M, K), dtype=np.uint64)
+    tail = sig & np.uint64((1 << 29) - 1)
+    kind = rng.integers(0, 6, size=(M, K))
+    half = np.uint64(1 << 28)
+    tail = np.where(kind == 0, half, tail)                    # tie
+    tail = np.where(kind == 1, half + np.uint64(1), tail)     # just above
+    tail = np.where(kind == 2, half - np.uint64(1), tail)     # just below
+    sig = (sig & ~np.uint64((1 << 29) - 1)) | tail
+    sig = np.where(kind == 3, np.uint64((1 << 52) - 1), sig)  # carry into the exponent
+    exp = rng.integers(1023 - 60, 1023 + 60, size=(M, K)).astype(np.uint64)
+    neg = rng.integers(0, 2, size=(M, K)).astype(np.uint64)
+    bits = (neg << np.uint64(63)) | (exp << np.uint64(52)) | sig
+    x = bits.view(np.float64).copy()
+    x[kind == 4] = 0.0
+    x[(kind == 4) & (neg == 1)] = -0.0
+    x[0, :4] = [1e18, -1e-18, 1.0, -2.0]
+    return x
+
+
+@pytest.mark.parametrize("M,K", [(64, 64), (64, 300), (200, 200), (130, 3000)])
+def test_split_conversions_exact(M, K):
+    """C = alpha A I through the split GEMM: at 3 planes the planes of an
+    identity hold it exactly and every product has one nonzero term, so C is
+    alpha times the FP32 rounding of A, bit for bit (power-of-two alpha: exact
+    scaling; other alpha: the FP64 product); at 1 plane, the BF16 rounding of
+    that FP32 value.  Covers the thin, exchanged, 128 x 128 and split-K paths."""
+    import numpy as np
+    import torch
+    import paper_2501_10515_gb300 as pkg
+    A = torch.from_numpy(_rounding_cases(M, K, M + K)).cuda()
+    I = torch.eye(K, dtype=torch.float64, device="cuda")
+    f32 = A.to(torch.float32)
+    for level, alpha, want in ((3, -0.25, -0.25 * f32.double()), (3, 0.3, 0.3 * f32.double()),
+                               (1, 2.0, 2.0 * f32.to(torch.bfloat16).double())):
+        C = torch.full((M, K), np.nan, dtype=torch.float64, device="cuda")
+        pkg.gemm_split_bf16(A, I, C, level, alpha=alpha, beta=0.0)
+        torch.cuda.synchronize()
+        same = (C.view(torch.int64) == want.view(torch.int64)) | ((C == 0) & (want == 0))
+        assert bool(same.all()), (level, alpha, int((~same).sum()))
+
+
 def test_split_gemm_levels_improve():
     import torch
     import paper_2501_10515_gb300 as pkg
