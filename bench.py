@@ -383,6 +383,9 @@ def main():
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=180.0)
     ap.add_argument("--level", type=int, default=2)
+    ap.add_argument("--diis", type=int, default=0,
+                    help="DIIS history length (0: 32 with T3', whose amplitudes converge more "
+                         "slowly, else the library default 16)")
     ap.add_argument("--gemm-shape", default="400,44000,4096")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -409,8 +412,10 @@ def main():
     stream = torch.cuda.current_stream()
     mixed = args.precision != "fp64"  # tensor-core contractions
     prec = precision_code(pkg, args.precision)
+    diis = args.diis or (32 if args.triples else 16)
     ctx = pkg.Context(o, v, s.naux, s.eps, s.B, hole=wl["hole"], particle=wl["particle"],
-                      linearize=1, triples=args.triples, stream=stream.cuda_stream, precision=prec)
+                      linearize=1, triples=args.triples, stream=stream.cuda_stream, precision=prec,
+                      diis_dim=diis)
 
     def one_unit():
         if args.step == "solve":
@@ -478,7 +483,7 @@ def main():
     if mixed and args.step == "solve" and (args.fp64_iterations > 0 or args.fp64_solve):
         cf = pkg.Context(o, v, s.naux, None, None, hole=wl["hole"], particle=wl["particle"],
                          base=ctx, linearize=1, triples=args.triples, stream=stream.cuda_stream,
-                         precision=pkg.ASCC_FP64)
+                         precision=pkg.ASCC_FP64, diis_dim=diis)
         cf.reset()
         cf.iterate(1)
         torch.cuda.synchronize()
@@ -516,7 +521,7 @@ def main():
     e2e_energy = None
     for _ in range(args.e2e_steps):
         c2 = pkg.Context(o, v, s.naux, eps_p, B_p, hole=wl["hole"], particle=wl["particle"],
-                         linearize=1, triples=args.triples, precision=prec)
+                         linearize=1, triples=args.triples, precision=prec, diis_dim=diis)
         r2 = c2.solve()
         e2e_energy = r2.energy
         c2.close()
@@ -532,7 +537,7 @@ def main():
                    "method": "PLASCC" + ("+T3'" if args.triples else ""),
                    "triples": int(args.triples), "sigma": s.sigma,
                    "n_t3": int(n3_of(wl, args.triples)),
-                   "precision": args.precision, "parallelism": f"replicas{world}",
+                   "precision": args.precision, "diis_dim": diis, "parallelism": f"replicas{world}",
                    "l2": ("inputs larger than L2: the (xc|bd) block (%.1f GB as 3 BF16 planes, "
                           "%.1f GB as 6 digit planes, %.1f GB FP64) is streamed every iteration"
                           % (6.0 * (o + v) * v ** 3 / 1e9, 12.0 * (o + v) * v ** 3 / 1e9,

@@ -268,7 +268,7 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
     if (oz_level) {
       // exact digit-plane products (FP64-class)
       auto* ws = static_cast<long long*>(scratch(2, oz::ws_bytes(Ms, Ns)));
-      const int z = oz::splitk_for(Ms, Ns, Ks);
+      const int z = oz::splitk_for(Ms, Ns, Ks, fill_ > 0);
       if (sp.c == cl) {
         oz::gemm(s_, Ms, Ns, Ks, alpha, qa.p, qa.e, 0, qb.p, qb.e, 0, beta, C.p, Ns, ws, err_, z);
       } else {
@@ -279,7 +279,7 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
       return;
     }
     const __nv_bfloat16 *pa = qa.p, *pb = qb.p;
-    const int z = tc::splitk_for(Ms, Ns, Ks);
+    const int z = tc::splitk_for(Ms, Ns, Ks, fill_);
     // an output in another layout is written through a view by the reduction
     MatView vc;
     const bool view_c = sp.c != cl && matrix_view(C, sp.c, Ml, Nl, vc, true);

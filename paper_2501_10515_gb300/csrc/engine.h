@@ -51,6 +51,10 @@ class Einsum {
     key_b_ = b;
   }
   void cache_reset(size_t bytes) const;
+  // Work items a split-K product aims for (tiles x K chunks); 0: no chunks
+  // beyond the accuracy rule (launches on concurrent streams fill the SMs).
+  void set_fill(int items) const { fill_ = items; }
+  int fill() const { return fill_; }
 
  private:
   struct CacheEntry {
@@ -62,6 +66,7 @@ class Einsum {
   mutable DevBuf cache_buf_;
   mutable size_t cache_used_ = 0;
   mutable int64_t key_a_ = -1, key_b_ = -1;
+  mutable int fill_ = 2 * 152;
   cudaStream_t s_;
   mutable bool frozen_ = false;
   int level_ = 0;

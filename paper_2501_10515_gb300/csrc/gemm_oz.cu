@@ -627,7 +627,8 @@ void split_view(cudaStream_t s, __nv_bfloat16* planes, int32_t* exps, const doub
   check_launch("oz_split_view");
 }
 
-int splitk_for(int64_t M, int64_t N, int64_t K) {
+int splitk_for(int64_t M, int64_t N, int64_t K, bool fill) {
+  if (!fill) return 1;
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int64_t num_kt = (K + BK - 1) / BK;
   // each slice keeps at least two exact chunks; among those, the split whose

@@ -64,7 +64,8 @@ void gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const _
           int splitk = 1);
 
 // Number of K slices that fills the GPU's SMs most evenly for an M x N x K product.
-int splitk_for(int64_t M, int64_t N, int64_t K);
+// (fill = false: one slice, the SMs left to concurrent launches.)
+int splitk_for(int64_t M, int64_t N, int64_t K, bool fill = true);
 
 // Number of BF16 x BF16 plane products per K step.
 constexpr int products() { return NSLICE * (NSLICE + 1) / 2; }

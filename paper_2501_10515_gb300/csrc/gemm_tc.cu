@@ -772,16 +772,16 @@ int products_for(int level) { return level == 1 ? 1 : level == 2 ? 3 : 6; }
 // its MMAs, and the persistent kernel overlaps the two.
 constexpr int64_t NARROW_N = 128, NARROW_M = 64, SHORT_K = 1024;
 
-int splitk_for(int64_t M, int64_t N, int64_t K) {
+int splitk_for(int64_t M, int64_t N, int64_t K, int fill) {
   // K chunks of at most 2048 (FP32 accumulation error ~ 2^-24 sqrt(K/16) per chunk),
-  // and enough work items to fill the GPU for small M x N
+  // and at least `fill` work items when K allows (fill the GPU for small M x N)
   const bool swap = M <= NARROW_M && N > NARROW_N;
   if (swap) std::swap(M, N);
   const int64_t bn = N <= NARROW_N ? 64 : padded_k(K) <= SHORT_K ? 128 : BN;
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + bn - 1) / bn);
   const int64_t num_kt = (K + BK - 1) / BK;
   int64_t z = (K + 2047) / 2048;
-  while (tiles * z < 2 * 152 && z < num_kt) ++z;
+  while (tiles * z < fill && z < num_kt) ++z;
   return (int)std::min<int64_t>(std::max<int64_t>(z, 1), std::min<int64_t>(num_kt, 512));
 }
 

@@ -41,7 +41,9 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
                 int64_t b_plane_stride = 0, const MatView* cview = nullptr);
 
 // Number of K chunks the residual engine uses for an M x N x K product.
-int splitk_for(int64_t M, int64_t N, int64_t K);
+// fill: the work items (tiles x chunks) aimed for; fewer chunks leave the SMs
+// to concurrent launches.
+int splitk_for(int64_t M, int64_t N, int64_t K, int fill = 2 * 152);
 
 }  // namespace tc
 }  // namespace ascc

@@ -304,6 +304,17 @@ void T3pProgram::select(int b, const char* spec, int64_t* offset, std::vector<in
 // state uses them: most of the program's products are small (an o x v x v
 // block against a v x v one), and the FP64 units would serialise them.
 // (ASCC_T3P_TC_MIN_FLOPS overrides it.)
+// Split-K work-item target of the program's products (ASCC_T3P_SPLITK_FILL
+// overrides it): the sections run on several streams, whose launches fill
+// the SMs that a product leaves.
+int t3p_fill() {
+  static const int v = [] {
+    const char* env = std::getenv("ASCC_T3P_SPLITK_FILL");
+    return env ? std::atoi(env) : 76;
+  }();
+  return v;
+}
+
 double tc_min_flops() {
   static const double v = [] {
     const char* env = std::getenv("ASCC_T3P_TC_MIN_FLOPS");
@@ -365,6 +376,8 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
   // every tensor of a section is written once before it is read, so its
   // planes stay valid for the rest of the section
   es.cache_reset(cache_bytes());
+  const int fill0 = es.fill();
+  es.set_fill(t3p_fill());
   // optional per-op timing (ASCC_T3P_PROFILE=<file>): CUDA events around
   // every op, summed per op and written to the file when the program is freed
   const bool prof = profile_path_ != nullptr;
@@ -381,6 +394,7 @@ void T3pProgram::run(Einsum& es, cudaStream_t s, int section, double* const* bas
     if (prof) ASCC_CUDA(cudaEventRecord(prof_ev_[2 * q + 1], s));
   }
   es.set_split(es.level(), es.err(), min0);
+  es.set_fill(fill0);
   if (prof) {
     ASCC_CUDA(cudaStreamSynchronize(s));
     for (int q = 0; q < kT3pOpCount; ++q) {
@@ -412,6 +426,7 @@ void T3pProgram::run_streams(T3pStreams& ex, int section, double* const* base, d
     min0[k] = e.min_flops();
     if (e.level() > 0) e.set_split(e.level(), e.err(), std::min(min0[k], tc_min_flops()));
     e.cache_reset(cache_bytes());
+    e.set_fill(t3p_fill());
   }
   std::vector<double*> outb(T3P_NBASE * ns);
   for (int k = 0; k < ns; ++k) {
