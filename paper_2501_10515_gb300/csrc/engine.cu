@@ -606,18 +606,28 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
     if (opt_.precision == ASCC_MIXED_BF16) need = rows * (6.0 * kp + 12.0 * kq);
     else if (opt_.precision == ASCC_FP64_TC) need = rows * 12.0 * kq;
     else need = rows * 16.0 * K;
+    const bool mixed = opt_.precision == ASCC_MIXED_BF16;
     if (opt_.ladder_stream == 1) {
       stream_ladder_ = true;
     } else if (opt_.ladder_stream == 0 && !have) {
       size_t freeb = 0, totalb = 0;
       ASCC_CUDA(cudaMemGetInfo(&freeb, &totalb));
-      stream_ladder_ = need > 0.6 * (double)freeb;
+      if (need > 0.6 * (double)freeb) {
+        // mixed precision whose two forms of the block do not fit: the digit
+        // planes alone (the exact ladder in every phase), else streaming
+        if (mixed && rows * 12.0 * kq <= 0.6 * (double)freeb)
+          ladder_digits_ = true;
+        else
+          stream_ladder_ = true;
+      }
+    } else if (mixed && have && mol_->Gext_oz.bytes() && !mol_->Gext_bf16.bytes()) {
+      ladder_digits_ = true;  // a sibling of a state that stored the digit planes alone
     }
   }
   if (stream_ladder_) {
     // nothing stored: ladder_streamed() rebuilds the block in x-chunks
   } else if (opt_.precision == ASCC_MIXED_BF16) {
-    mol_->ensure_bf16_ladder();
+    if (!ladder_digits_) mol_->ensure_bf16_ladder();
     mol_->ensure_oz_ladder();  // FP64-class polishing evaluations
   } else if (opt_.precision == ASCC_FP64_TC) {
     mol_->ensure_oz_ladder();
@@ -995,7 +1005,9 @@ void State::ladder(const T& t2, const T& r2) {
     prof_begin();
     ladder_streamed(t2);
     prof_end();
-  } else if (es_.level() == 4) {
+  } else if (es_.level() == 4 || (ladder_digits_ && es_.level() > 0)) {
+    // exact digit-plane products (also in the low-precision phase of a mixed
+    // state that holds the block as digit planes only)
     const int64_t K = vv, Kq = oz::padded_k(K), rows = (int64_t)n * v;
     const __nv_bfloat16* G = M.Gext_oz.as<__nv_bfloat16>();
     const int32_t* eG = M.Gext_oz_exp.as<int32_t>();
@@ -1057,7 +1069,7 @@ void State::ladder(const T& t2, const T& r2) {
                           ? 2.0 * (double)vv * ((double)o * o * o * v + (double)npair * vv)
                           : 2.0 * (double)npair * vvr * vv;
     ladder_flops_ += fl;
-    ladder_mma_flops_ += fl * (es_.level() == 4   ? oz::products()
+    ladder_mma_flops_ += fl * ((es_.level() == 4 || ladder_digits_) ? oz::products()
                                : es_.level() > 0 ? tc::products_for(es_.level())
                                                  : 1);
   }
@@ -1333,6 +1345,9 @@ void State::reset() {
   next_slot_ = 0;
   iter_ = 0;
   iter_low_ = 0;
+  best_r_ = 0.0;
+  stall_n_ = 0;
+  nrefresh_ = 0;
   fp64_evals_ = 0;
   polish_ = false;
   need_refresh_ = false;
@@ -1397,14 +1412,32 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     }
     const int it = iter_++;
     if (lev == 2) ++iter_low_;
-    if (lev == 2 && std::isfinite(r_last_) && r_last_ <= opt_.polish_tol) {
-      // hand over to the polishing precision and re-evaluate (with an FP64-class
-      // correction) before testing convergence.  The DIIS history is kept: its
-      // error vectors carry the coarser residual but age out within diis_dim
-      // steps, and slowly converging states need the long history
-      polish_ = true;
-      need_refresh_ = true;
-      have_prev_ = false;
+    if (lev == 2 && std::isfinite(r_last_)) {
+      bool hand = r_last_ <= opt_.polish_tol;
+      if (!hand && r_last_ <= 100.0 * opt_.polish_tol) {
+        // a low-precision phase whose noise floor lies above polish_tol: hand
+        // over once max|R| has not halved for 8 steps
+        if (best_r_ == 0.0 || r_last_ < 0.5 * best_r_) {
+          best_r_ = r_last_;
+          stall_n_ = 0;
+        } else if (++stall_n_ >= 8) {
+          hand = true;
+        }
+      }
+      if (hand) {
+        // hand over to the polishing precision and re-evaluate (with an
+        // FP64-class correction) before testing convergence.  The DIIS history
+        // is kept: its error vectors carry the coarser residual but age out
+        // within diis_dim steps, and slowly converging states need the long
+        // history.  A state with the ladder as digit planes only polishes with
+        // FP64-class residuals throughout (no 6-product phase).
+        polish_ = true;
+        need_refresh_ = true;
+        have_prev_ = false;
+        best_r_ = 0.0;
+        stall_n_ = 0;
+        if (ladder_digits_) fallback_ = true;
+      }
     }
     if (!std::isfinite(e_last_) || !std::isfinite(r_last_)) {
       status_ = ASCC_ERR_DIVERGED;
@@ -1421,11 +1454,27 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
       done_ = true;
       break;
     }
-    if (lev == 3 && ++polish_its_ >= 30 + opt_.diis_dim) {
-      // the corrected iteration stalls (slowly converging states): continue with
-      // FP64-class residuals in every step; the history of corrected residuals
-      // is kept (they are FP64-class up to the drift of the correction)
-      fallback_ = true;
+    if (lev == 3) {
+      // The corrected residual R3(t) + [R64(t0) - R3(t0)] has a floor: the part
+      // of the 6-product rounding error that changes with t.  When max|R| has
+      // not halved for kStallSteps steps, the correction is taken again at the
+      // current amplitudes; after kMaxRefresh such refreshes (or a long
+      // polishing phase) every further step uses FP64-class residuals.  The
+      // history of corrected residuals is kept (they are FP64-class up to the
+      // drift of the correction).
+      constexpr int kStallSteps = 6, kMaxRefresh = 4;
+      if (refreshed || r_last_ < 0.5 * best_r_) {
+        best_r_ = r_last_;
+        stall_n_ = 0;
+      } else if (++stall_n_ >= kStallSteps) {
+        stall_n_ = 0;
+        best_r_ = r_last_;
+        if (++nrefresh_ > kMaxRefresh)
+          fallback_ = true;
+        else
+          need_refresh_ = true;
+      }
+      if (++polish_its_ >= 30 + opt_.diis_dim) fallback_ = true;
     }
     if (it >= opt_.max_iter) {
       status_ = ASCC_ERR_NOT_CONVERGED;
@@ -1495,8 +1544,12 @@ void State::checkpoint_save(void* buf, int64_t bytes) {
   const int64_t head[kCkptHeader] = {kCkptMagic, 1, o_, v_, n3(), opt_.precision, opt_.linearize,
                                      m, cnt, next_slot_, iter_, iter_low_, fp64_evals_,
                                      polish_its_, flags, (int64_t)status_, hole_, particle_,
-                                     lh_, lp_, (int64_t)(xsign_ < 0), 0, 0, 0};
+                                     lh_, lp_, (int64_t)(xsign_ < 0), stall_n_, nrefresh_,
+                                     0};
+  int64_t best_bits;
+  std::memcpy(&best_bits, &best_r_, sizeof(best_bits));
   std::memcpy(w, head, sizeof(head));
+  w[23] = best_bits;
   for (int64_t q = 0; q < cnt; ++q) w[kCkptHeader + q] = slots_[q];
   auto* d = reinterpret_cast<double*>(w + kCkptHeader + cnt);
   d[0] = e_prev_;
@@ -1556,6 +1609,9 @@ void State::checkpoint_load(const void* buf, int64_t bytes) {
   have_corr_ = (flags >> 4) & 1;
   fallback_ = (flags >> 5) & 1;
   status_ = (ascc_status)w[15];
+  stall_n_ = (int)w[21];
+  nrefresh_ = (int)w[22];
+  std::memcpy(&best_r_, &w[23], sizeof(best_r_));
   const auto* d = reinterpret_cast<const double*>(w + kCkptHeader + cnt);
   e_prev_ = d[0];
   e_last_ = d[1];

@@ -235,6 +235,10 @@ class State {
   // residuals throughout (it stalled); polish_its_ counts its iterations
   bool fallback_ = false;
   int polish_its_ = 0;
+  // stall detection of the corrected polishing iteration: the best max|R|
+  // since the last improvement by half, the steps since, and the refreshes
+  double best_r_ = 0.0;
+  int stall_n_ = 0, nrefresh_ = 0;
   int fp64_evals_ = 0;
   OT corr_;  // FP64-minus-polishing residual correction (mixed precision)
   double tc_min_flops_ = 4e7;  // contractions below this stay FP64 (ASCC_TC_MIN_FLOPS overrides)
@@ -247,6 +251,9 @@ class State {
   OT tpair_, Yvv_, Yov_;  // pair-symmetric ladder operands
   // streamed ladder: chunk buffers and the t operand's planes
   bool stream_ladder_ = false;
+  // mixed precision with the block stored as digit planes only: the ladder
+  // is an exact digit-plane product in every phase
+  bool ladder_digits_ = false;
   int64_t stream_chunk_bytes_ = (int64_t)1 << 30;
   OT stream_ac_, stream_gc_;
   DevBuf stream_a_, stream_ae_, stream_b_, stream_be_;
