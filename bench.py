@@ -580,9 +580,13 @@ def main():
         "energy_error_vs_oracle": (abs(last.energy - ref_e) if ref_e is not None else None),
         "oracle_energy_source": (f"tests/golden/reference_energies.txt {gname}"
                                  if ref_e is not None else
-                                 "none: the oracle's solve with T3' at this size is not feasible "
-                                 "on the host; tests/test_gpu_fullsize.py checks this residual "
-                                 "against tests/golden/c2_t3_residual.txt instead"),
+                                 ("none: the oracle's solve with T3' at this size is not "
+                                  "feasible on the host; tests/test_gpu_fullsize.py checks this "
+                                  "residual against tests/golden/c2_t3_residual.txt instead"
+                                  if args.triples else
+                                  "none: no oracle solve of this state is stored (the host has no "
+                                  "room for its FP64 (vv|vv) block); tests/test_gpu_c3_mixed.py "
+                                  "holds the mixed energy to the FP64-class one")),
         "e2e_energy": e2e_energy,
         "fp64_path": fp64,
     }

@@ -27,6 +27,13 @@ struct ascc_ctx {
     state.reset();
     if (stream) cudaStreamSynchronize(stream);
     if (own_stream && stream) cudaStreamDestroy(stream);
+    // the stream-ordered pool keeps freed blocks (its release threshold is
+    // unbounded, so that iterations reuse them): hand back what no other
+    // state holds, for the device's other users
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+      cudaMemPoolTrimTo(pool, 0);
   }
 };
 

@@ -612,6 +612,19 @@ State::State(std::shared_ptr<Molecule> mol, int hole, int particle, double beta,
     } else if (opt_.ladder_stream == 0 && !have) {
       size_t freeb = 0, totalb = 0;
       ASCC_CUDA(cudaMemGetInfo(&freeb, &totalb));
+      {
+        // blocks the stream-ordered pool holds but no allocation uses are free too
+        int dev = 0;
+        cudaMemPool_t pool;
+        uint64_t reserved = 0, used = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) ==
+                cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess &&
+            reserved > used)
+          freeb += (size_t)(reserved - used);
+      }
       if (need > 0.6 * (double)freeb) {
         // mixed precision whose two forms of the block do not fit: the digit
         // planes alone (the exact ladder in every phase), else streaming
