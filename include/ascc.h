@@ -241,6 +241,29 @@ ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level,
                                  double alpha, const double* A, const double* B,
                                  double beta, double* C, void* stream);
 
+/* The same product with an explicit tile shape of the tcgen05 kernel:
+ *   tile = 1: 128 x 256 tiles, one per CTA; 2: a persistent kernel (one CTA
+ *   per SM looping over tiles) with 128 x 128 tiles; 3: the persistent kernel
+ *   with 128 x 64 tiles (for M <= 64 < N the operands exchanged, the tile
+ *   stored transposed); -1: the size rules (what ascc_gemm_split_bf16 uses);
+ *   0: the autotuner's choice for the product's shape class, which runs the
+ *   three shapes once each, timed, the first time a class is seen on a
+ *   stream that is not being captured (that call allocates scratch for one
+ *   output and synchronises the stream; products above 2^25 output elements
+ *   or below 1e8 flops keep the size rules; ASCC_AUTOTUNE=0 turns tuning off).
+ * Every tile shape accumulates each element over the same K tiles in the
+ * same order, so the result does not depend on `tile`, with one exception:
+ * for M <= 64 < N, tile 3 and the size rules exchange the operands, which
+ * changes the order of the tensor core's sums (the autotuner leaves such
+ * products to the size rules).  The residual engine's tensor-core
+ * contractions use tile = 0. */
+ascc_status ascc_gemm_split_bf16_tiled(int64_t M, int64_t N, int64_t K, int32_t level,
+                                       double alpha, const double* A, const double* B,
+                                       double beta, double* C, void* stream, int32_t tile);
+
+/* Number of shape classes the tile autotuner has timed in this process. */
+int64_t ascc_autotuned_classes(void);
+
 /* FP64-class GEMM on the BF16 tensor cores (the contraction device behind
  * ASCC_FP64_TC and the polishing evaluations of ASCC_MIXED_BF16):
  *   C = alpha * A B^T + beta * C,

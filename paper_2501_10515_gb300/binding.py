@@ -97,6 +97,10 @@ def load():
         "ascc_get_profile": (C.c_int, [vp, P(Profile)]),
         "ascc_gemm_split_bf16": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_double,
                                            vp, vp, C.c_double, vp, vp]),
+        "ascc_gemm_split_bf16_tiled": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                                 C.c_double, vp, vp, C.c_double, vp, vp,
+                                                 C.c_int32]),
+        "ascc_autotuned_classes": (C.c_int64, []),
         "ascc_gemm_fp64_tc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, vp, vp,
                                         C.c_double, vp, vp]),
         "ascc_gemm_split_bf16_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32,
@@ -135,13 +139,24 @@ def _check(st):
         raise AsccError(st, load().ascc_last_error().decode())
 
 
-def gemm_split_bf16(A, B, out, level, alpha=1.0, beta=0.0, stream=None):
-    """out = alpha A B^T + beta out on device FP64 tensors (split-BF16 tensor cores)."""
+def gemm_split_bf16(A, B, out, level, alpha=1.0, beta=0.0, stream=None, tile=None):
+    """out = alpha A B^T + beta out on device FP64 tensors (split-BF16 tensor cores);
+    tile: None (the size rules) or the tile shape of ascc_gemm_split_bf16_tiled."""
     M, K = A.shape
     N = B.shape[0]
     assert tuple(out.shape) == (M, N) and B.shape[1] == K
-    _check(load().ascc_gemm_split_bf16(M, N, K, level, alpha, C_void(A), C_void(B), beta,
-                                       C_void(out), C.c_void_p(stream) if stream else None))
+    st = C.c_void_p(stream) if stream else None
+    if tile is None:
+        _check(load().ascc_gemm_split_bf16(M, N, K, level, alpha, C_void(A), C_void(B), beta,
+                                           C_void(out), st))
+    else:
+        _check(load().ascc_gemm_split_bf16_tiled(M, N, K, level, alpha, C_void(A), C_void(B),
+                                                 beta, C_void(out), st, int(tile)))
+
+
+def autotuned_classes():
+    """Shape classes the tile autotuner has timed in this process."""
+    return int(load().ascc_autotuned_classes())
 
 
 def gemm_fp64_tc(A, B, out, alpha=1.0, beta=0.0, stream=None):

@@ -386,7 +386,14 @@ ascc_status ascc_get_profile(ascc_ctx* ctx, ascc_profile* out) {
 ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level, double alpha,
                                  const double* A, const double* B, double beta, double* C,
                                  void* stream) {
+  return ascc_gemm_split_bf16_tiled(M, N, K, level, alpha, A, B, beta, C, stream, -1);
+}
+
+ascc_status ascc_gemm_split_bf16_tiled(int64_t M, int64_t N, int64_t K, int32_t level,
+                                       double alpha, const double* A, const double* B, double beta,
+                                       double* C, void* stream, int32_t tile) {
   return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(tile >= -1 && tile <= 3, "tile must be -1, 0, 1, 2 or 3");
     ASCC_REQUIRE(A && B && C && M > 0 && N > 0 && K > 0, "bad argument");
     ASCC_REQUIRE(level >= 1 && level <= 3, "level must be 1, 2 or 3");
     cudaStream_t s = (cudaStream_t)stream;
@@ -409,7 +416,7 @@ ascc_status ascc_gemm_split_bf16(int64_t M, int64_t N, int64_t K, int32_t level,
     const int z = tc::splitk_for(M, N, K);
     DevBuf ws(z > 1 ? sizeof(float) * (size_t)(z * M * N) : 0, s);
     tc::gemm_split(s, M, N, K, level, alpha, pa.as<__nv_bfloat16>(), pb.as<__nv_bfloat16>(), beta,
-                   C, N, err, z, ws.as<float>());
+                   C, N, err, z, ws.as<float>(), 0, nullptr, tile);
     return ASCC_OK;
   });
 }
@@ -523,6 +530,8 @@ int64_t ascc_launch_count(const ascc_ctx* ctx) {
 }
 
 void ascc_destroy(ascc_ctx* ctx) { delete ctx; }
+
+int64_t ascc_autotuned_classes(void) { return tc::autotuned_classes(); }
 
 const char* ascc_status_string(ascc_status s) {
   switch (s) {

@@ -1427,7 +1427,7 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     if (lev == 2) ++iter_low_;
     if (lev == 2 && std::isfinite(r_last_)) {
       bool hand = r_last_ <= opt_.polish_tol;
-      if (!hand && r_last_ <= 100.0 * opt_.polish_tol) {
+      if (!hand && r_last_ <= 10.0 * opt_.polish_tol) {
         // a low-precision phase whose noise floor lies above polish_tol: hand
         // over once max|R| has not halved for 8 steps
         if (best_r_ == 0.0 || r_last_ < 0.5 * best_r_) {
@@ -1475,7 +1475,7 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
       // polishing phase) every further step uses FP64-class residuals.  The
       // history of corrected residuals is kept (they are FP64-class up to the
       // drift of the correction).
-      constexpr int kStallSteps = 6, kMaxRefresh = 4;
+      constexpr int kStallSteps = 8, kMaxRefresh = 4;
       if (refreshed || r_last_ < 0.5 * best_r_) {
         best_r_ = r_last_;
         stall_n_ = 0;

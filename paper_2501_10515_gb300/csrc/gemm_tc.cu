@@ -16,6 +16,8 @@
 // 2-second %globaltimer budget; on expiry the kernel records an error code,
 // skips the remaining work, frees its TMEM and returns.
 #include <algorithm>
+#include <cstdlib>
+#include <map>
 #include <mutex>
 
 #include "fpconv.cuh"
@@ -785,9 +787,88 @@ int splitk_for(int64_t M, int64_t N, int64_t K, int fill) {
   return (int)std::min<int64_t>(std::max<int64_t>(z, 1), std::min<int64_t>(num_kt, 512));
 }
 
+namespace {
+std::mutex g_tune_mu;
+std::map<uint64_t, int> g_tune;
+
+int ilog2_ceil(int64_t x) {
+  int r = 0;
+  while ((int64_t(1) << r) < x) ++r;
+  return r;
+}
+
+// The tile shape for this product: the tuned one of its class, tuning the
+// class first when allowed (see autotuned_classes in gemm_tc.h).
+int tuned_tile(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level,
+               const __nv_bfloat16* A, const __nv_bfloat16* B, int splitk, float* ws,
+               int64_t b_plane_stride, int* err) {
+  static const bool on = [] {
+    const char* e = std::getenv("ASCC_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  if (!on) return kTileRules;
+  const double flops = 2.0 * (double)M * N * K;
+  if (M * N > (int64_t(1) << 25) || flops < 1e8) return kTileRules;
+  // M <= 64 < N runs with the operands exchanged, which changes the order of
+  // the tensor core's sums: those products keep the size rules
+  if (M <= NARROW_M && N > NARROW_N) return kTileRules;
+  const int64_t kc = (padded_k(K) + splitk - 1) / splitk;
+  const uint64_t key = (uint64_t)level | (uint64_t)ilog2_ceil(M) << 4 |
+                       (uint64_t)ilog2_ceil(N) << 10 | (uint64_t)ilog2_ceil(kc) << 16 |
+                       (uint64_t)(splitk > 1) << 22;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return kTileRules;
+  // candidates: every shape; scratch output, beta = 0, the caller's planes and
+  // split-K workspace (all on this stream, before the caller's own product)
+  double* Cs = nullptr;
+  ASCC_CUDA(cudaMallocAsync(&Cs, sizeof(double) * (size_t)(M * N), s));
+  const int cands[3] = {kTileWide, kTile128, kTile64};
+  float best = 1e30f;
+  int pick = kTileRules;
+  cudaEvent_t e0, e1;
+  ASCC_CUDA(cudaEventCreate(&e0));
+  ASCC_CUDA(cudaEventCreate(&e1));
+  for (int c : cands) {
+    gemm_split(s, M, N, K, level, 1.0, A, B, 0.0, Cs, N, err, splitk, ws, b_plane_stride,
+               nullptr, c);  // warm-up
+    ASCC_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 2; ++r)
+      gemm_split(s, M, N, K, level, 1.0, A, B, 0.0, Cs, N, err, splitk, ws, b_plane_stride,
+                 nullptr, c);
+    ASCC_CUDA(cudaEventRecord(e1, s));
+    ASCC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    ASCC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  ASCC_CUDA(cudaEventDestroy(e0));
+  ASCC_CUDA(cudaEventDestroy(e1));
+  ASCC_CUDA(cudaFreeAsync(Cs, s));
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = pick;
+  return pick;
+}
+}  // namespace
+
+int64_t autotuned_classes() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int64_t)g_tune.size();
+}
+
 void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
                 const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C, int64_t ldc,
-                int* err, int splitk, float* ws, int64_t b_plane_stride, const MatView* cview) {
+                int* err, int splitk, float* ws, int64_t b_plane_stride, const MatView* cview,
+                int tile) {
+  if (tile == kTileAuto) tile = tuned_tile(s, M, N, K, level, A, B, splitk, ws, b_plane_stride, err);
   ASCC_REQUIRE(level >= 1 && level <= 3, "split level 1..3");
   ASCC_REQUIRE(!cview || ws, "gemm_split: an output view needs a workspace");
   ASCC_REQUIRE(M > 0 && N > 0 && K > 0, "gemm_split: empty");
@@ -810,9 +891,18 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   const int64_t Kp = padded_k(K);
   const int num_kt = (int)(Kp / TK);
   const int kt_chunk = (num_kt + splitk - 1) / splitk;
-  const bool swap = M <= NARROW_M && N > NARROW_N;
-  const bool thin = N <= NARROW_N || swap;
-  const bool shortk = !thin && (int64_t)kt_chunk * TK <= SHORT_K;
+  bool swap = M <= NARROW_M && N > NARROW_N;
+  bool thin = N <= NARROW_N || swap;
+  bool shortk = !thin && (int64_t)kt_chunk * TK <= SHORT_K;
+  if (tile == kTileWide) {
+    swap = thin = shortk = false;
+  } else if (tile == kTile128) {
+    swap = thin = false;
+    shortk = true;
+  } else if (tile == kTile64) {
+    thin = true;
+    shortk = false;
+  }
   const bool narrow = thin || shortk;   // the persistent kernel
   const int nbt = thin ? 64 : 128;      // its tile width
   const int64_t bstride = b_plane_stride > 0 ? b_plane_stride : N * Kp;

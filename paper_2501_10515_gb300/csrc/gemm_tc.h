@@ -35,10 +35,31 @@ void split_bf16_view(cudaStream_t s, __nv_bfloat16* out, const double* in, const
 // so that a row block of a larger plane set can serve as B.
 // cview: C written through a view (rows over its M dimensions, columns over
 // its column dimensions; ldc unused), the partials always going through ws.
+// tile: the kernel's tile shape (TileShape).  For a given splitk every shape
+// accumulates each element over the same K tiles in the same order, so the
+// choice does not change the result, except that kTile64 (and the size rules)
+// exchange the operands for M <= 64 < N, which changes the order of the
+// tensor core's sums; the autotuner leaves those products to the rules.
+enum TileShape {
+  kTileRules = -1,  // the size rules alone (no tuning: no allocation, no sync)
+  kTileAuto = 0,    // the autotuner's choice for the shape class, else the rules
+  kTileWide = 1,    // 128 x 256, one tile per CTA
+  kTile128 = 2,     // persistent, 128 x 128
+  kTile64 = 3       // persistent, 128 x 64 (operands exchanged for M <= 64 < N)
+};
 void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, double alpha,
                 const __nv_bfloat16* A, const __nv_bfloat16* B, double beta, double* C,
                 int64_t ldc, int* err, int splitk = 1, float* ws = nullptr,
-                int64_t b_plane_stride = 0, const MatView* cview = nullptr);
+                int64_t b_plane_stride = 0, const MatView* cview = nullptr,
+                int tile = kTileAuto);
+
+// Autotuner of the tile shape (ASCC_AUTOTUNE=0 turns it off): the first
+// product of a shape class (level, and M, N, K per chunk and split-K rounded
+// to powers of two) on a stream that is not being captured runs once per
+// candidate shape into scratch memory, timed with CUDA events, and the
+// fastest is kept for the class.  Products above 2^25 output elements or
+// below 10^8 flops keep the size rules.  Returns the number of classes tuned.
+int64_t autotuned_classes();
 
 // Number of K chunks the residual engine uses for an M x N x K product.
 // fill: the work items (tiles x chunks) aimed for; fewer chunks leave the SMs

@@ -100,7 +100,8 @@ extern "C" ascc_status ascc_gemm_split_bf16_noalloc(int64_t M, int64_t N, int64_
     ASCC_CUDA(cudaMemsetAsync(sc.err, 0, sizeof(int), s));
     tc::split_bf16(s, pa, A, M, K, K, level);
     tc::split_bf16(s, pb, B, N, K, K, level);
-    tc::gemm_split(s, M, N, K, level, alpha, pa, pb, beta, C, N, sc.err, z, ws);
+    tc::gemm_split(s, M, N, K, level, alpha, pa, pb, beta, C, N, sc.err, z, ws, 0, nullptr,
+                   tc::kTileRules);
     // this call's bounded device waits: read the flag back (synchronises s)
     int flag = 0;
     ASCC_CUDA(cudaMemcpyAsync(&flag, sc.err, sizeof(int), cudaMemcpyDeviceToHost, s));

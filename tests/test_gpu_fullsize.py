@@ -91,6 +91,22 @@ def test_fullsize_solve_matches_oracle_energy(system, prec_name, tol, exc, name)
     assert abs(res.energy - e_ref) <= tol, (res.energy, e_ref)
 
 
+def test_fullsize_fp64_dfma_solve_matches_oracle_energy(system):
+    """The plain FP64 path (every contraction on the DFMA units, no tensor
+    cores) solves the benchmark's excited state to the oracle's converged
+    energy within 1e-10 Eh (about 70 s on one GB300)."""
+    import paper_2501_10515_gb300 as pkg
+    s = system
+    e_ref = _golden("c2_plascc_excited")
+    assert e_ref is not None
+    ctx = pkg.Context(O, V, s.naux, s.eps, s.B, hole=19, particle=3, linearize=1,
+                      precision=pkg.ASCC_FP64)
+    res = ctx.solve()
+    ctx.close()
+    assert res.status == 0
+    assert abs(res.energy - e_ref) <= 1e-10, (res.energy, e_ref)
+
+
 def _t3_golden():
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_t3_residual.txt")
     if not os.path.exists(path):
