@@ -260,7 +260,8 @@ struct NarrowRing {
                                          : (LEVEL == 3 ? 3 : LEVEL == 2 ? 4 : 6);
   static constexpr int RING_BYTES = STAGES * STAGE_BYTES;
   static constexpr int EPI = BM * (NB + 1) * 4;
-  static constexpr int SMEM_BYTES = RING_BYTES + EPI + 1024 + 512;
+  static constexpr int OFFS = (BM + NB) * 8;     // a tile's row and column offsets (output view)
+  static constexpr int SMEM_BYTES = RING_BYTES + EPI + OFFS + 1024 + 512;
   static constexpr int NACC = Ring<LEVEL>::NACC;
   static constexpr int ACC_COLS = NACC * NB;      // one accumulator set
   static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two sets (a power of 2)
@@ -274,14 +275,15 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
                       const __grid_constant__ CUtensorMap bmap, int M, int N, int num_kt,
                       int kt_chunk, int splitk, double alpha, double beta,
                       double* __restrict__ C, long long ldc, float* __restrict__ ws, int* err,
-                      int trans) {
+                      int trans, const __grid_constant__ MatView cview, int has_view) {
   using G = NarrowRing<LEVEL, NB>;
   using R = Ring<LEVEL>;
   constexpr int STAGES = G::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* epi = reinterpret_cast<float*>(smem + G::RING_BYTES);
-  uint64_t* bars = (uint64_t*)(smem + G::RING_BYTES + G::EPI);
+  long long* voff = reinterpret_cast<long long*>(smem + G::RING_BYTES + G::EPI);  // [BM + NB]
+  uint64_t* bars = (uint64_t*)(smem + G::RING_BYTES + G::EPI + G::OFFS);
   // bars: full[STAGES], empty[STAGES], acc_full[2], acc_empty[2]
   uint32_t* tmem_holder = (uint32_t*)(bars + 2 * STAGES + 4);
   __shared__ int abort_flag, epi_fail;
@@ -455,17 +457,44 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
         }
       };
       const long long Mo = trans ? N : M, No = trans ? M : N;
+      // element (r, c) of the caller's C: row-major with ldc, or through the
+      // output view (rows over its M dimensions, columns over its others),
+      // whose offsets for this tile's rows and columns are formed once
+      const long long r0 = trans ? n0 : m0, c0 = trans ? m0 : n0;
+      const int nr = trans ? NB : BM, nc = trans ? BM : NB;
+      if (has_view) {
+        const long long Mc = trans ? N : M, Nc = trans ? M : N;  // the caller's C
+        for (int i = t; i < nr; i += 128)
+          voff[i] = r0 + i < Mc ? matview_row<uint32_t>(cview, (uint32_t)(r0 + i)) : 0;
+        for (int j = t; j < nc; j += 128) {
+          long long off = 0;
+          if (c0 + j < Nc) {
+            uint32_t q = (uint32_t)(c0 + j);
+            for (int d = cview.nk - 1; d >= 0; --d) {
+              const uint32_t e = (uint32_t)cview.kext[d], qq = q / e;
+              off += (long long)(q - qq * e) * cview.kstr[d];
+              q = qq;
+            }
+          }
+          voff[nr + j] = off;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
+      auto at = [&](long long r, long long c) -> long long {
+        return has_view ? voff[r - r0] + voff[nr + (c - c0)] : r * ldc + c;
+      };
       if (smode == 0)
         tile_loop([&](float a, long long r, long long c) { ws[((long long)kz * Mo + r) * No + c] = a; });
       else if (smode == kStorePow2)
         tile_loop([&](float a, long long r, long long c) {
-          C[r * ldc + c] = f32_to_f64_pow2(a, p2, alpha);
+          C[at(r, c)] = f32_to_f64_pow2(a, p2, alpha);
         });
       else if (smode == kStoreScaled)
-        tile_loop([&](float a, long long r, long long c) { C[r * ldc + c] = alpha * f32_to_f64(a); });
+        tile_loop([&](float a, long long r, long long c) { C[at(r, c)] = alpha * f32_to_f64(a); });
       else
         tile_loop([&](float a, long long r, long long c) {
-          C[r * ldc + c] = fma(alpha, (double)a, beta * C[r * ldc + c]);
+          const long long o = at(r, c);
+          C[o] = fma(alpha, (double)a, beta * C[o]);
         });
       asm volatile("bar.sync 1, 128;" ::: "memory");
     }
@@ -911,7 +940,11 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
   const CUtensorMap bm = swap ? make_planes_map(A, M, Kp, M * Kp, level, nbt)
                               : make_planes_map(B, N, Kp, bstride, level, narrow ? nbt : BN);
   count_flops(2.0 * (double)M * N * K);
-  float* wsp = (splitk > 1 || cview) ? ws : nullptr;
+  // the persistent kernel writes an output view itself when K is not split
+  const bool epi_view = cview && narrow && splitk == 1;
+  float* wsp = (splitk > 1 || (cview && !epi_view)) ? ws : nullptr;
+  MatView vnone;
+  const MatView& vpass = epi_view ? *cview : vnone;
   if (narrow) {
     static std::once_flag narrow_once;
     cudaError_t e = cudaSuccess;
@@ -936,7 +969,7 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
 #define ASCC_NARROW(LV, NBV)                                                                  \
   gemm_tc_narrow_kernel<LV, NBV><<<grid, threads, NarrowRing<LV, NBV>::SMEM_BYTES, s>>>(       \
       am, bm, (int)Mk, (int)Nk, num_kt, kt_chunk, splitk, alpha, beta, C, (long long)ldc, wsp, \
-      err, tr)
+      err, tr, vpass, epi_view ? 1 : 0)
     if (nbt == 64) {
       if (level == 1)
         ASCC_NARROW(1, 64);
@@ -974,7 +1007,7 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
     count_launch();
     check_launch("gemm_tc");
   }
-  if (cview) {
+  if (cview && !epi_view) {
     const MatView& v = *cview;
     ASCC_REQUIRE(M < (1ll << 32) && N < (1ll << 32), "gemm_split: output view too large");
     const bool by_rows = v.kstr[v.nk - 1] != 1 && v.mstr[v.nm - 1] == 1;
