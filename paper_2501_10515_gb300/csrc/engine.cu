@@ -1360,7 +1360,6 @@ void State::reset() {
   iter_low_ = 0;
   best_r_ = 0.0;
   stall_n_ = 0;
-  nrefresh_ = 0;
   fp64_evals_ = 0;
   polish_ = false;
   need_refresh_ = false;
@@ -1427,8 +1426,9 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
     if (lev == 2) ++iter_low_;
     if (lev == 2 && std::isfinite(r_last_)) {
       bool hand = r_last_ <= opt_.polish_tol;
-      if (!hand && r_last_ <= 10.0 * opt_.polish_tol) {
-        // a low-precision phase whose noise floor lies above polish_tol: hand
+      if (!hand && ladder_digits_ && r_last_ <= 10.0 * opt_.polish_tol) {
+        // a state that polishes with FP64-class steps (ladder as digit planes
+        // only) whose low-precision noise floor lies above polish_tol: hand
         // over once max|R| has not halved for 8 steps
         if (best_r_ == 0.0 || r_last_ < 0.5 * best_r_) {
           best_r_ = r_last_;
@@ -1467,27 +1467,11 @@ ascc_status State::iterate(int max_steps, ascc_result* res) {
       done_ = true;
       break;
     }
-    if (lev == 3) {
-      // The corrected residual R3(t) + [R64(t0) - R3(t0)] has a floor: the part
-      // of the 6-product rounding error that changes with t.  When max|R| has
-      // not halved for kStallSteps steps, the correction is taken again at the
-      // current amplitudes; after kMaxRefresh such refreshes (or a long
-      // polishing phase) every further step uses FP64-class residuals.  The
-      // history of corrected residuals is kept (they are FP64-class up to the
-      // drift of the correction).
-      constexpr int kStallSteps = 8, kMaxRefresh = 4;
-      if (refreshed || r_last_ < 0.5 * best_r_) {
-        best_r_ = r_last_;
-        stall_n_ = 0;
-      } else if (++stall_n_ >= kStallSteps) {
-        stall_n_ = 0;
-        best_r_ = r_last_;
-        if (++nrefresh_ > kMaxRefresh)
-          fallback_ = true;
-        else
-          need_refresh_ = true;
-      }
-      if (++polish_its_ >= 30 + opt_.diis_dim) fallback_ = true;
+    if (lev == 3 && ++polish_its_ >= 30 + opt_.diis_dim) {
+      // the corrected iteration stalls (slowly converging states): continue with
+      // FP64-class residuals in every step; the history of corrected residuals
+      // is kept (they are FP64-class up to the drift of the correction)
+      fallback_ = true;
     }
     if (it >= opt_.max_iter) {
       status_ = ASCC_ERR_NOT_CONVERGED;
@@ -1557,8 +1541,7 @@ void State::checkpoint_save(void* buf, int64_t bytes) {
   const int64_t head[kCkptHeader] = {kCkptMagic, 1, o_, v_, n3(), opt_.precision, opt_.linearize,
                                      m, cnt, next_slot_, iter_, iter_low_, fp64_evals_,
                                      polish_its_, flags, (int64_t)status_, hole_, particle_,
-                                     lh_, lp_, (int64_t)(xsign_ < 0), stall_n_, nrefresh_,
-                                     0};
+                                     lh_, lp_, (int64_t)(xsign_ < 0), stall_n_, 0, 0};
   int64_t best_bits;
   std::memcpy(&best_bits, &best_r_, sizeof(best_bits));
   std::memcpy(w, head, sizeof(head));
@@ -1623,7 +1606,6 @@ void State::checkpoint_load(const void* buf, int64_t bytes) {
   fallback_ = (flags >> 5) & 1;
   status_ = (ascc_status)w[15];
   stall_n_ = (int)w[21];
-  nrefresh_ = (int)w[22];
   std::memcpy(&best_r_, &w[23], sizeof(best_r_));
   const auto* d = reinterpret_cast<const double*>(w + kCkptHeader + cnt);
   e_prev_ = d[0];

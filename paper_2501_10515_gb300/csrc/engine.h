@@ -235,10 +235,10 @@ class State {
   // residuals throughout (it stalled); polish_its_ counts its iterations
   bool fallback_ = false;
   int polish_its_ = 0;
-  // stall detection of the corrected polishing iteration: the best max|R|
-  // since the last improvement by half, the steps since, and the refreshes
+  // stall detection of the low-precision phase of a digit-planes-only state:
+  // the best max|R| since its last halving and the steps since
   double best_r_ = 0.0;
-  int stall_n_ = 0, nrefresh_ = 0;
+  int stall_n_ = 0;
   int fp64_evals_ = 0;
   OT corr_;  // FP64-minus-polishing residual correction (mixed precision)
   double tc_min_flops_ = 4e7;  // contractions below this stay FP64 (ASCC_TC_MIN_FLOPS overrides)
