@@ -264,6 +264,16 @@ ascc_status ascc_gemm_split_bf16_tiled(int64_t M, int64_t N, int64_t K, int32_t 
 /* Number of shape classes the tile autotuner has timed in this process. */
 int64_t ascc_autotuned_classes(void);
 
+/* Race check of the T3' program's stream plan (host only, no device call):
+ * builds the plan of a state of size o, v, naux on `nstreams` streams and
+ * returns the number of op pairs of a section whose memory footprints
+ * conflict (a write against a read or write of overlapping workspace, or two
+ * accumulations into R1 or R2) but that neither stream order nor the plan's
+ * event waits order; 0 means race-free.  drop_waits = 1 checks the plan
+ * without its event waits.  Returns -1 on bad arguments. */
+int64_t ascc_t3p_plan_check(int32_t o, int32_t v, int32_t naux, int32_t nstreams,
+                            int32_t drop_waits);
+
 /* FP64-class GEMM on the BF16 tensor cores (the contraction device behind
  * ASCC_FP64_TC and the polishing evaluations of ASCC_MIXED_BF16):
  *   C = alpha * A B^T + beta * C,

@@ -101,6 +101,8 @@ def load():
                                                  C.c_double, vp, vp, C.c_double, vp, vp,
                                                  C.c_int32]),
         "ascc_autotuned_classes": (C.c_int64, []),
+        "ascc_t3p_plan_check": (C.c_int64, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                            C.c_int32]),
         "ascc_gemm_fp64_tc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, vp, vp,
                                         C.c_double, vp, vp]),
         "ascc_gemm_split_bf16_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32,
@@ -152,6 +154,11 @@ def gemm_split_bf16(A, B, out, level, alpha=1.0, beta=0.0, stream=None, tile=Non
     else:
         _check(load().ascc_gemm_split_bf16_tiled(M, N, K, level, alpha, C_void(A), C_void(B),
                                                  beta, C_void(out), st, int(tile)))
+
+
+def t3p_plan_check(o, v, naux, nstreams, drop_waits=False):
+    """Unordered conflicting op pairs of the T3' stream plan (0: race-free); host only."""
+    return int(load().ascc_t3p_plan_check(o, v, naux, nstreams, int(bool(drop_waits))))
 
 
 def autotuned_classes():

@@ -533,6 +533,18 @@ void ascc_destroy(ascc_ctx* ctx) { delete ctx; }
 
 int64_t ascc_autotuned_classes(void) { return tc::autotuned_classes(); }
 
+int64_t ascc_t3p_plan_check(int32_t o, int32_t v, int32_t naux, int32_t nstreams,
+                            int32_t drop_waits) {
+  try {
+    if (o < 2 || v < 2 || naux < 1 || nstreams < 1 || nstreams > 16) return -1;
+    T3pProgram prog(o, v, naux, o - 1, 0, nstreams);
+    return prog.plan_hazards(drop_waits != 0);
+  } catch (const std::exception& e) {
+    record_error(e.what());
+    return -1;
+  }
+}
+
 const char* ascc_status_string(ascc_status s) {
   switch (s) {
     case ASCC_OK: return "ok";

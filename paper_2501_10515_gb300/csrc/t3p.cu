@@ -106,6 +106,73 @@ T3pProgram::T3pProgram(int o, int v, int naux, int h, int p, int nstreams)
 
 int T3pProgram::op_count() const { return kT3pOpCount; }
 
+// Race check of the stream plan, from memory footprints alone (independent
+// of how plan_streams derives its dependencies): two ops of a section
+// conflict when one writes workspace memory the other reads or writes, or
+// both accumulate into R1 or R2 (RA..RD and the temporaries are per stream).
+// Each conflict must be ordered by stream order or by the event waits:
+// vector clocks over the streams record, for every op, the latest op of each
+// stream known to be complete when it starts.
+int64_t T3pProgram::plan_hazards(bool drop_waits) const {
+  const int Q = kT3pOpCount, ns = nstreams_;
+  if (ns <= 1 || op_stream_.empty()) return 0;
+  auto size_of = [&](int t) {
+    int64_t e = 1;
+    for (auto d : shape_[t]) e *= d;
+    return std::max<int64_t>(e, 1);
+  };
+  struct Fp { int64_t b, e; bool w; };
+  std::vector<std::vector<Fp>> fp(Q);
+  std::vector<int> r12(Q, -1);
+  for (int q = 0; q < Q; ++q) {
+    const T3pOp& op = kT3pOps[q];
+    if (op.out >= 0 && offset_[op.out] >= 0)
+      fp[q].push_back({offset_[op.out], offset_[op.out] + size_of(op.out), true});
+    for (int t : {op.a, op.b})
+      if (t >= 0 && offset_[t] >= 0) fp[q].push_back({offset_[t], offset_[t] + size_of(t), false});
+    if ((op.kind == 2 || (op.kind == 4 && op.out < 0)) && (op.base == T3P_R1 || op.base == T3P_R2))
+      r12[q] = op.base;
+  }
+  std::vector<std::vector<int>> vc(Q, std::vector<int>(ns, -1));
+  std::vector<int> last(ns, -1);
+  int section = -1;
+  int64_t hazards = 0;
+  std::vector<int> members;
+  for (int q = 0; q < Q; ++q) {
+    const T3pOp& op = kT3pOps[q];
+    if (op.section != section) {
+      section = op.section;
+      std::fill(last.begin(), last.end(), -1);
+      members.clear();
+    }
+    const int st = op_stream_[q];
+    std::vector<int>& c = vc[q];
+    if (last[st] >= 0) c = vc[last[st]];
+    if (!drop_waits)
+      for (int d : deps_[q])
+        if (kT3pOps[d].section == section)
+          for (int k = 0; k < ns; ++k) c[k] = std::max(c[k], vc[d][k]);
+    c[st] = q;
+    for (int p : members) {
+      const int sp = op_stream_[p];
+      if (sp == st || c[sp] >= p) continue;  // ordered
+      bool clash = r12[p] >= 0 && r12[p] == r12[q];
+      for (const Fp& x : fp[p]) {
+        if (clash) break;
+        for (const Fp& y : fp[q])
+          if ((x.w || y.w) && x.b < y.e && y.b < x.e) {
+            clash = true;
+            break;
+          }
+      }
+      if (clash) ++hazards;
+    }
+    members.push_back(q);
+    last[st] = q;
+  }
+  return hazards;
+}
+
 int t3p_streams() {
   if (const char* env = std::getenv("ASCC_T3P_STREAMS")) {
     const int n = std::atoi(env);

@@ -93,6 +93,10 @@ class T3pProgram {
   void run_streams(T3pStreams& ex, int section, double* const* base, double scale,
                    double* ws) const;
   int nstreams() const { return nstreams_; }
+  // Pairs of ops of a section whose memory footprints conflict but that the
+  // stream plan leaves unordered (0 for a race-free plan); drop_waits checks
+  // the plan without its event waits (a test of the checker itself).
+  int64_t plan_hazards(bool drop_waits = false) const;
   // room of each planner's plane cache during a run
   size_t cache_bytes() const {
     return (size_t)std::min<int64_t>(int64_t(1) << 30, ws_elems_ / 2) / 256 * 256;
