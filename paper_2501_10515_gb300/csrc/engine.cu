@@ -213,6 +213,10 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
       __nv_bfloat16* p = nullptr;
       int32_t* e = nullptr;
     };
+    // BF16 splits are collected (job) and launched together after both operands
+    tc::SplitSpec jobs[2];
+    int njobs = 0;
+    OT keep[2];  // permuted copies that a collected split still reads
     auto planes = [&](const T& X, const std::string& xl, const std::string& ml, int64_t key,
                       int which) {
       const int64_t rows = prod(ml);
@@ -244,27 +248,38 @@ void Einsum::operator()(const char* spec, double alpha, const T& A, const T& B, 
         if (oz_level) r.e = static_cast<int32_t*>(scratch(3 + which, ebytes));
       }
       MatView vx;
+      auto plain = [&](const double* src) {
+        MatView pv;
+        pv.nm = pv.nk = 1;
+        pv.mext[0] = rows;
+        pv.mstr[0] = Ks;
+        pv.kext[0] = Ks;
+        pv.kstr[0] = 1;
+        jobs[njobs++] = tc::SplitSpec{r.p, src, pv, level_};
+      };
       if (xl == ml + Kl) {
         if (oz_level)
           oz::split(s_, r.p, r.e, X.p, rows, Ks, Ks);
         else
-          tc::split_bf16(s_, r.p, X.p, rows, Ks, Ks, level_);
+          plain(X.p);
       } else if (matrix_view(X, xl, ml, Kl, vx)) {
         if (oz_level)
           oz::split_view(s_, r.p, r.e, X.p, vx);
         else
-          tc::split_bf16_view(s_, r.p, X.p, vx, level_);
+          jobs[njobs++] = tc::SplitSpec{r.p, X.p, vx, level_};
       } else {
-        OT Xt(shape_of(ml + Kl), s_);
+        OT& Xt = keep[which];
+        Xt.make(shape_of(ml + Kl), s_);
         perm((xl + "->" + ml + Kl).c_str(), 1.0, X, 0.0, Xt.t);
         if (oz_level)
           oz::split(s_, r.p, r.e, Xt.p(), rows, Ks, Ks);
         else
-          tc::split_bf16(s_, r.p, Xt.p(), rows, Ks, Ks, level_);
+          plain(Xt.p());
       }
       return r;
     };
     const Planes qa = planes(A, sp.a, Ml, key_a, 0), qb = planes(B, sp.b, Nl, key_b, 1);
+    if (njobs > 0) tc::split_bf16_pair(s_, &jobs[0], njobs > 1 ? &jobs[1] : nullptr);
     if (oz_level) {
       // exact digit-plane products (FP64-class)
       auto* ws = static_cast<long long*>(scratch(2, oz::ws_bytes(Ms, Ns)));

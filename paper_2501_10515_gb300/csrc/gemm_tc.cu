@@ -718,6 +718,72 @@ __global__ void __launch_bounds__(256) split_bf16_view_t_kernel(
   }
 }
 
+struct SplitJob {
+  __nv_bfloat16* out;
+  const double* in;
+  MatView v;
+  long long rows, K, Kp, plane_stride;
+  int nsplit, mode, fast, blocks;
+};
+
+// Both operand splits of one product in one launch: blocks [0, j0.blocks) take
+// the first job, the rest the second; each job is a view read in runs of 8
+// (mode 1, which covers plain [rows][K] operands) or in transposing tiles
+// (mode 2).  32-bit index arithmetic (the host checks the sizes).
+__global__ void __launch_bounds__(256) split_pair_kernel(SplitJob j0, SplitJob j1) {
+  __shared__ double tile[kViewTileK][kViewTileM + 1];
+  __shared__ long long roff[kViewTileM], coff[kViewTileK];
+  const bool second = blockIdx.x >= (unsigned)j0.blocks;
+  const SplitJob& j = second ? j1 : j0;
+  const uint32_t bid = second ? blockIdx.x - (unsigned)j0.blocks : blockIdx.x;
+  const uint32_t nb = (uint32_t)j.blocks;
+  if (j.mode == 2) {
+    const long long ntm = (j.rows + kViewTileM - 1) / kViewTileM, ntk = j.Kp / kViewTileK;
+    for (long long tix = bid; tix < ntm * ntk; tix += nb) {
+      const long long m0 = (tix / ntk) * kViewTileM, k0 = (tix % ntk) * kViewTileK;
+      matview_load_tile_t(j.v, j.in, j.rows, j.K, m0, k0, tile, roff, coff);
+      const int mi = threadIdx.x >> 2, kr = (threadIdx.x & 3) * 8;
+      float f[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) f[q] = f64_to_f32_rn(tile[kr + q][mi]);
+      if (m0 + mi < j.rows) {
+        for (int s = 0; s < j.nsplit; ++s) {
+          __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            h[q] = __float2bfloat16_rn(f[q]);
+            f[q] -= __bfloat162float(h[q]);
+          }
+          *reinterpret_cast<uint4*>(j.out + (long long)s * j.plane_stride + (m0 + mi) * j.Kp +
+                                    k0 + kr) = *reinterpret_cast<const uint4*>(h);
+        }
+      }
+      __syncthreads();  // the tile is rewritten by the next pass
+    }
+    return;
+  }
+  const uint32_t runs = (uint32_t)(j.Kp / 8), total = (uint32_t)j.rows * runs;
+  for (uint32_t idx = bid * 256u + threadIdx.x; idx < total; idx += nb * 256u) {
+    const uint32_t rq = idx / runs;
+    const long long r = rq, k0 = (long long)(idx - rq * runs) * 8;
+    double x[8];
+    matview_run8<uint32_t>(j.v, j.in + matview_row<uint32_t>(j.v, rq), k0, j.K, j.fast != 0, x);
+    float f[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) f[q] = f64_to_f32_rn(x[q]);
+    for (int s = 0; s < j.nsplit; ++s) {
+      __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        h[q] = __float2bfloat16_rn(f[q]);
+        f[q] -= __bfloat162float(h[q]);
+      }
+      *reinterpret_cast<uint4*>(j.out + (long long)s * j.plane_stride + r * j.Kp + k0) =
+          *reinterpret_cast<const uint4*>(h);
+    }
+  }
+}
+
 // 3-D map over the planes [level][rows][Kp] (plane stride in elements): one
 // box brings all planes of a 32-wide K tile, 64-byte swizzle.
 CUtensorMap make_planes_map(const __nv_bfloat16* base, int64_t rows, int64_t Kp,
@@ -791,6 +857,53 @@ void split_bf16_view(cudaStream_t s, __nv_bfloat16* out, const double* in, const
                                                         plane_stride, fast);
   count_launch();
   check_launch("split_bf16_view");
+}
+
+void split_bf16_pair(cudaStream_t s, const SplitSpec* a, const SplitSpec* b) {
+  SplitJob job[2];
+  const SplitSpec* spec[2] = {a, b};
+  int n = 0;
+  bool fits = true;
+  for (int q = 0; q < 2; ++q) {
+    if (!spec[q]) continue;
+    const MatView& v = spec[q]->v;
+    ASCC_REQUIRE(v.nm >= 1 && v.nm <= 4 && v.nk >= 1 && v.nk <= 4, "split_bf16_pair: 1..4 dims");
+    SplitJob& j = job[n];
+    j.out = spec[q]->out;
+    j.in = spec[q]->in;
+    j.v = v;
+    j.rows = v.rows();
+    j.K = v.cols();
+    j.Kp = padded_k(j.K);
+    j.plane_stride = j.rows * j.Kp;
+    j.nsplit = spec[q]->nsplit;
+    j.mode = v.kstr[v.nk - 1] != 1 ? 2 : 1;
+    j.fast = v.kext[v.nk - 1] % 8 == 0 ? 1 : 0;
+    if (j.mode == 2) {
+      const int64_t tiles = (j.rows + kViewTileM - 1) / kViewTileM * (j.Kp / kViewTileK);
+      j.blocks = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * 8));
+    } else {
+      const int64_t runs = j.rows * (j.Kp / 8);
+      j.blocks = (int)std::max<int64_t>(1, std::min<int64_t>((runs + 255) / 256, 152 * 16));
+      fits = fits && runs + 256ll * j.blocks < (1ll << 32);
+    }
+    fits = fits && j.rows < (1ll << 31) && j.K < (1ll << 31);
+    if (j.rows * j.Kp > 0) ++n;
+  }
+  if (n == 0) return;
+  if (!fits) {
+    // beyond 32-bit indices: the separate kernels (64-bit paths)
+    for (int q = 0; q < 2; ++q)
+      if (spec[q]) split_bf16_view(s, spec[q]->out, spec[q]->in, spec[q]->v, spec[q]->nsplit);
+    return;
+  }
+  if (n == 1) {
+    job[1] = job[0];
+    job[1].blocks = 0;
+  }
+  split_pair_kernel<<<job[0].blocks + job[1].blocks, 256, 0, s>>>(job[0], job[1]);
+  count_launch();
+  check_launch("split_bf16_pair");
 }
 
 int products_for(int level) { return level == 1 ? 1 : level == 2 ? 3 : 6; }

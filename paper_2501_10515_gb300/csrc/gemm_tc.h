@@ -25,6 +25,18 @@ void split_bf16(cudaStream_t s, __nv_bfloat16* out, const double* in, int64_t ro
 void split_bf16_view(cudaStream_t s, __nv_bfloat16* out, const double* in, const MatView& v,
                      int nsplit, int64_t plane_stride = 0);
 
+// One split for split_bf16_pair: the planes [nsplit][v.rows()][Kp] of `in`
+// read as the matrix v (a plain [rows][K] operand with row stride ld is the
+// view nm = nk = 1, mstr = ld, kstr = 1).
+struct SplitSpec {
+  __nv_bfloat16* out;
+  const double* in;
+  MatView v;
+  int nsplit;
+};
+// Both splits of one product in one launch (either may be null).
+void split_bf16_pair(cudaStream_t s, const SplitSpec* a, const SplitSpec* b);
+
 // C[M][N] (FP64, row stride ldc) = alpha * A B^T + beta * C with A [level][M][Kp] and
 // B [level][N][Kp] BF16 planes from split_bf16 (K-major).  err: device int that
 // receives a nonzero code if a bounded wait inside the kernel gives up.
