@@ -264,6 +264,15 @@ ascc_status ascc_gemm_split_bf16_tiled(int64_t M, int64_t N, int64_t K, int32_t 
 /* Number of shape classes the tile autotuner has timed in this process. */
 int64_t ascc_autotuned_classes(void);
 
+/* Self-test of the bounded device waits that guard every tensor-core kernel:
+ * one thread of a one-block kernel waits, with the kernels' own wait
+ * function but a budget of limit_ms (1..2000) milliseconds, on an mbarrier
+ * phase that nothing completes.  The budget runs out, the kernel records a
+ * code and returns, and the call returns ASCC_ERR_TIMEOUT, the status a
+ * tensor-core GEMM whose wait gave up reports; the context stays usable.
+ * Synchronises `stream` (NULL: the default stream). */
+ascc_status ascc_selftest_bounded_wait(int32_t limit_ms, void* stream);
+
 /* Race check of the T3' program's stream plan (host only, no device call):
  * builds the plan of a state of size o, v, naux on `nstreams` streams and
  * returns the number of op pairs of a section whose memory footprints

@@ -8,9 +8,9 @@ loudly when libascc.so has not been built.
 from .binding import (ASCC_FP64, ASCC_FP64_TC, ASCC_MIXED_BF16, AsccError, Context, Excitation,
                       Server, Options, Profile, Result, TwoAnsatzResult, default_options,
                       gemm_fp64_tc, gemm_split_bf16, gemm_split_bf16_noalloc, load, symbols,
-                      autotuned_classes, t3p_plan_check)
+                      autotuned_classes, t3p_plan_check, selftest_bounded_wait)
 
 __all__ = ["ASCC_FP64", "ASCC_FP64_TC", "ASCC_MIXED_BF16", "AsccError", "Context", "Excitation",
            "Server", "Options", "Profile", "Result", "default_options", "gemm_fp64_tc",
            "gemm_split_bf16", "gemm_split_bf16_noalloc", "load", "symbols", "TwoAnsatzResult",
-           "autotuned_classes", "t3p_plan_check"]
+           "autotuned_classes", "t3p_plan_check", "selftest_bounded_wait"]

@@ -101,6 +101,7 @@ def load():
                                                  C.c_double, vp, vp, C.c_double, vp, vp,
                                                  C.c_int32]),
         "ascc_autotuned_classes": (C.c_int64, []),
+        "ascc_selftest_bounded_wait": (C.c_int, [C.c_int32, vp]),
         "ascc_t3p_plan_check": (C.c_int64, [C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_int32]),
         "ascc_gemm_fp64_tc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, vp, vp,
@@ -154,6 +155,12 @@ def gemm_split_bf16(A, B, out, level, alpha=1.0, beta=0.0, stream=None, tile=Non
     else:
         _check(load().ascc_gemm_split_bf16_tiled(M, N, K, level, alpha, C_void(A), C_void(B),
                                                  beta, C_void(out), st, int(tile)))
+
+
+def selftest_bounded_wait(limit_ms=100, stream=None):
+    """Status of a bounded device wait that cannot complete (ASCC_ERR_TIMEOUT expected)."""
+    return int(load().ascc_selftest_bounded_wait(int(limit_ms),
+                                                C.c_void_p(stream) if stream else None))
 
 
 def t3p_plan_check(o, v, naux, nstreams, drop_waits=False):

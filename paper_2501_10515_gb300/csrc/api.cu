@@ -533,6 +533,16 @@ void ascc_destroy(ascc_ctx* ctx) { delete ctx; }
 
 int64_t ascc_autotuned_classes(void) { return tc::autotuned_classes(); }
 
+ascc_status ascc_selftest_bounded_wait(int32_t limit_ms, void* stream) {
+  return guard([&]() -> ascc_status {
+    ASCC_REQUIRE(limit_ms >= 1 && limit_ms <= 2000, "limit_ms in 1..2000");
+    const int code = tc::wait_selftest((cudaStream_t)stream, limit_ms);
+    if (code != 0)
+      throw Error(ASCC_ERR_TIMEOUT, "bounded wait gave up (code " + std::to_string(code) + ")");
+    return ASCC_OK;
+  });
+}
+
 int64_t ascc_t3p_plan_check(int32_t o, int32_t v, int32_t naux, int32_t nstreams,
                             int32_t drop_waits) {
   try {

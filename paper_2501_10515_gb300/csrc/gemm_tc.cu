@@ -784,6 +784,19 @@ __global__ void __launch_bounds__(256) split_pair_kernel(SplitJob j0, SplitJob j
   }
 }
 
+// Self-test of the bounded wait: one thread waits, with the kernels' wait
+// function and a budget of limit_ns, on the first phase of an mbarrier that
+// nothing arrives at; the budget runs out, the code goes to err, the kernel
+// returns.
+__global__ void wait_selftest_kernel(int* err, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait_ns(b, 0, err, 99, limit_ns);
+}
+
 // 3-D map over the planes [level][rows][Kp] (plane stride in elements): one
 // box brings all planes of a 32-wide K tile, 64-byte swizzle.
 CUtensorMap make_planes_map(const __nv_bfloat16* base, int64_t rows, int64_t Kp,
@@ -904,6 +917,20 @@ void split_bf16_pair(cudaStream_t s, const SplitSpec* a, const SplitSpec* b) {
   split_pair_kernel<<<job[0].blocks + job[1].blocks, 256, 0, s>>>(job[0], job[1]);
   count_launch();
   check_launch("split_bf16_pair");
+}
+
+int wait_selftest(cudaStream_t s, int limit_ms) {
+  int* err = nullptr;
+  ASCC_CUDA(cudaMalloc(&err, sizeof(int)));
+  ASCC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  wait_selftest_kernel<<<1, 32, 0, s>>>(err, (unsigned long long)limit_ms * 1000000ull);
+  count_launch();
+  check_launch("wait_selftest");
+  int h = 0;
+  ASCC_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ASCC_CUDA(cudaStreamSynchronize(s));
+  ASCC_CUDA(cudaFree(err));
+  return h;
 }
 
 int products_for(int level) { return level == 1 ? 1 : level == 2 ? 3 : 6; }

@@ -73,6 +73,10 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
 // below 10^8 flops keep the size rules.  Returns the number of classes tuned.
 int64_t autotuned_classes();
 
+// Runs one bounded wait that cannot complete (see ascc_selftest_bounded_wait)
+// with a budget of limit_ms and returns the code it recorded (0: none).
+int wait_selftest(cudaStream_t s, int limit_ms);
+
 // Number of K chunks the residual engine uses for an M x N x K product.
 // fill: the work items (tiles x chunks) aimed for; fewer chunks leave the SMs
 // to concurrent launches.

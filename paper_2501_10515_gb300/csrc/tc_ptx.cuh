@@ -46,17 +46,24 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; returns false (and records code) when the budget runs out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+// Bounded wait; returns false (and records code) when the budget of limit_ns
+// nanoseconds runs out.
+__device__ __forceinline__ bool mbar_wait_ns(uint32_t bar, uint32_t parity, int* err, int code,
+                                             unsigned long long limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtime();
   while (true) {
     if (mbar_try(bar, parity)) return true;
-    if (gtime() - t0 > WAIT_NS) {
+    if (gtime() - t0 > limit_ns) {
       atomicCAS(err, 0, code);
       return false;
     }
   }
+}
+
+// The kernels' bounded wait (budget WAIT_NS).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  return mbar_wait_ns(bar, parity, err, code, WAIT_NS);
 }
 
 // Instruction descriptor of kind::f16: BF16 x BF16 -> F32, both K-major.

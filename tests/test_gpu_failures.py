@@ -87,3 +87,21 @@ def test_checkpoint_resume_reproduces_the_solve(precision, triples):
     from paper_2501_10515_gb300.binding import AsccError
     with pytest.raises(AsccError):
         other.restore(blob)
+
+
+def test_bounded_wait_times_out_and_the_context_survives():
+    """A bounded device wait on an mbarrier phase that nothing completes (the
+    kernels' own wait function, 100 ms budget) gives up, the call reports
+    ASCC_ERR_TIMEOUT, and the next tensor-core product on the same context
+    runs normally."""
+    import torch
+    import paper_2501_10515_gb300 as pkg
+    st = pkg.selftest_bounded_wait(100)
+    assert st == 6, st  # ASCC_ERR_TIMEOUT
+    A = torch.randn(300, 200, device="cuda", dtype=torch.float64)
+    B = torch.randn(250, 200, device="cuda", dtype=torch.float64)
+    C = torch.empty(300, 250, device="cuda", dtype=torch.float64)
+    pkg.gemm_split_bf16(A, B, C, 3)
+    torch.cuda.synchronize()
+    ref = A @ B.T
+    assert (C - ref).abs().max().item() < 1e-4 * ref.abs().max().item()
