@@ -108,6 +108,8 @@ def test_residual_with_triples_mid_size(precision):
     ("c1_plascc_excited_t3", 1, 1e-6),
     ("mid_plascc_excited_t3", 2, E_TOL),
     ("mid_plascc_excited_t3", 1, 1e-6),
+    ("c2_plascc_excited_t3", 2, E_TOL),
+    ("c2_plascc_excited_t3", 1, 1e-6),
 ])
 def test_solve_with_triples_matches_stored_oracle_energy(name, precision, tol):
     """Converged ASCCSD / PLASCCSD energies with T3' against the oracle's
