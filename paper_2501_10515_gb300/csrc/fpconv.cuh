@@ -84,10 +84,12 @@ __device__ __forceinline__ double f32_to_f64_pow2(float x, const Pow2& p, double
 // How an epilogue writes alpha * acc (+ beta * C), decided once per kernel so
 // that no per-element select evaluates an FP64 operation it does not need:
 // beta = 0 with a power-of-two alpha (integer arithmetic only), beta = 0 with
-// another alpha (one FP64 product), beta != 0 (FP64 fma).
-enum StoreMode { kStorePow2 = 1, kStoreScaled = 2, kStoreBeta = 3 };
+// another alpha (one FP64 product), beta = 1 (one FP64 fma: beta * C = C),
+// other beta (FP64 fma of alpha acc and beta C).
+enum StoreMode { kStorePow2 = 1, kStoreScaled = 2, kStoreBeta = 3, kStoreBeta1 = 4 };
 
 inline int host_store_mode(double alpha, double beta) {
+  if (beta == 1.0) return kStoreBeta1;
   if (beta != 0.0) return kStoreBeta;
   uint64_t u;
   __builtin_memcpy(&u, &alpha, sizeof(u));

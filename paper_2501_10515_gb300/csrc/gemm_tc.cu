@@ -206,25 +206,32 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
           C[row * ldc + col] = alpha * f32_to_f64(a);
         });
     } else {
+      const bool beta1 = beta == 1.0;  // kernel-uniform: beta * old = old
       // C = alpha * tile + beta * C: the old values of RB rows are loaded
       // before the first store, so that each thread has RB loads in flight
       // instead of one round trip to memory per row
       constexpr int RB = 16;
-      for (int r0 = 0; r0 < rows; r0 += RB) {
-        for (int c = threadIdx.x; c < cols; c += NTHREADS) {
-          double old[RB];
+      auto rmw = [&](auto combine) {
+        for (int r0 = 0; r0 < rows; r0 += RB) {
+          for (int c = threadIdx.x; c < cols; c += NTHREADS) {
+            double old[RB];
 #pragma unroll
-          for (int u = 0; u < RB; ++u)
-            old[u] = (r0 + u < rows) ? C[(long long)(m0 + r0 + u) * ldc + n0 + c] : 0.0;
+            for (int u = 0; u < RB; ++u)
+              old[u] = (r0 + u < rows) ? C[(long long)(m0 + r0 + u) * ldc + n0 + c] : 0.0;
 #pragma unroll
-          for (int u = 0; u < RB; ++u) {
-            if (r0 + u < rows) {
-              const float a = total > 0 ? tile[(r0 + u) * PITCH + c] : 0.f;
-              C[(long long)(m0 + r0 + u) * ldc + n0 + c] = fma(alpha, (double)a, beta * old[u]);
+            for (int u = 0; u < RB; ++u) {
+              if (r0 + u < rows) {
+                const float a = total > 0 ? tile[(r0 + u) * PITCH + c] : 0.f;
+                C[(long long)(m0 + r0 + u) * ldc + n0 + c] = combine(a, old[u]);
+              }
             }
           }
         }
-      }
+      };
+      if (beta1)
+        rmw([&](float a, double o) { return fma(alpha, f32_to_f64(a), o); });
+      else
+        rmw([&](float a, double o) { return fma(alpha, (double)a, beta * o); });
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -395,7 +402,11 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
     const int lrow = warp * 32 + lane;
     const int t = threadIdx.x;  // 0..127
     const Pow2 p2 = pow2_of(alpha);
-    const int smode = ws ? 0 : beta != 0.0 ? kStoreBeta : p2.ok ? kStorePow2 : kStoreScaled;
+    const int smode = ws            ? 0
+                      : beta == 1.0 ? kStoreBeta1
+                      : beta != 0.0 ? kStoreBeta
+                      : p2.ok       ? kStorePow2
+                                    : kStoreScaled;
     int tc = 0;
     for (int w = blockIdx.x; w < items; w += gridDim.x, ++tc) {
       int m0, n0, kt0, nkt;
@@ -491,6 +502,11 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
         });
       else if (smode == kStoreScaled)
         tile_loop([&](float a, long long r, long long c) { C[at(r, c)] = alpha * f32_to_f64(a); });
+      else if (smode == kStoreBeta1)
+        tile_loop([&](float a, long long r, long long c) {
+          const long long o = at(r, c);
+          C[o] = fma(alpha, f32_to_f64(a), C[o]);
+        });
       else
         tile_loop([&](float a, long long r, long long c) {
           const long long o = at(r, c);
@@ -529,6 +545,7 @@ __device__ __forceinline__ double reduce_out(float hi, float lo, const Pow2& p2,
   }
   const double acc = f32_to_f64(hi) + f32_to_f64(lo);
   if (MODE == kStoreScaled) return alpha * acc;
+  if (MODE == kStoreBeta1) return fma(alpha, acc, *c);
   return fma(alpha, acc, beta * *c);
 }
 
@@ -1162,6 +1179,8 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
       ASCC_RV(kStorePow2);
     else if (mode == kStoreScaled)
       ASCC_RV(kStoreScaled);
+    else if (mode == kStoreBeta1)
+      ASCC_RV(kStoreBeta1);
     else
       ASCC_RV(kStoreBeta);
 #undef ASCC_RV
@@ -1179,6 +1198,8 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
         ASCC_R4(kStorePow2);
       else if (mode == kStoreScaled)
         ASCC_R4(kStoreScaled);
+      else if (mode == kStoreBeta1)
+        ASCC_R4(kStoreBeta1);
       else
         ASCC_R4(kStoreBeta);
 #undef ASCC_R4
@@ -1192,6 +1213,8 @@ void gemm_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, int level, doub
         ASCC_R1(kStorePow2);
       else if (mode == kStoreScaled)
         ASCC_R1(kStoreScaled);
+      else if (mode == kStoreBeta1)
+        ASCC_R1(kStoreBeta1);
       else
         ASCC_R1(kStoreBeta);
 #undef ASCC_R1
