@@ -273,15 +273,18 @@ int64_t ascc_autotuned_classes(void);
  * Synchronises `stream` (NULL: the default stream). */
 ascc_status ascc_selftest_bounded_wait(int32_t limit_ms, void* stream);
 
-/* Race check of the T3' program's stream plan (host only, no device call):
- * builds the plan of a state of size o, v, naux on `nstreams` streams and
+/* Race and placement check of the T3' program (host only, no device call):
+ * builds the program of a state of size o, v, naux on `nstreams` streams and
  * returns the number of op pairs of a section whose memory footprints
  * conflict (a write against a read or write of overlapping workspace, or two
  * accumulations into R1 or R2) but that neither stream order nor the plan's
- * event waits order; 0 means race-free.  drop_waits = 1 checks the plan
- * without its event waits.  Returns -1 on bad arguments. */
+ * event waits order, plus the number of intermediate pairs that share
+ * workspace while both are live; 0 means race-free and correctly placed.
+ * mode 0: the plan as built; 1: without its event waits; 2: with every
+ * intermediate placed at offset 0 (modes 1 and 2 test the checks themselves).
+ * Returns -1 on bad arguments. */
 int64_t ascc_t3p_plan_check(int32_t o, int32_t v, int32_t naux, int32_t nstreams,
-                            int32_t drop_waits);
+                            int32_t mode);
 
 /* FP64-class GEMM on the BF16 tensor cores (the contraction device behind
  * ASCC_FP64_TC and the polishing evaluations of ASCC_MIXED_BF16):

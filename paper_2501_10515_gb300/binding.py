@@ -163,9 +163,11 @@ def selftest_bounded_wait(limit_ms=100, stream=None):
                                                 C.c_void_p(stream) if stream else None))
 
 
-def t3p_plan_check(o, v, naux, nstreams, drop_waits=False):
-    """Unordered conflicting op pairs of the T3' stream plan (0: race-free); host only."""
-    return int(load().ascc_t3p_plan_check(o, v, naux, nstreams, int(bool(drop_waits))))
+def t3p_plan_check(o, v, naux, nstreams, mode=0):
+    """Unordered conflicting op pairs of the T3' stream plan plus intermediates that
+    share workspace while live (0: race-free and correctly placed); host only.
+    mode 1 drops the plan's event waits, mode 2 places every intermediate at 0."""
+    return int(load().ascc_t3p_plan_check(o, v, naux, nstreams, int(mode)))
 
 
 def autotuned_classes():

@@ -544,11 +544,12 @@ ascc_status ascc_selftest_bounded_wait(int32_t limit_ms, void* stream) {
 }
 
 int64_t ascc_t3p_plan_check(int32_t o, int32_t v, int32_t naux, int32_t nstreams,
-                            int32_t drop_waits) {
+                            int32_t mode) {
   try {
-    if (o < 2 || v < 2 || naux < 1 || nstreams < 1 || nstreams > 16) return -1;
+    if (o < 2 || v < 2 || naux < 1 || nstreams < 1 || nstreams > 16 || mode < 0 || mode > 2)
+      return -1;
     T3pProgram prog(o, v, naux, o - 1, 0, nstreams);
-    return prog.plan_hazards(drop_waits != 0);
+    return prog.plan_hazards(mode == 1) + prog.placement_clobbers(mode == 2);
   } catch (const std::exception& e) {
     record_error(e.what());
     return -1;

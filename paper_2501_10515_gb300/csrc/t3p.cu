@@ -113,6 +113,65 @@ int T3pProgram::op_count() const { return kT3pOpCount; }
 // Each conflict must be ordered by stream order or by the event waits:
 // vector clocks over the streams record, for every op, the latest op of each
 // stream known to be complete when it starts.
+// Placement check, from the op table alone (independent of the constructor's
+// liveness): the sections run as pro, lin, quad, quad (the second run for
+// PLASCC), mix; a tensor is live from a write to its last read before its next
+// write (writes with no read between them, the rows of a stack, extend one
+// interval); two tensors whose workspace ranges overlap must never be live at
+// once.  collapse: every tensor placed at offset 0 (a test of the check).
+int64_t T3pProgram::placement_clobbers(bool collapse) const {
+  const int T = kT3pTensorCount;
+  std::vector<int> seq;
+  for (int sec : {T3P_PRO, T3P_LIN, T3P_QUAD, T3P_QUAD, T3P_MIX})
+    for (int q = 0; q < kT3pOpCount; ++q)
+      if (kT3pOps[q].section == sec) seq.push_back(q);
+  struct Iv { int b, e; };
+  std::vector<std::vector<Iv>> iv(T);
+  std::vector<bool> read_since(T, true);
+  for (int pos = 0; pos < (int)seq.size(); ++pos) {
+    const T3pOp& op = kT3pOps[seq[pos]];
+    for (int t : {op.a, op.b})
+      if (t >= 0 && offset_[t] >= 0 && !iv[t].empty()) {
+        iv[t].back().e = pos;
+        read_since[t] = true;
+      }
+    if (op.out >= 0 && offset_[op.out] >= 0) {
+      const int t = op.out;
+      if (iv[t].empty() || read_since[t])
+        iv[t].push_back({pos, pos});
+      else
+        iv[t].back().e = pos;
+      read_since[t] = false;
+    }
+  }
+  auto size_of = [&](int t) {
+    int64_t e = 1;
+    for (auto d : shape_[t]) e *= d;
+    return std::max<int64_t>(e, 1);
+  };
+  int64_t clobbers = 0;
+  for (int x = 0; x < T; ++x) {
+    if (offset_[x] < 0 || iv[x].empty()) continue;
+    const int64_t xb = collapse ? 0 : offset_[x], xe = xb + size_of(x);
+    for (int y = x + 1; y < T; ++y) {
+      if (offset_[y] < 0 || iv[y].empty()) continue;
+      const int64_t yb = collapse ? 0 : offset_[y], ye = yb + size_of(y);
+      if (!(xb < ye && yb < xe)) continue;
+      bool clash = false;
+      for (const Iv& a : iv[x]) {
+        for (const Iv& b : iv[y])
+          if (a.b <= b.e && b.b <= a.e) {
+            clash = true;
+            break;
+          }
+        if (clash) break;
+      }
+      if (clash) ++clobbers;
+    }
+  }
+  return clobbers;
+}
+
 int64_t T3pProgram::plan_hazards(bool drop_waits) const {
   const int Q = kT3pOpCount, ns = nstreams_;
   if (ns <= 1 || op_stream_.empty()) return 0;

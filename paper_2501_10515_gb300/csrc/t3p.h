@@ -97,6 +97,10 @@ class T3pProgram {
   // stream plan leaves unordered (0 for a race-free plan); drop_waits checks
   // the plan without its event waits (a test of the checker itself).
   int64_t plan_hazards(bool drop_waits = false) const;
+  // Pairs of intermediates whose workspace ranges overlap while both are live
+  // (0 for a correct placement); collapse places every tensor at offset 0
+  // (a test of the check itself).
+  int64_t placement_clobbers(bool collapse = false) const;
   // room of each planner's plane cache during a run
   size_t cache_bytes() const {
     return (size_t)std::min<int64_t>(int64_t(1) << 30, ws_elems_ / 2) / 256 * 256;
