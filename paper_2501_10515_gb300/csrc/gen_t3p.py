@@ -54,6 +54,17 @@ Steps:
     sum_P B[P][.][.] B[P][.][.].  Each term is contracted pairwise in the
     order of fewest flops (sizes o = 20, v = 200, naux = 660), and equal
     intermediates are computed once.
+ 6. Contractions of a section that share a large operand (>= 10^6
+    elements) with the same indices contracted are stacked into one product:
+    their other operands are copied into the rows of a stack S (member by
+    member), W = X . S^T is one GEMM, and each member's result is copied out
+    of its columns of W (stacks capped at 6.4 10^7 elements of W).  The ops
+    are re-ordered so that each stack's members are ready when it is formed.
+ 7. The op table (tensors with their kind, base operand, selector and
+    dimensions; ops with section, kind, operands, einsum labels, weight and
+    output selector) is written for the C++ executor (t3p.cu), which places
+    the intermediates in one workspace by lifetime, plans the streams and
+    runs each section with its t2 binding.
 """
 from __future__ import annotations
 
