@@ -343,7 +343,11 @@ ascc_status ascc_gemm_split_bf16_noalloc(int64_t M, int64_t N, int64_t K,
  * integrals once, solve its states (ground state first if listed; a ground
  * state takes the primary pair of the request's first excitation for PLASCC)
  * and free the memory, so requests that arrive while others run are admitted
- * as memory frees up and their work overlaps on the device.  Times are seconds since creation. */
+ * as memory frees up and their work overlaps on the device.  With
+ * ASCC_MIXED_BF16, a state whose mixed solve ends ASCC_ERR_NOT_CONVERGED is
+ * solved again on the FP64-class path (ASCC_FP64_TC) from the initial guess;
+ * its result then carries that solve's status and energy and the iterations
+ * of both.  Times are seconds since creation. */
 typedef struct ascc_server ascc_server;
 typedef struct {
   int64_t request_id;

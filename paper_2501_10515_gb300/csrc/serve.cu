@@ -135,9 +135,24 @@ struct ascc_server {
             xsign = e.ansatz == 1 ? -1.0 : 1.0;
             if (beta == 0.0) beta = e.ansatz == 1 ? 1.0 / (1.0 - e.alpha) : 1.0 / (1.0 + e.alpha);
           }
-          ascc::State st(mol, hole, particle, beta, o, s, xsign);
           ascc_result res{};
-          st.solve(&res);
+          {
+            ascc::State st(mol, hole, particle, beta, o, s, xsign);
+            st.solve(&res);
+          }
+          if (o.precision == ASCC_MIXED_BF16 && res.status == ASCC_ERR_NOT_CONVERGED) {
+            // a mixed solve that did not converge is solved again on the
+            // FP64-class path (the molecule holds its digit planes), so that a
+            // state the FP64-class iteration converges is not lost to the
+            // low-precision phase; the result counts both solves' iterations
+            ascc::Options o2 = o;
+            o2.precision = ASCC_FP64_TC;
+            ascc_result res2{};
+            ascc::State st2(mol, hole, particle, beta, o2, s, xsign);
+            st2.solve(&res2);
+            res2.iterations += res.iterations;
+            res = res2;
+          }
           ascc_serve_result sr{};
           sr.request_id = r.id;
           sr.state_index = (int32_t)k;
