@@ -73,3 +73,31 @@ def test_admission_respects_the_memory_budget():
         running = [rid for rid, (a, b) in spans.items() if a <= t < b]
         if len(running) > 1:
             assert sum(fps[rid] for rid in running) <= budget
+
+
+def test_mixed_state_that_does_not_converge_is_solved_again_fp64_class():
+    """With an iteration cap too small for any state, a mixed solve ends
+    NOT_CONVERGED and the server solves the state again on the FP64-class
+    path: the result carries the iterations of both solves (each one the
+    FP64-class context's count alone with the same cap)."""
+    import paper_2501_10515_gb300 as pkg
+    o, v = 4, 20
+    s = synth.make_system(o, v, seed=0)
+    cap = 3
+    ref = pkg.Context(o, v, s.naux, s.eps, s.B, hole=3, particle=0, precision=pkg.ASCC_FP64_TC,
+                      max_iter=cap)
+    r_tc = ref.solve()
+    ref.close()
+    mix = pkg.Context(o, v, s.naux, s.eps, s.B, hole=3, particle=0,
+                      precision=pkg.ASCC_MIXED_BF16, max_iter=cap)
+    r_mx = mix.solve()
+    mix.close()
+    assert r_tc.status == 4 and r_mx.status == 4
+    srv = pkg.Server(8 << 30, max_active=1, precision=pkg.ASCC_MIXED_BF16, max_iter=cap)
+    srv.submit(o, v, s.naux, s.eps, s.B, [(3, 0)])
+    srv.drain()
+    res = srv.results()
+    srv.close()
+    assert len(res) == 1 and res[0]["status"] == 4
+    assert res[0]["iterations"] == r_mx.iterations + r_tc.iterations
+    assert abs(res[0]["energy"] - r_tc.energy) < 1e-12
