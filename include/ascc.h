@@ -322,7 +322,7 @@ ascc_status ascc_gemm_fp64_tc(int64_t M, int64_t N, int64_t K, double alpha,
  *   ascc_gemm_split_bf16 chooses it) must not exceed 32 MiB; larger requests
  *   return ASCC_ERR_INVALID without touching the GPU.
  *   The first call on a device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   that device current).
  *   Each call ends by reading its device timeout flag back to the host, so
  *   it synchronises `stream` before returning; a bounded wait that gave up
  *   returns ASCC_ERR_TIMEOUT.
