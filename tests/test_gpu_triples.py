@@ -17,6 +17,13 @@ pytestmark = pytest.mark.gpu
 
 REL_TOL = 1e-9
 E_TOL = 1e-10
+# Both solves stop at max|R| <= 1e-8 and |dE| <= 1e-10 (the stopping rule of
+# Sec. III.A, tightened), not a bound on the distance to the fixed point.  At o=20, v=200 with
+# T3' the energy left at that residual is about 1e-10 Eh: two FP64-class GPU
+# solves of this state that differ only in DIIS depth (16 and 32) stop
+# 1.1e-10 Eh apart.  Two trajectories (oracle and GPU) are therefore compared
+# at ten times that.
+C2_T3_E_TOL = 1e-9
 
 
 def _ctx(s, hole, part, **kw):
@@ -108,13 +115,14 @@ def test_residual_with_triples_mid_size(precision):
     ("c1_plascc_excited_t3", 1, 1e-6),
     ("mid_plascc_excited_t3", 2, E_TOL),
     ("mid_plascc_excited_t3", 1, 1e-6),
-    ("c2_plascc_excited_t3", 2, E_TOL),
+    ("c2_plascc_excited_t3", 2, C2_T3_E_TOL),
     ("c2_plascc_excited_t3", 1, 1e-6),
 ])
 def test_solve_with_triples_matches_stored_oracle_energy(name, precision, tol):
     """Converged ASCCSD / PLASCCSD energies with T3' against the oracle's
     (tests/golden/make_reference_energies.py); FP64 and FP64-class paths at
-    1e-10 Eh, mixed precision at 1e-6 Eh."""
+    1e-10 Eh (1e-9 Eh at o=20, v=200, see C2_T3_E_TOL), mixed precision at
+    1e-6 Eh."""
     o, v, seed, hole, part, method, e_ref = _golden(name)
     s = synth.make_system(o, v, seed=seed)
     ctx = _ctx(s, hole, part, linearize=int(method.startswith("PL")), precision=precision,
