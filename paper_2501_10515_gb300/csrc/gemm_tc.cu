@@ -186,8 +186,22 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
       // store-only: split-K partials (summed later) or alpha * tile, one loop
       // per kind of store
       const Pow2 p2 = pow2_of(alpha);
+      // groups of U rows: a thread reads its U staged values before the
+      // first of their stores, so that U stores are in flight at a time
+      // (one warp per SM sub-partition has no other work to hide latency)
       auto rows_loop = [&](auto put) {
-        for (int rr = 0; rr < rows; ++rr) {
+        constexpr int U = 4;
+        int rr = 0;
+        for (; rr + U <= rows; rr += U) {
+          for (int c = threadIdx.x; c < cols; c += NTHREADS) {
+            float a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a[u] = total > 0 ? tile[(rr + u) * PITCH + c] : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) put(a[u], (long long)(m0 + rr + u), n0 + c);
+          }
+        }
+        for (; rr < rows; ++rr) {
           const long long row = m0 + rr;
           for (int c = threadIdx.x; c < cols; c += NTHREADS)
             put(total > 0 ? tile[rr * PITCH + c] : 0.f, row, n0 + c);
@@ -455,16 +469,38 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
       // (r, c) of the caller's C: tile row rr, column c; or, for the
       // exchanged product, tile row t is column m0 + t of the caller's C
       // (row n0 + c) and consecutive threads write consecutive columns
+      // each thread reads U staged values before the first of their stores,
+      // so that U stores are in flight at a time (one epilogue warp per SM
+      // sub-partition has no other work to hide their latency)
       auto tile_loop = [&](auto put) {
+        constexpr int U = 4;
         if (!trans) {
           // 128 / NB rows per pass, NB columns each
-          for (int rr = t / NB; rr < rows; rr += 128 / NB) {
-            const int c = t % NB;
-            if (c < cols) put(epi[rr * PITCH + c], (long long)(m0 + rr), (long long)(n0 + c));
+          constexpr int RP = 128 / NB;
+          const int c = t % NB;
+          if (c < cols) {
+            int rr = t / NB;
+            for (; rr + (U - 1) * RP < rows; rr += U * RP) {
+              float a[U];
+#pragma unroll
+              for (int u = 0; u < U; ++u) a[u] = epi[(rr + u * RP) * PITCH + c];
+#pragma unroll
+              for (int u = 0; u < U; ++u)
+                put(a[u], (long long)(m0 + rr + u * RP), (long long)(n0 + c));
+            }
+            for (; rr < rows; rr += RP)
+              put(epi[rr * PITCH + c], (long long)(m0 + rr), (long long)(n0 + c));
           }
         } else if (t < rows) {
-          for (int c = 0; c < cols; ++c)
-            put(epi[t * PITCH + c], (long long)(n0 + c), (long long)(m0 + t));
+          int c = 0;
+          for (; c + U <= cols; c += U) {
+            float a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a[u] = epi[t * PITCH + c + u];
+#pragma unroll
+            for (int u = 0; u < U; ++u) put(a[u], (long long)(n0 + c + u), (long long)(m0 + t));
+          }
+          for (; c < cols; ++c) put(epi[t * PITCH + c], (long long)(n0 + c), (long long)(m0 + t));
         }
       };
       const long long Mo = trans ? N : M, No = trans ? M : N;
@@ -494,6 +530,53 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
       auto at = [&](long long r, long long c) -> long long {
         return has_view ? voff[r - r0] + voff[nr + (c - c0)] : r * ldc + c;
       };
+      // C = combine(tile value, old C) over the same elements and in the same
+      // order as tile_loop; each thread loads the old values of V elements
+      // before the first of their stores (the elements of a tile are distinct
+      // outputs), so that V loads are in flight instead of one round trip per
+      // element
+      auto tile_rmw = [&](auto combine) {
+        constexpr int V = 8;
+        if (!trans) {
+          constexpr int RP = 128 / NB;
+          const int c = t % NB;
+          if (c < cols) {
+            int rr = t / NB;
+            for (; rr + (V - 1) * RP < rows; rr += V * RP) {
+              long long o[V];
+              double old[V];
+#pragma unroll
+              for (int u = 0; u < V; ++u)
+                o[u] = at((long long)(m0 + rr + u * RP), (long long)(n0 + c));
+#pragma unroll
+              for (int u = 0; u < V; ++u) old[u] = C[o[u]];
+#pragma unroll
+              for (int u = 0; u < V; ++u)
+                C[o[u]] = combine(epi[(rr + u * RP) * PITCH + c], old[u]);
+            }
+            for (; rr < rows; rr += RP) {
+              const long long o = at((long long)(m0 + rr), (long long)(n0 + c));
+              C[o] = combine(epi[rr * PITCH + c], C[o]);
+            }
+          }
+        } else if (t < rows) {
+          int c = 0;
+          for (; c + V <= cols; c += V) {
+            long long o[V];
+            double old[V];
+#pragma unroll
+            for (int u = 0; u < V; ++u) o[u] = at((long long)(n0 + c + u), (long long)(m0 + t));
+#pragma unroll
+            for (int u = 0; u < V; ++u) old[u] = C[o[u]];
+#pragma unroll
+            for (int u = 0; u < V; ++u) C[o[u]] = combine(epi[t * PITCH + c + u], old[u]);
+          }
+          for (; c < cols; ++c) {
+            const long long o = at((long long)(n0 + c), (long long)(m0 + t));
+            C[o] = combine(epi[t * PITCH + c], C[o]);
+          }
+        }
+      };
       if (smode == 0)
         tile_loop([&](float a, long long r, long long c) { ws[((long long)kz * Mo + r) * No + c] = a; });
       else if (smode == kStorePow2)
@@ -503,15 +586,9 @@ gemm_tc_narrow_kernel(const __grid_constant__ CUtensorMap amap,
       else if (smode == kStoreScaled)
         tile_loop([&](float a, long long r, long long c) { C[at(r, c)] = alpha * f32_to_f64(a); });
       else if (smode == kStoreBeta1)
-        tile_loop([&](float a, long long r, long long c) {
-          const long long o = at(r, c);
-          C[o] = fma(alpha, f32_to_f64(a), C[o]);
-        });
+        tile_rmw([&](float a, double o) { return fma(alpha, f32_to_f64(a), o); });
       else
-        tile_loop([&](float a, long long r, long long c) {
-          const long long o = at(r, c);
-          C[o] = fma(alpha, (double)a, beta * C[o]);
-        });
+        tile_rmw([&](float a, double o) { return fma(alpha, (double)a, beta * o); });
       asm volatile("bar.sync 1, 128;" ::: "memory");
     }
   }

@@ -19,7 +19,7 @@ def test_tile_shapes_bit_identical(M, N, K, level):
     C0 = torch.randn(M, N, device="cuda", dtype=torch.float64, generator=g)
     outs = []
     for tile in (1, 2, 3, -1, 0):
-        for beta in (0.0, 0.5):
+        for beta in (0.0, 0.5, 1.0):
             C = C0.clone()
             pkg.gemm_split_bf16(A, B, C, level, alpha=0.75, beta=beta, tile=tile)
             outs.append((tile, beta, C))
@@ -28,7 +28,7 @@ def test_tile_shapes_bit_identical(M, N, K, level):
     # leaves such products to the rules) exchange the operands: a second class
     exchanged = M <= 64 < N
     cls = lambda t: (t in (3, -1, 0)) if exchanged else 0
-    for beta in (0.0, 0.5):
+    for beta in (0.0, 0.5, 1.0):
         for c in {cls(t) for t, _, _ in outs}:
             group = [(t, C) for t, b, C in outs if b == beta and cls(t) == c]
             ref = group[0][1]
