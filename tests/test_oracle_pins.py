@@ -70,6 +70,96 @@ def test_spin_relations_signs():
     assert np.allclose(ss, -ss.transpose(0, 1, 2, 4, 3, 5))
 
 
+def _det_apply(ops, det):
+    """Applies a string of creation (True, q) / annihilation (False, q)
+    operators, rightmost first, to the determinant bit mask det (spin orbital
+    q = 2 p + spin, alpha = 0); returns (sign, det), sign 0 if it vanishes."""
+    sign = 1
+    for dag, q in reversed(ops):
+        bit = 1 << q
+        if dag == ((det & bit) != 0):
+            return 0, 0
+        if bin(det & (bit - 1)).count("1") & 1:
+            sign = -sign
+        det ^= bit
+    return sign, det
+
+
+def _singlet_amplitudes(o, v, rank, seed):
+    """T|phi0> for T = sum s[i..,a..] E_ai E_bj (E_ck), E_ai = sum_spin
+    a+_{a spin} a_{i spin} the spin-free excitation generators: T|phi0> is a
+    singlet whatever s is.  Returns a function giving the coefficient of the
+    determinant that an operator string makes from phi0, in the phase of
+    that string."""
+    import itertools
+    so = lambda p, sp: 2 * p + sp
+    phi0 = sum(1 << so(i, sp) for i in range(o) for sp in (0, 1))
+    s = np.random.default_rng(seed).standard_normal((o,) * rank + (v,) * rank)
+    wf = {}
+    for idx in itertools.product(*([range(o)] * rank + [range(v)] * rank)):
+        dets = {phi0: 1.0}
+        for a, i in zip(idx[rank:], idx[:rank]):
+            new = {}
+            for d, c in dets.items():
+                for sp in (0, 1):
+                    sg, d2 = _det_apply([(True, so(o + a, sp)), (False, so(i, sp))], d)
+                    if sg:
+                        new[d2] = new.get(d2, 0.0) + sg * c
+            dets = new
+        for d, c in dets.items():
+            wf[d] = wf.get(d, 0.0) + s[idx] * c
+
+    def coef(occ, vir):
+        # occ, vir: (spatial index, spin) in the order of
+        # a+_vir[0] a+_vir[1] ... a_occ[-1] ... a_occ[0]
+        ops = [(True, so(o + a, sp)) for a, sp in vir] + [(False, so(i, sp)) for i, sp in occ[::-1]]
+        sg, d = _det_apply(ops, phi0)
+        return sg * wf.get(d, 0.0) if sg else 0.0
+    return coef
+
+
+def test_same_spin_relations_hold_for_a_spin_free_singlet():
+    """Eqs. S1 and S2 against determinant algebra: the same-spin doubles and
+    triples of a singlet built from spin-free generators equal the relations
+    applied to its alpha-beta / alpha-beta-beta amplitudes (amplitude = the
+    coefficient of a+_a a+_b (a+_c) ... a_j a_i phi0, as T is written).  A sign
+    or index slip in either relation fails this (checked below by planting
+    one)."""
+    import itertools
+    o, v = 3, 4
+    coef = _singlet_amplitudes(o, v, 2, seed=11)
+    t2 = np.zeros((o, o, v, v))
+    for i, j, a, b in itertools.product(range(o), range(o), range(v), range(v)):
+        t2[i, j, a, b] = coef([(i, 0), (j, 1)], [(a, 0), (b, 1)])
+    assert np.abs(t2 - t2.transpose(1, 0, 3, 2)).max() < 1e-14   # singlet pair symmetry
+    ss2 = amp.t2_same_spin(t2)
+    n = 0
+    for i, j, a, b in itertools.product(range(o), range(o), range(v), range(v)):
+        if i < j and a < b:
+            assert ss2[i, j, a, b] == pytest.approx(coef([(i, 0), (j, 0)], [(a, 0), (b, 0)]),
+                                                    abs=1e-13)
+            n += 1
+    assert n == 18
+
+    o, v = 4, 4
+    coef = _singlet_amplitudes(o, v, 3, seed=12)
+    t3 = np.zeros((o, o, o, v, v, v))
+    for i, j, k, a, b, c in itertools.product(*([range(o)] * 3 + [range(v)] * 3)):
+        t3[i, j, k, a, b, c] = coef([(i, 0), (j, 1), (k, 1)], [(a, 0), (b, 1), (c, 1)])
+    want = {}
+    for i, j, k, a, b, c in itertools.product(*([range(o)] * 3 + [range(v)] * 3)):
+        if i < j < k and a < b < c:
+            want[i, j, k, a, b, c] = coef([(i, 0), (j, 0), (k, 0)], [(a, 0), (b, 0), (c, 0)])
+    assert len(want) == 16 and max(abs(x) for x in want.values()) > 0.1
+    ss3 = amp.t3_same_spin(t3)
+    for key, w in want.items():
+        assert ss3[key] == pytest.approx(w, abs=1e-12)
+    # a planted sign slip in the middle term fails the comparison
+    s_ = t3.transpose(1, 2, 0, 3, 4, 5)
+    wrong = s_.transpose(0, 1, 2, 4, 5, 3) + s_.transpose(0, 1, 2, 4, 3, 5) + s_
+    assert max(abs(wrong[key] - w) for key, w in want.items()) > 1e-3
+
+
 # ------------------------------------------------------------ H-bar closed forms
 def test_reference_energy_of_hbar_closed_form():
     """<phi0|H-bar|phi0> = E_HF + 1/2 (ph|ph) (Brillouin: f_hp = 0)."""
