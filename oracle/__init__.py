@@ -17,4 +17,6 @@ Modules
   spinorb       O-SO: spin-orbital factorised residual.
   spinadapted   O-SA: spin-adapted closed-shell residual (the hot-path oracle).
   solver        diagonal-Jacobian update with DIIS (Sec. III.B).
+  twocsf        two-CSF ASCC (Sec. II.B.2) by brute force: reference, guess,
+                T3'/T4'/T5' slices, Newton solve (tiny systems only).
 """
