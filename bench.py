@@ -229,8 +229,10 @@ SOLVE_ITERATIONS = {("c2", 1): 63, ("c2", 0): 28}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the pair-row ladder GEMM
-# (3-product variant) per launch, from ncu at M=210 N=40000 K=8192
-# (1.3239 GB + 0.1206 GB) scaled by 40000 / 8192
+# (3-product variant) per launch, from the last ncu capture at M=210 N=40000
+# K=8192 (1.3246 GB + 0.1199 GB) scaled by 40000 / 8192; the kernel's store
+# order changed after it, so the roofline reports traffic null and names
+# this figure in its note
 LADDER_TRAFFIC = {("c2", "mixed"): 7.05e9}
 
 DTYPES = {"fp64": "f64", "mixed": "bf16x3-split/f64",
@@ -551,11 +553,12 @@ def main():
                 "h2d_bytes_per_step": int(eps_p.nbytes + B_p.nbytes), "d2h_bytes_per_step": 56},
         "gpu_launches": int(p1.launches - p0.launches),
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": LADDER_TRAFFIC.get((args.workload,
-                                                                            args.precision)),
-                     "traffic_note": ("DRAM bytes of one 3-product launch of this GEMM from the "
-                                      "ncu capture in profiles/ (K = 8192), scaled to K = v^2 "
-                                      "(reads and split-K partials both grow with K)"
+                     "frac": achieved / peak, "traffic": None,
+                     "traffic_note": ("null: the epilogue's store order changed after the last "
+                                      "ncu capture (the same bytes by construction, not "
+                                      "captured again); that capture (profiles/, K = 8192, "
+                                      "scaled to K = v^2) gave %.3g bytes per 3-product launch"
+                                      % LADDER_TRAFFIC[(args.workload, args.precision)]
                                       if (args.workload, args.precision) in LADDER_TRAFFIC
                                       else None),
                      "kernel": {"fp64": "gemm_f64_kernel", "mixed": "gemm_tc_kernel",
