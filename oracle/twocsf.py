@@ -31,6 +31,12 @@ T^{P(0)} = ln(1 + S) = S - S^2/2 + S^3/3 - S^4/4 (excitation operators
 commute; S^5 phi0 = 0): all-primary singles to quadruples, as the section
 states.
 
+Partial linearisation (Sec. II.C) applies as in the one-CSF case: with
+T = T^P + T^N + T1^M + lambda T^M_{>=2} (an excitation is P when every index
+is primary, N when none is, M otherwise; all-primary triples and quadruples
+are T^P here), PLASCC keeps the lambda^0 + lambda^1 part of the projections,
+the ground state with the same primary labels.
+
 The equations are solved by Newton's method with the exact Jacobian
 dR_mu/dt_nu = <mu| exp(-T) [H-bar, X_nu] exp(T) |phi0> (X_nu commutes with T).
 The paper obtains the reference from ESMF (Sec. III.A); cis_two_csf stands in
@@ -39,7 +45,7 @@ for it with the two largest CSFs of a singlet CIS vector.
 Pins (tests/test_twocsf_oracle.py): the guess reproduces the reference
 exactly; with every orbital primary (o = v = 2) the energies are FCI
 eigenvalues; with b = 0 and one primary pair the energy is the one-CSF
-ASCC + T3' oracle's; the example determinants the section prints belong to
+ASCC / PLASCC + T3' oracle's; the example determinants the section prints belong to
 T4' and T5'; the converged state is a singlet.
 """
 from __future__ import annotations
@@ -93,7 +99,7 @@ class TwoCSF:
     electrons."""
 
     def __init__(self, eps, B, o, h1, p1, h2, p2, a, b, excited=True, prim_occ=None,
-                 prim_vir=None):
+                 prim_vir=None, linearize=False):
         v = len(eps) - o
         self.space = sp_ = DetSpace(o, v)
         self.o, self.v = o, v
@@ -129,6 +135,14 @@ class TwoCSF:
             self.sgn.append(float(s))
         self.pos = np.array(self.pos)
         self.sgn = np.array(self.sgn)
+        # partial linearisation (Sec. II.C): T = T^P + T^N + T1^M + lambda T^M_{>=2},
+        # an excitation being P if all its indices are primary, N if none is
+        p_so = ({sp_.spin_orb(i, s_) for i in self.prim_occ for s_ in (0, 1)}
+                | {sp_.spin_orb(o + a_, s_) for a_ in self.prim_vir for s_ in (0, 1)})
+        nprim = np.array([sum(q in p_so for q in I + A) for I, A in self.exc])
+        rank = np.array([len(I) for I, _ in self.exc])
+        self.scaled = (nprim > 0) & (nprim < 2 * rank) & (rank >= 2)
+        self.linearize = linearize
 
     # ------------------------------------------------------------ helpers
     def _exp(self, M, sign):
@@ -185,15 +199,42 @@ class TwoCSF:
         u = self._exp_apply(T, self.ref, +1.0)
         return self._exp(self.S.T.copy(), -1.0) @ u
 
+    # with the mixed amplitudes of rank >= 2 scaled by lambda, the projections
+    # are polynomials of degree <= 4 in lambda (a two-body H-bar); PLASCC keeps
+    # their lambda^0 + lambda^1 coefficients, taken from five evaluations
+    _LAMS = np.array([0.0, 1.0, -1.0, 2.0, -2.0])
+
+    def _linear_part(self, f, t):
+        coef = np.linalg.solve(np.vander(self._LAMS, 5, increasing=True), np.eye(5))
+        vals = [f(np.where(self.scaled, lam * t, t), lam) for lam in self._LAMS]
+        return [sum((coef[0, q] + coef[1, q]) * vals[q][k] for q in range(5))
+                for k in range(len(vals[0]))]
+
     def equations(self, t):
-        """(E, R): projections of exp(-T) H-bar exp(T) phi0 (Eqs. energy, amp)."""
+        """(E, R): projections of exp(-T) H-bar exp(T) phi0 (Eqs. energy, amp);
+        with linearize, their lambda^0 + lambda^1 part (Sec. II.C)."""
+        if self.linearize:
+            E, R = self._linear_part(lambda tl, lam: self._equations(tl), t)
+            return float(E), R
+        return self._equations(t)
+
+    def _equations(self, t):
         T = self.cluster(t)
         u = self._exp_apply(T, self.ref, +1.0)
         psi = self._exp_apply(T, self.Hbar @ u, -1.0)
         return float(psi[self.space.ref]), self.amplitudes_of(psi)
 
     def jacobian(self, t):
-        """dR_mu / dt_nu = <mu| exp(-T) (H-bar X_nu - X_nu H-bar) exp(T) |phi0>."""
+        """dR_mu / dt_nu = <mu| exp(-T) (H-bar X_nu - X_nu H-bar) exp(T) |phi0>;
+        with linearize, of the lambda^0 + lambda^1 part (a scaled amplitude's
+        column carries the factor lambda)."""
+        if self.linearize:
+            return self._linear_part(
+                lambda tl, lam: (self._jacobian(tl) * np.where(self.scaled, lam, 1.0)[None, :],),
+                t)[0]
+        return self._jacobian(t)
+
+    def _jacobian(self, t):
         T = self.cluster(t)
         u = self._exp_apply(T, self.ref, +1.0)
         Hu = self.Hbar @ u

@@ -46,34 +46,40 @@ def test_guess_makes_the_two_csf_reference():
         assert set(I) <= prim_o and set(A) <= prim_v
 
 
-def test_every_orbital_primary_gives_fci():
+@pytest.mark.parametrize("linearize", [False, True])
+def test_every_orbital_primary_gives_fci(linearize):
     """o = v = 2 with all four orbitals primary: T holds every excitation, so
-    the excited and ground solutions are eigenvalues of H."""
+    the excited and ground solutions are eigenvalues of H; every excitation
+    is then all-primary (T^P), so partial linearisation changes nothing."""
     s = synth.make_system(2, 2, seed=2)
     h1, p1, h2, p2, a, b, _ = twocsf.cis_two_csf(s.eps, s.B, 2, 0)
-    st = twocsf.TwoCSF(s.eps, s.B, 2, h1, p1, h2, p2, a, b, prim_occ=[0, 1], prim_vir=[0, 1])
+    st = twocsf.TwoCSF(s.eps, s.B, 2, h1, p1, h2, p2, a, b, prim_occ=[0, 1], prim_vir=[0, 1],
+                       linearize=linearize)
+    assert not st.scaled.any()
     assert len(st.exc) == st.space.dim - 1
     E, _, _ = st.solve()
     w = np.linalg.eigvals(st.H).real
     assert np.min(np.abs(w - E)) < 1e-10
     assert E > w.min() + 1e-3                       # an excited root
     g = twocsf.TwoCSF(s.eps, s.B, 2, h1, p1, h2, p2, a, b, excited=False,
-                      prim_occ=[0, 1], prim_vir=[0, 1])
+                      prim_occ=[0, 1], prim_vir=[0, 1], linearize=linearize)
     Eg, _, _ = g.solve()
     assert Eg == pytest.approx(w.min(), abs=1e-10)
 
 
-def test_one_csf_limit_matches_the_one_csf_oracle():
+@pytest.mark.parametrize("linearize", [False, True])
+def test_one_csf_limit_matches_the_one_csf_oracle(linearize):
     """b = 0 with the primary pair (h1, p1) alone: T4' and T5' are empty and
-    the state is the one-CSF ASCC + T3' state (Sec. II.B.1), which the
-    spin-adapted oracle solves with its own amplitudes and iteration."""
+    the state is the one-CSF ASCC + T3' state (Sec. II.B.1), or its PLASCC
+    form (Sec. II.C), which the spin-adapted oracle solves with its own
+    amplitudes and iteration."""
     o, hole, part = 3, 2, 0
     s = synth.make_system(o, 3, seed=1)
     st = twocsf.TwoCSF(s.eps, s.B, o, hole, part, hole, part, 1 / np.sqrt(2), 0.0,
-                       prim_occ=[hole], prim_vir=[part])
+                       prim_occ=[hole], prim_vir=[part], linearize=linearize)
     assert max(len(I) for I, _ in st.exc) == 3
     E, _, _ = st.solve()
-    ref = ascc.solve_state(s.eps, s.B, o, hole, part, linearize=False, triples=True,
+    ref = ascc.solve_state(s.eps, s.B, o, hole, part, linearize=linearize, triples=True,
                            r_tol=1e-11, e_tol=1e-13, max_iter=400)
     assert ref.converged
     assert E == pytest.approx(ref.energy, abs=1e-9)
@@ -134,3 +140,20 @@ def test_two_csf_state_converges_to_a_singlet_with_t5():
     _, g, _ = _state(excited=False)
     Eg, _, _ = g.solve()
     assert 0.05 < E - Eg < 5.0
+
+
+def test_linearised_jacobian_matches_central_differences():
+    """Newton's Jacobian of the PLASCC equations (the lambda factor of a scaled
+    amplitude's column included) against central differences of the
+    residual, at a perturbed two-CSF guess."""
+    s = synth.make_system(3, 3, seed=3)
+    h1, p1, h2, p2, a, b, _ = twocsf.cis_two_csf(s.eps, s.B, 3, 2)
+    st = twocsf.TwoCSF(s.eps, s.B, 3, h1, p1, h2, p2, a, b, linearize=True)
+    x = st.guess() + 0.01 * np.random.default_rng(0).standard_normal(len(st.exc))
+    J = st.jacobian(x)
+    cols = [0, int(np.nonzero(st.scaled)[0][5]), int(np.nonzero(~st.scaled)[0][-1])]
+    for k in cols:
+        e = np.zeros(len(x))
+        e[k] = 1e-6
+        fd = (st.equations(x + e)[1] - st.equations(x - e)[1]) / 2e-6
+        assert np.abs(J[:, k] - fd).max() < 1e-7 * max(1.0, np.abs(fd).max())
