@@ -71,6 +71,8 @@ enum { ASCC_FP64 = 0, ASCC_MIXED_BF16 = 1, ASCC_FP64_TC = 2 };
 
 typedef struct {
   int32_t n_csf;     /* 0 = ground state (S = 0); 1 = one-CSF excited state     */
+                     /* (two-CSF states, Sec. II.B.2, are not built on the GPU:  */
+                     /*  n_csf = 2 returns ASCC_ERR_INVALID)                      */
   int32_t hole;      /* occupied index h in [0, o) of S (n_csf = 1)              */
   int32_t particle;  /* virtual index p in [0, v) of S (n_csf = 1)               */
   double beta;       /* T^P(0) = beta S + gamma S^2, gamma = -beta^2/2 (Eq.
