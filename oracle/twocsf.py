@@ -46,7 +46,8 @@ Pins (tests/test_twocsf_oracle.py): the guess reproduces the reference
 exactly; with every orbital primary (o = v = 2) the energies are FCI
 eigenvalues; with b = 0 and one primary pair the energy is the one-CSF
 ASCC / PLASCC + T3' oracle's; the example determinants the section prints belong to
-T4' and T5'; the converged state is a singlet.
+T4' and T5'; the converged state is a singlet; the CIS matrix is H on
+the singlet singles.
 """
 from __future__ import annotations
 
@@ -267,13 +268,9 @@ class TwoCSF:
         return E, t, max_iter
 
 
-def cis_two_csf(eps, B, o, root):
-    """A two-CSF reference from a singlet CIS vector (stand-in for the ESMF
-    wave function of Sec. III.A, which is CIS with orbital relaxation): the two
-    largest singlet CSF coefficients c1 (h1 -> p1) and c2 (h2 -> p2) of CIS
-    root `root`, scaled to 2a^2 + 2b^2 = 1 (Eq. 2csf).  Singlet CIS matrix:
-    A[ia, jb] = delta_ij delta_ab (e_a - e_i) + 2 (ia|jb) - (ij|ab).
-    Returns (h1, p1, h2, p2, a, b, weights of the three largest CSFs)."""
+def cis_singlet_matrix(eps, B, o):
+    """Singlet CIS matrix over the CSFs (phi_i^a + phi_ib^ab)/sqrt(2), row
+    i * v + a: A[ia, jb] = delta_ij delta_ab (e_a - e_i) + 2 (ia|jb) - (ij|ab)."""
     eps = np.asarray(eps, float)
     v = len(eps) - o
     g = ham.eri_from_df(np.asarray(B, float))
@@ -282,7 +279,15 @@ def cis_two_csf(eps, B, o, root):
         for j, b in itertools.product(range(o), range(v)):
             A[i * v + a, j * v + b] = ((i == j) * (a == b) * (eps[o + a] - eps[i])
                                        + 2.0 * g[i, o + a, j, o + b] - g[i, j, o + a, o + b])
-    _, U = np.linalg.eigh(A)
+    return A
+
+
+def cis_two_csf(eps, B, o, root):
+    """A two-CSF reference from a singlet CIS vector (stand-in for the ESMF
+    wave function of Sec. III.A, which is CIS with orbital relaxation): the two
+    largest singlet CSF coefficients c1 (h1 -> p1) and c2 (h2 -> p2) of CIS
+    root `root`, scaled to 2a^2 + 2b^2 = 1 (Eq. 2csf).  Returns (h1, p1, h2, p2, a, b, weights of the three largest CSFs)."""
+    _, U = np.linalg.eigh(cis_singlet_matrix(eps, B, o))
     c = U[:, root]
     order = np.argsort(-np.abs(c))
     (h1, p1), (h2, p2) = divmod(int(order[0]), v), divmod(int(order[1]), v)

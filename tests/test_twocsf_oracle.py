@@ -157,3 +157,23 @@ def test_linearised_jacobian_matches_central_differences():
         e[k] = 1e-6
         fd = (st.equations(x + e)[1] - st.equations(x - e)[1]) / 2e-6
         assert np.abs(J[:, k] - fd).max() < 1e-7 * max(1.0, np.abs(fd).max())
+
+
+def test_cis_matrix_is_h_on_the_singlet_singles():
+    """The CIS matrix that picks the reference equals <CSF_ia| H - E_HF |CSF_jb>
+    for the singlet CSFs (phi_i^a + phi_ib^ab) / sqrt(2), built in the
+    determinant space from H itself."""
+    o, v = 3, 3
+    s = synth.make_system(o, v, seed=4)
+    st = twocsf.TwoCSF(s.eps, s.B, o, 0, 0, 0, 0, 0.0, 0.0, excited=False)
+    sp_ = st.space
+    C = np.zeros((sp_.dim, o * v))
+    for i in range(o):
+        for a in range(v):
+            for sg in (0, 1):
+                sgn, d = apply_ops(sp_.dets[sp_.ref], [(sp_.spin_orb(o + a, sg), True),
+                                                       (sp_.spin_orb(i, sg), False)])
+                C[sp_.index[d], i * v + a] += sgn / np.sqrt(2.0)
+    e_hf = st.H[sp_.ref, sp_.ref]
+    want = C.T @ st.H @ C - e_hf * np.eye(o * v)
+    assert np.abs(twocsf.cis_singlet_matrix(s.eps, s.B, o) - want).max() < 1e-12
