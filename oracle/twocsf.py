@@ -286,7 +286,9 @@ def cis_two_csf(eps, B, o, root):
     """A two-CSF reference from a singlet CIS vector (stand-in for the ESMF
     wave function of Sec. III.A, which is CIS with orbital relaxation): the two
     largest singlet CSF coefficients c1 (h1 -> p1) and c2 (h2 -> p2) of CIS
-    root `root`, scaled to 2a^2 + 2b^2 = 1 (Eq. 2csf).  Returns (h1, p1, h2, p2, a, b, weights of the three largest CSFs)."""
+    root `root`, scaled to 2a^2 + 2b^2 = 1 (Eq. 2csf).  Returns (h1, p1, h2,
+    p2, a, b, weights of the three largest CSFs)."""
+    v = len(eps) - o
     _, U = np.linalg.eigh(cis_singlet_matrix(eps, B, o))
     c = U[:, root]
     order = np.argsort(-np.abs(c))
