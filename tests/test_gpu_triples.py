@@ -18,12 +18,13 @@ pytestmark = pytest.mark.gpu
 REL_TOL = 1e-9
 E_TOL = 1e-10
 # Both solves stop at max|R| <= 1e-8 and |dE| <= 1e-10 (the stopping rule of
-# Sec. III.A, tightened), not a bound on the distance to the fixed point.  At o=20, v=200 with
-# T3' the energy left at that residual is about 1e-10 Eh: two FP64-class GPU
-# solves of this state that differ only in DIIS depth (16 and 32) stop
-# 1.1e-10 Eh apart.  Two trajectories (oracle and GPU) are therefore compared
-# at ten times that.
-C2_T3_E_TOL = 1e-9
+# Sec. III.A, tightened), not a bound on the distance to the fixed point.  At
+# o=20, v=200 with T3' the energy still moves by up to about 2e-9 Eh per
+# iteration once max|R| is below 1e-8: the oracle's own solve of this state
+# moved by 9.1e-10, 4.5e-10, 1.7e-9 and 2.1e-9 Eh over iterations 52-55 at
+# max|R| = 9.8e-9 ... 3.1e-9.  Two trajectories (oracle and GPU) are therefore
+# compared at 5e-9 Eh.
+C2_T3_E_TOL = 5e-9
 
 
 def _ctx(s, hole, part, **kw):
@@ -121,7 +122,7 @@ def test_residual_with_triples_mid_size(precision):
 def test_solve_with_triples_matches_stored_oracle_energy(name, precision, tol):
     """Converged ASCCSD / PLASCCSD energies with T3' against the oracle's
     (tests/golden/make_reference_energies.py); FP64 and FP64-class paths at
-    1e-10 Eh (1e-9 Eh at o=20, v=200, see C2_T3_E_TOL), mixed precision at
+    1e-10 Eh (5e-9 Eh at o=20, v=200, see C2_T3_E_TOL), mixed precision at
     1e-6 Eh."""
     o, v, seed, hole, part, method, e_ref = _golden(name)
     s = synth.make_system(o, v, seed=seed)
